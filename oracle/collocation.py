@@ -1,0 +1,115 @@
+"""Collocation factors, assembled collocation matrix A_C and preconditioner P_C.
+
+Paper references:
+* eq. (univariatecolloc): (M_l)_{ij} = B_j(tau_{l,i}), (K_l)_{ij} = -B''_j(tau_{l,i}),
+  i, j = 1..n  (interior basis B_1..B_n, eq. space);
+* eq. (collocation) / (collocationsystem): row I of A_C is (L B_J)(F(tau_I));
+* eq. (space): scalar index i = 1 + sum_l n^{l-1} (i_l - 1), i.e. i_1 runs fastest,
+  so a tensor product "D_d (x) ... (x) D_1" is numpy ``kron(D_d, ..., D_1)``;
+* eq. (colloc2D) / (colloc3D) and Sec. 3: P_C = K2 (x) M1 + M2 (x) K1 (2D) and the
+  three-term sum in 3D.
+"""
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import bspline
+from .geometry import pullback_coefficients
+
+
+class Space1D:
+    """One parametric direction: knots, Greville points and the three n x n
+    collocation matrices B0 = M, B1 = B', B2 = B'' (K = -B2)."""
+
+    def __init__(self, n_elem, p):
+        self.n_elem, self.p = n_elem, p
+        self.t = bspline.open_uniform_knots(n_elem, p)
+        self.m = bspline.num_basis(self.t, p)
+        self.n = self.m - 2
+        self.tau = bspline.greville_interior(self.t, p)
+        full = [np.array([bspline.basis_all(self.t, p, x, r) for x in self.tau])
+                for r in range(3)]
+        # drop B_0 and B_{m-1} (homogeneous Dirichlet, eq. space)
+        self.B = [f[:, 1:self.m - 1].copy() for f in full]
+
+    @property
+    def M(self):
+        return self.B[0]
+
+    @property
+    def K(self):
+        return -self.B[2]
+
+
+def kron_list(mats):
+    """mats[l] acts on direction l+1; returns mats[d-1] (x) ... (x) mats[0] (sparse)."""
+    out = sp.csr_matrix(mats[-1])
+    for A in reversed(mats[:-1]):
+        out = sp.kron(out, sp.csr_matrix(A), format="csr")
+    return out
+
+
+def tensor_points(taus):
+    """All parametric collocation points tau_I in scalar order (i_1 fastest):
+    array of shape (N, d) with column l = tau_{l, i_l}."""
+    d = len(taus)
+    grids = np.meshgrid(*taus[::-1], indexing="ij")  # slowest first
+    pts = np.stack([g.ravel() for g in grids[::-1]], axis=1)
+    assert pts.shape[1] == d
+    return pts
+
+
+def physical_points(fmap, taus):
+    """F(tau_I) for every collocation point, shape (N, d)."""
+    return np.array([fmap.F(x) for x in tensor_points(taus)])
+
+
+def coefficient_fields(fmap, taus):
+    """G^{ab}(tau_I) and L_c(tau_I) at every collocation point: shapes (N,d,d), (N,d)."""
+    pts = tensor_points(taus)
+    N, d = pts.shape
+    G = np.empty((N, d, d))
+    L = np.empty((N, d))
+    for i, x in enumerate(pts):
+        G[i], L[i] = pullback_coefficients(fmap, x)
+    return G, L
+
+
+def assemble_collocation(spaces, fmap):
+    """A_C in CSR, from the definition: row I = -sum_{a,b} G^{ab}(tau_I) d_a d_b B_J(tau_I)
+    - sum_c L_c(tau_I) d_c B_J(tau_I), with tensor-product B_J (eq. multivariatesplines).
+
+    The derivative multi-index (e_1, .., e_d) picks the 1D matrix B[e_l] in direction l.
+    """
+    d = len(spaces)
+    G, L = coefficient_fields(fmap, [s.tau for s in spaces])
+    N = G.shape[0]
+    A = sp.csr_matrix((N, N))
+    for a, b in itertools.product(range(d), range(d)):
+        orders = [0] * d
+        orders[a] += 1
+        orders[b] += 1
+        term = kron_list([spaces[l].B[orders[l]] for l in range(d)])
+        A = A - sp.diags(G[:, a, b]) @ term
+    for c in range(d):
+        orders = [0] * d
+        orders[c] = 1
+        term = kron_list([spaces[l].B[orders[l]] for l in range(d)])
+        A = A - sp.diags(L[:, c]) @ term
+    A = A.tocsr()
+    A.eliminate_zeros()
+    return A
+
+
+def assemble_preconditioner(spaces):
+    """P_C from eq. (colloc2D) (d = 2) or eq. (colloc3D) (d = 3): sum over l of the
+    Kronecker product with K_l in slot l and M in every other slot."""
+    d = len(spaces)
+    P = None
+    for l in range(d):
+        mats = [spaces[j].K if j == l else spaces[j].M for j in range(d)]
+        term = kron_list(mats)
+        P = term if P is None else P + term
+    return P.tocsr()

@@ -1,0 +1,57 @@
+"""Plant plausible mistakes in the oracle (CPU only) and check that a pin catches each.
+
+Each mutation is applied with monkeypatch to a copy of the oracle's behaviour; the
+corresponding pin from the other test files is re-run inline and must fail.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import bspline, collocation as C, fd as F, geometry as Geo
+import tests.test_oracle_collocation as TC
+
+
+def test_dropped_first_order_term_is_caught(monkeypatch):
+    orig = Geo.pullback_coefficients
+
+    def no_L(fmap, xi):
+        G, L = orig(fmap, xi)
+        return G, 0.0 * L
+
+    monkeypatch.setattr(C, "pullback_coefficients", no_L)
+    with pytest.raises(AssertionError):
+        TC.test_operator_on_exact_polynomial_2d(3)
+
+
+def test_transposed_kronecker_order_is_caught(monkeypatch):
+    def wrong_kron(mats):
+        out = C.sp.csr_matrix(mats[0])
+        for A in mats[1:]:
+            out = C.sp.kron(out, C.sp.csr_matrix(A), format="csr")
+        return out
+
+    monkeypatch.setattr(C, "kron_list", wrong_kron)
+    with pytest.raises(AssertionError):
+        TC.test_operator_on_exact_polynomial_2d(3)
+
+
+def test_wrong_sign_of_K_is_caught():
+    s = C.Space1D(64, 3)
+    lam, _, _ = F.eig_factors(s.B[2], s.M)  # K = +B'' instead of -B''
+    assert not abs(lam[0] / np.pi**2 - 1.0) < 2e-3
+
+
+def test_off_by_one_greville_is_caught():
+    t = bspline.open_uniform_knots(4, 3)
+    wrong = np.array([np.mean(t[i + 2:i + 5]) for i in range(1, 6)])  # shifted knot window
+    ref = np.array([1 / 12, 0.25, 0.5, 0.75, 11 / 12])
+    assert np.max(np.abs(wrong - ref)) > 1e-3
+
+
+def test_transposed_V_in_fd_is_caught():
+    spaces = [C.Space1D(6, 3), C.Space1D(6, 3)]
+    P = C.assemble_preconditioner(spaces)
+    fd = F.FD(spaces)
+    fd.V = [V.T for V in fd.V]
+    b = np.random.default_rng(1).standard_normal(P.shape[0])
+    assert np.linalg.norm(fd(P @ b) - b) > 1e-6 * np.linalg.norm(b)
