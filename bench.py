@@ -1,0 +1,384 @@
+"""Benchmark: GMRES + FD time-to-1e-8 and DOF-iterations per second on one GB300.
+
+Workload (default): the 3D extruded thick quarter annulus r in [1,2], z in [0,1],
+64 elements per direction, p = 3, 4, 5 (N = 274,625 / 287,496 / 300,763), forcing
+from the manufactured solution plus the seeded 1e-3 perturbation, GMRES tol 1e-8,
+FP64 throughout.  One step = one solve for each p (cached setup).  The mixed
+(TF32-FD flexible GMRES) form of the same solves is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (the
+path does not shard); value = all ranks' DOF-iterations / max time over ranks.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload as W  # noqa: E402
+
+METRIC = "GMRES+FD time-to-1e-8 residual, DOF-iter/s (mixed vs FP64, 1 GB300); p50/p99"
+UNIT = "DOF-iter/s"
+WORKLOAD = "3d_annulus_ne64"
+TOL = 1e-8
+MAX_ITER = 200
+FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64 (recipe table); derivation in the design doc
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------- helpers
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_fd64.cu",):
+        with open(os.path.join(ROOT, "paper_1705_04384_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """dram bytes per launch of the dominant kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    return t.get("bytes_per_launch_full")
+
+
+def percentile(vals, q):
+    return float(np.percentile(np.asarray(vals, dtype=np.float64), q)) if vals else None
+
+
+# ------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """Time the FP64 CPU oracle on a bounded sample of the same workload."""
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import collocation as C, fd as F, geometry as Geo, gmres as G
+    c = W.CONFIGS[WORKLOAD]
+    p = c["ps"][0]
+    spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
+    fmap = Geo.make_map("annulus", 3, c["r0"], c["r1"])
+    A = C.assemble_collocation(spaces, fmap)
+    pts = C.physical_points(fmap, [s.tau for s in spaces])
+    b = W.config_rhs(WORKLOAD, pts, 0)
+    fd = F.FD(spaces)
+    N = A.shape[0]
+    k_sample = 6
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = G.gmres(A, b, M=fd, tol=0.0, max_iter=k_sample)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = N * k_sample * len(times) / tot
+    cores = os.cpu_count()
+    sample = (f"oracle GMRES+FD, {WORKLOAD} p={p} (N={N}), {k_sample} Arnoldi steps per step "
+              f"(iteration phase; CSR assembly and eigendecomposition outside the timer)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{WORKLOAD} p={p}", "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "last_relres_est": float(r["hist"][-1])}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands on the host cores, bounded: iteration phase of a
+    few GMRES steps on the p = 3 problem of the workload."""
+    from oracle import collocation as C, fd as F, geometry as Geo, gmres as G
+    c = W.CONFIGS[WORKLOAD]
+    p = c["ps"][0]
+    spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
+    fmap = Geo.make_map("annulus", 3, c["r0"], c["r1"])
+    A = C.assemble_collocation(spaces, fmap)
+    pts = C.physical_points(fmap, [s.tau for s in spaces])
+    b = W.config_rhs(WORKLOAD, pts, 0)
+    fd = F.FD(spaces)
+    k = 10
+    t0 = time.perf_counter()
+    G.gmres(A, b, M=fd, tol=0.0, max_iter=k)
+    dt = time.perf_counter() - t0
+    N = A.shape[0]
+    return {"value": N * k / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{k} GMRES+FD steps (iteration phase) of {WORKLOAD} p={p}, N={N}; "
+                      f"{dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1705_04384_gb300.api import Problem
+
+    c = W.CONFIGS[WORKLOAD]
+    stream = torch.cuda.current_stream(dev)
+
+    def make(prec):
+        probs = []
+        for i, p in enumerate(c["ps"]):
+            P = Problem(3, c["n_elem"], p, "annulus", c["r0"], c["r1"], precision=prec,
+                        device=dev, stream=stream)
+            pts = P.collocation_points()
+            rhs = torch.from_numpy(W.config_rhs(WORKLOAD, pts, i)).to(dev)
+            probs.append((p, P, rhs, torch.empty_like(rhs)))
+        return probs
+
+    t_setup = time.perf_counter()
+    fp64 = make("fp64")
+    t_setup = time.perf_counter() - t_setup
+    mixed = None
+    if not args.no_mixed:
+        try:
+            mixed = make("tf32")
+        except Exception as e:  # the mixed form is reported when it is built
+            mixed = None
+            mixed_err = str(e)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_step(probs, record):
+        per = []
+        for p, P, rhs, x in probs:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+            e1.record(stream)
+            per.append((p, P, info, e0, e1))
+        torch.cuda.synchronize(dev)
+        out = []
+        for p, P, info, e0, e1 in per:
+            out.append((p, P.N, info["iters"], e0.elapsed_time(e1) * 1e-3, info["relres_true"]))
+        return out
+
+    def timed(probs, steps, warmup):
+        for _ in range(warmup):
+            run_step(probs, False)
+        results = []
+        for _ in range(steps):
+            flush.fill_(1.0)  # L2 flush between steps, outside the timed solves
+            torch.cuda.synchronize(dev)
+            results.append(run_step(probs, True))
+        return results
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    res64 = timed(fp64, args.steps, args.warmup)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_times = [sum(s[3] for s in step) for step in res64]
+    dof_iters = [sum(s[1] * s[2] for s in step) for step in res64]
+    total_t = sum(step_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_t = float(t.item())
+        dist.barrier()
+    value = world * sum(dof_iters) / total_t
+    solve_ms = [s[3] * 1e3 for step in res64 for s in step]
+    iters = {str(s[0]): s[2] for s in res64[-1]}
+    relres = {str(s[0]): s[4] for s in res64[-1]}
+    launches = 0
+    for step in res64:
+        for (p, P, rhs, x), s in zip(fp64, step):
+            f, it = P.launch_counts()
+            launches += f + it * s[2]
+
+    # dominant kernel: the FP64 FD mode-product GEMM (6 launches per FD apply)
+    p0, P0, rhs0, x0 = fp64[0]
+    reps = 20
+    flush.fill_(1.0)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    buf = torch.empty_like(rhs0)
+    e0.record(stream)
+    for _ in range(reps):
+        P0.precond_apply(rhs0, out=buf)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_launch = e0.elapsed_time(e1) * 1e-3 / (reps * 6)
+    n = P0.n
+    flops = 2.0 * n ** 4
+    achieved = flops / t_launch / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": committed_traffic(),
+                "kernel": "gemm_fp64_kernel (FD mode product, FP64 CUDA cores)",
+                "per_launch_us": t_launch * 1e6, "flops_per_launch": flops,
+                "peak_note": "nominal GB300 FP64 1.25 TFLOP/s (recipe table); of nominal"}
+
+    # end to end through the host-buffer entry point
+    e2e_times, e2e_dofit, h2d, d2h = [], 0, 0, 0
+    host = []
+    for p, P, rhs, x in fp64:
+        hr = torch.empty(P.N, dtype=torch.float64, pin_memory=True)
+        hr.copy_(rhs.cpu())
+        hx = torch.empty(P.N, dtype=torch.float64, pin_memory=True)
+        host.append((P, hr, hx))
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        its = 0
+        for P, hr, hx in host:
+            info = P.solve_host(hr, hx, tol=TOL, max_iter=MAX_ITER)
+            its += P.N * info["iters"]
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            e2e_times.append(dt)
+            e2e_dofit += its
+    for P, hr, hx in host:
+        h2d += P.N * 8
+        d2h += P.N * 8 + (MAX_ITER + 1) * 8 + 64
+    e2e = {"value": world * e2e_dofit / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    mixed_out = None
+    if mixed is not None:
+        resm = timed(mixed, args.steps, args.warmup)
+        mt = sum(sum(s[3] for s in step) for step in resm)
+        md = sum(sum(s[1] * s[2] for s in step) for step in resm)
+        mixed_out = {"value": world * md / mt, "unit": UNIT,
+                     "iters": {str(s[0]): s[2] for s in resm[-1]},
+                     "relres_true": {str(s[0]): s[4] for s in resm[-1]},
+                     "p50_ms": percentile([s[3] * 1e3 for st in resm for s in st], 50),
+                     "p99_ms": percentile([s[3] * 1e3 for st in resm for s in st], 99),
+                     "time_to_solution_ms_per_step": 1e3 * mt / len(resm)}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(res64),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 3D extruded quarter annulus r in [1,2], 64 "
+                                   f"elements/dir, p=3,4,5, FP64 FD-GMRES, tol 1e-8",
+                       "step": "one solve per p (setup cached)",
+                       "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"},
+            "p50_ms": percentile(solve_ms, 50), "p99_ms": percentile(solve_ms, 99),
+            "iters": iters, "relres_true": relres, "setup_s_cold": t_setup,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "mixed": mixed_out}
+    if mixed_out is None and not args.no_mixed:
+        line["mixed_unavailable"] = mixed_err if "mixed_err" in locals() else "not built"
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * iga_fd.h -- C ABI of the GB300 (sm_103a) library for IGA collocation of the
+ * Poisson problem solved by GMRES preconditioned with fast diagonalization (FD).
+ *
+ * Method: M. Tani, "A preconditioning strategy for linear systems arising from
+ * nonsymmetric schemes in isogeometric analysis", arXiv:1705.04384.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Degrees of freedom: n = n_elem + p - 2 per direction (Sec. 2.1, eq. space:
+ *   interior basis B_1..B_n of the open knot vector with n_elem uniform elements,
+ *   simple interior knots, C^{p-1}); N = n^d.
+ * - Vector layout: one value per DOF / collocation point in the scalar order of
+ *   eq. (space), i = i_1 + n i_2 + n^2 i_3 (0-based), i_1 fastest, contiguous,
+ *   IEEE binary64.
+ * - "_dev" pointers are CUDA device pointers on the device that was current at
+ *   iga_setup; "_host" pointers are ordinary host memory.  The CALLER owns every
+ *   pointer it passes; the library never frees or retains them after returning.
+ * - The LIBRARY owns all state behind an iga_handle (1D factors, eigen-factors,
+ *   geometry coefficients, Krylov workspace, CUDA graphs); iga_destroy frees it.
+ *   1D factors are cached per (n_elem, p) and shared between handles.
+ * - All device work is ordered on the stream given to iga_setup (NULL = legacy
+ *   default stream).  Calls returning results to host memory synchronize that
+ *   stream before returning; iga_apply_operator and iga_precond_apply are
+ *   asynchronous (stream-ordered) and return right after enqueueing.
+ * - A handle must not be used from two host threads at once.
+ * - Errors: every call returns an iga_status; nothing is thrown across the ABI
+ *   and nothing calls exit().  iga_last_error() gives a message for the most
+ *   recent failure on the calling thread.  On IGA_ERR_CUDA the handle should be
+ *   destroyed.
+ */
+#ifndef IGA_FD_H
+#define IGA_FD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iga_ctx *iga_handle;
+
+typedef enum {
+  IGA_OK = 0,
+  IGA_ERR_INVALID_ARG = 1,        /* bad size, pointer or enum value                  */
+  IGA_ERR_OOM = 2,                /* device or host allocation failed                 */
+  IGA_ERR_CUDA = 3,               /* a CUDA runtime / cuSOLVER call failed            */
+  IGA_ERR_NOT_DIAGONALIZABLE = 4, /* Remark 1 violated: complex eigenvalues or
+                                     ill-conditioned eigenvector matrix               */
+  IGA_ERR_NO_CONVERGENCE = 5,     /* tolerance not reached within max_iter            */
+  IGA_ERR_DEVICE_TIMEOUT = 6,     /* a bounded device-side wait gave up               */
+  IGA_ERR_NAN = 7,                /* non-finite value in the right-hand side or solve */
+  IGA_ERR_UNSUPPORTED = 8         /* valid request this build does not implement      */
+} iga_status;
+
+/* Geometry map F : [0,1]^d -> Omega (Sec. 2.1, single patch).  Analytic maps:
+ *  IDENTITY          Omega = [0,1]^d; then A_C = P_C (eqs. colloc2D / colloc3D).
+ *  QUARTER_ANNULUS   d = 2: x = r cos(pi eta/2), y = r sin(pi eta/2),
+ *                    r = r_inner + (r_outer - r_inner) xi  (Sec. 5 quarter of ring);
+ *                    d = 3: the same ring extruded, z = zeta.
+ *  REVOLVED_ANNULUS  d = 3: the ring turned by pi/2 * zeta about the axis through
+ *                    (-1,-1,-1) with direction (0,1,0) (Sec. 5 revolved ring).       */
+typedef enum {
+  IGA_GEOM_IDENTITY = 0,
+  IGA_GEOM_QUARTER_ANNULUS = 1,
+  IGA_GEOM_REVOLVED_ANNULUS = 2
+} iga_geom_kind;
+
+typedef struct {
+  int kind;       /* iga_geom_kind */
+  double r_inner; /* ring radii (ignored for IDENTITY); 0 < r_inner < r_outer */
+  double r_outer;
+} iga_geometry;
+
+/* Precision of the preconditioner apply (Sec. 4 FD).  FP64: plain GMRES with an
+ * FP64 FD.  TF32 / BF16: FD mode products on the tcgen05 tensor cores with FP32
+ * accumulation inside flexible GMRES; operator, orthogonalization, least squares
+ * and eigen-factors stay FP64.  NONE: no preconditioner (P = I).                    */
+typedef enum {
+  IGA_PREC_FP64 = 0,
+  IGA_PREC_TF32 = 1,
+  IGA_PREC_BF16 = 2,
+  IGA_PREC_NONE = 3
+} iga_precision;
+
+/* Factor selectors for iga_get_factor (all n x n row-major unless noted). */
+typedef enum {
+  IGA_FACTOR_TAU = 0,    /* Greville points tau_i, eq. (greville): n values        */
+  IGA_FACTOR_M = 1,      /* (M)_ij = B_j(tau_i), eq. (univariatecolloc)            */
+  IGA_FACTOR_B1 = 2,     /* B'_j(tau_i)                                            */
+  IGA_FACTOR_K = 3,      /* (K)_ij = -B''_j(tau_i), eq. (univariatecolloc)         */
+  IGA_FACTOR_LAMBDA = 4, /* eigenvalues D of M^{-1}K, eq. (eigendecomposition), asc */
+  IGA_FACTOR_U = 5,      /* eigenvectors U (unit 2-norm columns)                   */
+  IGA_FACTOR_VT = 6      /* V^T = (M U)^{-1}  (Sec. 4, V := (M U)^{-T})             */
+} iga_factor;
+
+/* Build a problem: 1D spaces and collocation factors (Sec. 2.1-2.2), geometry
+ * coefficients of the pulled-back operator at the collocation points F(tau_I),
+ * and the FD eigen-factors of eq. (eigendecomposition) for each direction.
+ *   d          2 or 3
+ *   n_elem     elements per direction, >= 3 (so that n >= p + 1)
+ *   p          spline degree, 2..6
+ *   geom       geometry (not retained)
+ *   precision  iga_precision
+ *   stream     cudaStream_t to order all work on (NULL = default stream)
+ *   out        receives the handle
+ * Synchronous.  Errors: INVALID_ARG, OOM, CUDA, NOT_DIAGONALIZABLE.           */
+iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom,
+                     int precision, void *stream, iga_handle *out);
+
+/* n (DOFs per direction) and N = n^d.  Either pointer may be NULL. */
+iga_status iga_dims(iga_handle h, int *n, long long *N);
+
+/* Physical collocation points F(tau_I) (eq. collocation), written as N x d
+ * row-major doubles (point I at xyz_host[I*d .. I*d+d-1]) in DOF order.  The
+ * right-hand side of eq. (collocationsystem) is f evaluated at these points. */
+iga_status iga_collocation_points(iga_handle h, double *xyz_host);
+
+/* Copy a 1D factor of direction dir (0..d-1) to host memory (see iga_factor for
+ * shapes).  Synchronous.                                                     */
+iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host);
+
+/* Au = A_C u: the collocation matrix of eq. (collocationsystem), applied matrix-
+ * free by sum factorization of the banded 1D factors and a pointwise contraction
+ * with the geometry coefficients.  u_dev, Au_dev: N doubles, must not overlap.
+ * Stream-ordered, asynchronous.                                              */
+iga_status iga_apply_operator(iga_handle h, const double *u_dev, double *Au_dev);
+
+/* s = P^{-1} b by the FD method, eq. (FD2D) (d = 2) or eq. (FD3D) (d = 3), in the
+ * handle's precision (TF32/BF16 round the input and intermediates; the result is
+ * returned in binary64).  For IGA_PREC_NONE it copies b.  b_dev, s_dev: N doubles,
+ * must not overlap.  Stream-ordered, asynchronous.                           */
+iga_status iga_precond_apply(iga_handle h, const double *b_dev, double *s_dev);
+
+/* Solve A_C x = rhs (eq. collocationsystem) by unrestarted GMRES (Sec. 3, Saad &
+ * Schultz), right-preconditioned with P^{-1} (flexible GMRES for TF32/BF16),
+ * until |g_{k+1}| <= tol * ||rhs||_2 or max_iter iterations.
+ *   rhs_dev       N doubles (device)
+ *   x_dev         N doubles (device): the solution on return; if use_x0 != 0 it
+ *                 holds the initial guess on entry, else x0 = 0
+ *   tol           relative residual target (> 0 or 0 to run max_iter steps)
+ *   max_iter      1..4096
+ *   iters         (host, may be NULL) iterations performed
+ *   res_hist_host (host, may be NULL) max_iter + 1 doubles: estimated relative
+ *                 residuals |g_j| / ||rhs||, j = 0..iters
+ *   true_relres   (host, may be NULL) ||rhs - A_C x|| / ||rhs|| evaluated in FP64
+ * Returns IGA_OK, IGA_ERR_NO_CONVERGENCE (x and outputs still valid), IGA_ERR_NAN
+ * (non-finite rhs or breakdown), or an error.  Synchronizes the stream.      */
+iga_status iga_solve(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0,
+                     double tol, int max_iter, int *iters, double *res_hist_host,
+                     double *true_relres);
+
+/* iga_solve with host buffers: copies rhs_host (N doubles) to the device, solves
+ * with x0 = 0, and copies the solution to x_host (N doubles).  Same outputs and
+ * errors as iga_solve.  Synchronous.                                         */
+iga_status iga_solve_host(iga_handle h, const double *rhs_host, double *x_host,
+                          double tol, int max_iter, int *iters, double *res_hist_host,
+                          double *true_relres);
+
+/* Kernel launches of one iga_solve with this handle: fixed + per_iteration * iters.
+ * Counts this library's kernels in the captured solve graph (prologue + epilogue,
+ * and one Arnoldi step); builds the graph if no solve has run yet.           */
+iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration);
+
+/* Release everything the handle owns.  NULL is accepted. */
+iga_status iga_destroy(iga_handle h);
+
+/* Static English description of a status code. */
+const char *iga_status_string(iga_status s);
+
+/* Message for the last failure on the calling thread ("" if none). */
+const char *iga_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGA_FD_H */

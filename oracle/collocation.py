@@ -113,3 +113,41 @@ def assemble_preconditioner(spaces):
         term = kron_list(mats)
         P = term if P is None else P + term
     return P.tocsr()
+
+
+def collocation_rows(spaces, fmap, rows):
+    """Selected rows of A_C (same definition as ``assemble_collocation``), for
+    checking large problems on sampled collocation points.  Returns a dense array
+    of shape (len(rows), N)."""
+    d = len(spaces)
+    ns = [s.n for s in spaces]
+    N = int(np.prod(ns))
+    out = np.zeros((len(rows), N))
+    for r, I in enumerate(rows):
+        idx = []
+        rem = int(I)
+        for l in range(d):
+            idx.append(rem % ns[l])
+            rem //= ns[l]
+        xi = np.array([spaces[l].tau[idx[l]] for l in range(d)])
+        G, Lv = pullback_coefficients(fmap, xi)
+        row = np.zeros(N)
+
+        def add(coef, orders):
+            vecs = [spaces[l].B[orders[l]][idx[l]] for l in range(d)]
+            t = vecs[-1]
+            for v in reversed(vecs[:-1]):
+                t = np.kron(t, v)
+            row[:] -= coef * t
+
+        for a, b in itertools.product(range(d), range(d)):
+            orders = [0] * d
+            orders[a] += 1
+            orders[b] += 1
+            add(G[a, b], orders)
+        for c in range(d):
+            orders = [0] * d
+            orders[c] = 1
+            add(Lv[c], orders)
+        out[r] = row
+    return out

@@ -1,0 +1,141 @@
+"""Thin Python binding over the C ABI (include/iga_fd.h).
+
+Argument marshalling only: torch tensors supply device memory and the stream;
+every step of the method runs inside ``libiga_fd.so``.
+"""
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Geometry, check
+
+GEOM = {"identity": 0, "annulus": 1, "revolved": 2}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3}
+FACTOR = {"tau": 0, "M": 1, "B1": 2, "K": 3, "lambda": 4, "U": 5, "Vt": 6}
+STATUS_OK, STATUS_NO_CONVERGENCE, STATUS_NAN = 0, 5, 7
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """One collocation problem: ``iga_setup`` ... ``iga_destroy``."""
+
+    def __init__(self, d, n_elem, p, geometry="annulus", r_inner=1.0, r_outer=2.0,
+                 precision="fp64", device="cuda", stream=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        self.d, self.n_elem, self.p = d, n_elem, p
+        self.precision = precision
+        self.geometry = geometry
+        self.r_inner, self.r_outer = r_inner, r_outer
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        g = Geometry(GEOM[geometry], float(r_inner), float(r_outer))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.iga_setup(d, n_elem, p, ctypes.byref(g), PREC[precision],
+                                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
+                  "iga_setup")
+        self.h = h
+        n = ctypes.c_int()
+        N = ctypes.c_longlong()
+        check(self.lib.iga_dims(self.h, ctypes.byref(n), ctypes.byref(N)), "iga_dims")
+        self.n, self.N = n.value, N.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.iga_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- host queries
+    def collocation_points(self):
+        out = np.empty((self.N, self.d), dtype=np.float64)
+        check(self.lib.iga_collocation_points(self.h, out.ctypes.data_as(ctypes.c_void_p)),
+              "iga_collocation_points")
+        return out
+
+    def factor(self, which, direction=0):
+        shape = (self.n,) if which in ("tau", "lambda") else (self.n, self.n)
+        out = np.empty(shape, dtype=np.float64)
+        check(self.lib.iga_get_factor(self.h, direction, FACTOR[which],
+                                      out.ctypes.data_as(ctypes.c_void_p)), "iga_get_factor")
+        return out
+
+    def launch_counts(self):
+        """(fixed, per_iteration): kernel launches of one solve = fixed + per_iteration * iters."""
+        f, it = ctypes.c_int(), ctypes.c_int()
+        check(self.lib.iga_launch_counts(self.h, ctypes.byref(f), ctypes.byref(it)),
+              "iga_launch_counts")
+        return f.value, it.value
+
+    # ---------------------------------------------------------------- device ops
+    def _vec(self, v):
+        v = torch.as_tensor(v, dtype=torch.float64, device=self.device).contiguous()
+        if v.numel() != self.N:
+            raise ValueError(f"expected {self.N} values, got {v.numel()}")
+        return v
+
+    def apply_operator(self, u, out=None):
+        u = self._vec(u)
+        out = torch.empty_like(u) if out is None else out
+        check(self.lib.iga_apply_operator(self.h, _ptr(u), _ptr(out)), "iga_apply_operator")
+        return out
+
+    def precond_apply(self, b, out=None):
+        b = self._vec(b)
+        out = torch.empty_like(b) if out is None else out
+        check(self.lib.iga_precond_apply(self.h, _ptr(b), _ptr(out)), "iga_precond_apply")
+        return out
+
+    def solve(self, rhs, x0=None, tol=1e-8, max_iter=200, out=None, allow_no_convergence=True):
+        """Returns (x, info) with info = dict(iters, hist, relres_true, status)."""
+        rhs = self._vec(rhs)
+        if out is None:
+            out = torch.empty_like(rhs)
+        use_x0 = 0
+        if x0 is not None:
+            out.copy_(self._vec(x0))
+            use_x0 = 1
+        iters = ctypes.c_int()
+        rel = ctypes.c_double()
+        hist = np.zeros(max_iter + 1, dtype=np.float64)
+        st = self.lib.iga_solve(self.h, _ptr(rhs), _ptr(out), use_x0, float(tol), int(max_iter),
+                                ctypes.byref(iters), hist.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(rel))
+        allow = (STATUS_NO_CONVERGENCE,) if allow_no_convergence else ()
+        check(st, "iga_solve", allow)
+        k = iters.value
+        return out, dict(iters=k, hist=hist[:k + 1].copy(), relres_true=rel.value, status=st)
+
+    def solve_host(self, rhs_host, x_host, tol=1e-8, max_iter=200):
+        """Host-buffer solve (copies inside the call).  rhs_host/x_host: float64 arrays or
+        CPU tensors (pinned for asynchronous copies)."""
+        iters = ctypes.c_int()
+        rel = ctypes.c_double()
+        hist = np.zeros(max_iter + 1, dtype=np.float64)
+        rp = rhs_host.data_ptr() if isinstance(rhs_host, torch.Tensor) else rhs_host.ctypes.data
+        xp = x_host.data_ptr() if isinstance(x_host, torch.Tensor) else x_host.ctypes.data
+        st = self.lib.iga_solve_host(self.h, ctypes.c_void_p(rp), ctypes.c_void_p(xp), float(tol),
+                                     int(max_iter), ctypes.byref(iters),
+                                     hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rel))
+        check(st, "iga_solve_host", (STATUS_NO_CONVERGENCE,))
+        return dict(iters=iters.value, hist=hist[:iters.value + 1].copy(),
+                    relres_true=rel.value, status=st)

@@ -1,0 +1,203 @@
+// extern "C" boundary (include/iga_fd.h).  Every entry point converts internal
+// exceptions into an iga_status and records a message for iga_last_error().
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "context.h"
+
+struct iga_ctx {
+  iga::Ctx c;
+};
+
+namespace iga {
+static thread_local std::string g_last_error;
+thread_local long long g_launch_count = 0;
+void set_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace iga
+
+template <class F> static iga_status guarded(F &&f) {
+  try {
+    iga::g_last_error.clear();
+    return f();
+  } catch (const iga::Error &e) {
+    iga::set_error(e.msg);
+    return e.status;
+  } catch (const std::bad_alloc &) {
+    iga::set_error("host allocation failed");
+    return IGA_ERR_OOM;
+  } catch (const std::exception &e) {
+    iga::set_error(e.what());
+    return IGA_ERR_CUDA;
+  }
+}
+
+extern "C" {
+
+iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom, int precision,
+                     void *stream, iga_handle *out) {
+  return guarded([&]() -> iga_status {
+    if (!out || !geom) throw iga::Error{IGA_ERR_INVALID_ARG, "null pointer argument"};
+    *out = nullptr;
+    if (d != 2 && d != 3) throw iga::Error{IGA_ERR_INVALID_ARG, "d must be 2 or 3"};
+    if (p < 2 || p > iga::kMaxDeg) throw iga::Error{IGA_ERR_INVALID_ARG, "p must be in 2..6"};
+    if (n_elem < 3 || n_elem > 4096)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "n_elem must be in 3..4096"};
+    if (precision < IGA_PREC_FP64 || precision > IGA_PREC_NONE)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "bad precision"};
+    if (geom->kind < IGA_GEOM_IDENTITY || geom->kind > IGA_GEOM_REVOLVED_ANNULUS)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "bad geometry kind"};
+    if (geom->kind != IGA_GEOM_IDENTITY &&
+        !(geom->r_inner > 0.0 && geom->r_outer > geom->r_inner && std::isfinite(geom->r_outer)))
+      throw iga::Error{IGA_ERR_INVALID_ARG, "need 0 < r_inner < r_outer"};
+    if (geom->kind == IGA_GEOM_REVOLVED_ANNULUS && d != 3)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "the revolved ring is 3D"};
+    const double n = n_elem + p - 2;
+    if (std::pow(n, d) > 2.0e9) throw iga::Error{IGA_ERR_INVALID_ARG, "problem too large"};
+    iga_ctx *h = new iga_ctx();
+    try {
+      h->c.setup(d, n_elem, p, *geom, precision, (cudaStream_t)stream);
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return IGA_OK;
+  });
+}
+
+iga_status iga_dims(iga_handle h, int *n, long long *N) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    if (n) *n = h->c.n;
+    if (N) *N = h->c.N;
+    return IGA_OK;
+  });
+}
+
+iga_status iga_collocation_points(iga_handle h, double *xyz_host) {
+  return guarded([&]() -> iga_status {
+    if (!h || !xyz_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    h->c.collocation_points(xyz_host);
+    return IGA_OK;
+  });
+}
+
+iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host) {
+  return guarded([&]() -> iga_status {
+    if (!h || !out_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    if (dir < 0 || dir >= h->c.d) throw iga::Error{IGA_ERR_INVALID_ARG, "bad direction"};
+    const iga::Factor1D &f = *h->c.fac;
+    const int n = f.n, W = f.W;
+    auto dense = [&](int o, double sign) {
+      std::memset(out_host, 0, sizeof(double) * n * n);
+      for (int i = 0; i < n; ++i)
+        for (int t = 0; t < W; ++t)
+          out_host[(size_t)i * n + f.start[i] + t] = sign * f.band[o][(size_t)i * W + t];
+    };
+    switch (which) {
+      case IGA_FACTOR_TAU: std::memcpy(out_host, f.tau.data(), sizeof(double) * n); break;
+      case IGA_FACTOR_M: dense(0, 1.0); break;
+      case IGA_FACTOR_B1: dense(1, 1.0); break;
+      case IGA_FACTOR_K: dense(2, -1.0); break;
+      case IGA_FACTOR_LAMBDA: std::memcpy(out_host, f.lam.data(), sizeof(double) * n); break;
+      case IGA_FACTOR_U: std::memcpy(out_host, f.U.data(), sizeof(double) * n * n); break;
+      case IGA_FACTOR_VT: std::memcpy(out_host, f.Vt.data(), sizeof(double) * n * n); break;
+      default: throw iga::Error{IGA_ERR_INVALID_ARG, "bad factor selector"};
+    }
+    return IGA_OK;
+  });
+}
+
+iga_status iga_apply_operator(iga_handle h, const double *u_dev, double *Au_dev) {
+  return guarded([&]() -> iga_status {
+    if (!h || !u_dev || !Au_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    h->c.apply_operator<double>(iga::plain_ptr<const double>(u_dev), Au_dev, h->c.stream);
+    return IGA_OK;
+  });
+}
+
+iga_status iga_precond_apply(iga_handle h, const double *b_dev, double *s_dev) {
+  return guarded([&]() -> iga_status {
+    if (!h || !b_dev || !s_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    if (h->c.prec == IGA_PREC_NONE) {
+      IGA_CUDA_TRY(cudaMemcpyAsync(s_dev, b_dev, h->c.N * 8, cudaMemcpyDeviceToDevice,
+                                   h->c.stream));
+      return IGA_OK;
+    }
+    h->c.precond(iga::plain_ptr<const double>(b_dev), s_dev, h->c.stream);
+    return IGA_OK;
+  });
+}
+
+iga_status iga_solve(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0, double tol,
+                     int max_iter, int *iters, double *res_hist_host, double *true_relres) {
+  return guarded([&]() -> iga_status {
+    if (!h || !rhs_dev || !x_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    if (max_iter < 1 || max_iter > iga::kMaxIter)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "max_iter must be in 1..4096"};
+    if (!(tol >= 0.0)) throw iga::Error{IGA_ERR_INVALID_ARG, "tol must be >= 0"};
+    return h->c.solve(rhs_dev, x_dev, use_x0 ? 1 : 0, tol, max_iter, iters, res_hist_host,
+                      true_relres);
+  });
+}
+
+iga_status iga_solve_host(iga_handle h, const double *rhs_host, double *x_host, double tol,
+                          int max_iter, int *iters, double *res_hist_host, double *true_relres) {
+  return guarded([&]() -> iga_status {
+    if (!h || !rhs_host || !x_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    if (max_iter < 1 || max_iter > iga::kMaxIter)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "max_iter must be in 1..4096"};
+    iga::Ctx &c = h->c;
+    IGA_CUDA_TRY(cudaMemcpyAsync(c.r.ptr, rhs_host, c.N * 8, cudaMemcpyHostToDevice, c.stream));
+    // solve reads rhs from c.r into c.b before using c.r as scratch
+    const iga_status st = c.solve(c.r.ptr, c.x0.ptr, 0, tol, max_iter, iters, res_hist_host,
+                                  true_relres);
+    IGA_CUDA_TRY(cudaMemcpyAsync(x_host, c.x.ptr, c.N * 8, cudaMemcpyDeviceToHost, c.stream));
+    IGA_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return st;
+  });
+}
+
+iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    iga::Ctx &c = h->c;
+    if (!c.gexec) {
+      c.ensure_ws(1);
+      c.build_graph(c.ws_max_iter, 0);
+    }
+    if (fixed) *fixed = c.launches_fixed;
+    if (per_iteration) *per_iteration = c.launches_iter;
+    return IGA_OK;
+  });
+}
+
+iga_status iga_destroy(iga_handle h) {
+  return guarded([&]() -> iga_status {
+    delete h;
+    return IGA_OK;
+  });
+}
+
+const char *iga_status_string(iga_status s) {
+  switch (s) {
+    case IGA_OK: return "ok";
+    case IGA_ERR_INVALID_ARG: return "invalid argument";
+    case IGA_ERR_OOM: return "out of memory";
+    case IGA_ERR_CUDA: return "CUDA error";
+    case IGA_ERR_NOT_DIAGONALIZABLE: return "pencil not diagonalizable with real spectrum";
+    case IGA_ERR_NO_CONVERGENCE: return "no convergence within max_iter";
+    case IGA_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case IGA_ERR_NAN: return "non-finite value";
+    case IGA_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *iga_last_error(void) { return iga::g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Problem context behind an iga_handle: factors, geometry fields, operator plan,
+// FD buffers, Krylov workspace and the captured solve graph.
+#pragma once
+
+#include "iga_internal.h"
+
+namespace iga {
+
+void launch_field_maxabs(const double *fields, long long ldf, long long N, int nf,
+                         unsigned long long *out, cudaStream_t s);
+
+// tcgen05 FD (TF32 / BF16) -- defined in kernels_fd_tc.cu
+struct TcFd;
+TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s);
+void tc_fd_apply(TcFd &fd, IdxPtr<const double> in, IdxPtr<float> out, cudaStream_t s);
+void tc_fd_apply_f64out(TcFd &fd, IdxPtr<const double> in, double *out, cudaStream_t s);
+void destroy_tc_fd(TcFd *fd);
+struct TcFdDeleter {
+  void operator()(TcFd *p) const { destroy_tc_fd(p); }
+};
+
+struct OpPlan {
+  int nA = 0;
+  int ordA[3] = {0, 0, 0};
+  int nB = 0;
+  int B_in[6] = {0, 0, 0, 0, 0, 0};
+  int B_ord[6] = {0, 0, 0, 0, 0, 0};
+  int nterm = 0;
+  ContractTerm terms[kMaxFields];
+};
+
+struct Ctx {
+  int d = 0, n_elem = 0, p = 0, n = 0;
+  long long N = 0;
+  iga_geometry geom{};
+  int prec = IGA_PREC_FP64;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::shared_ptr<Factor1D> fac;
+  BandDev band{};
+
+  DevBuf<double> fields;
+  long long ldf = 0;
+  int active[kMaxFields] = {};
+  int nactive = 0;
+  double field_maxabs[kMaxFields] = {};
+  OpPlan plan;
+  DevBuf<double> op_scratch;  // (nA + nB) x N
+  DevBuf<double> fd_scratch;  // 2 x N
+  std::unique_ptr<TcFd, TcFdDeleter> tc;
+
+  DevBuf<double> b, x, x0, w, r;
+
+  // Krylov workspace
+  int ws_max_iter = 0;
+  DevBuf<double> V, Zd, H, cs, sn, g, y, hist, partials, scal;
+  DevBuf<float> Zf;
+  DevBuf<unsigned int> counter;
+  DevBuf<SolveState> st;
+  KrylovWs ws{};
+  SolveState *h_st = nullptr;  // pinned
+  double *h_hist = nullptr;    // pinned, max_iter + 2
+
+  // captured solve graph
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int g_max_iter = -1, g_use_x0 = -1;
+  int launches_fixed = 0, launches_iter = 0;  // kernels in the captured graph
+
+  ~Ctx();
+  void setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_);
+  template <class Tin> void apply_operator(IdxPtr<const Tin> in, double *out, cudaStream_t s);
+  void precond(IdxPtr<const double> in, double *out, cudaStream_t s);  // FP64 result
+  void ensure_ws(int max_iter);
+  void launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
+  void launch_solve_prologue(int use_x0, cudaGraphConditionalHandle cond, int has_cond,
+                             cudaStream_t s);
+  void launch_solve_epilogue(int use_x0, cudaStream_t s);
+  void build_graph(int max_iter, int use_x0);
+  iga_status solve(const double *rhs_dev, double *x_dev, int use_x0, double tol, int max_iter,
+                   int *iters, double *hist_out, double *relres);
+  void collocation_points(double *xyz) const;
+};
+
+}  // namespace iga

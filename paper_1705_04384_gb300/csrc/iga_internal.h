@@ -1,0 +1,205 @@
+// Internal declarations shared by the host setup, the CUDA kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/iga_fd.h"
+
+namespace iga {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxDeg = 6;
+constexpr int kMaxBand = kMaxDeg + 1;
+constexpr int kMaxIter = 4096;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+struct Error {
+  iga_status status;
+  std::string msg;
+};
+#define IGA_CUDA_TRY(expr)                                                          \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      throw ::iga::Error{IGA_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+// Every kernel launch of the library is followed by IGA_LAUNCH_CHECK(), which also
+// counts launches on the calling thread (used to report launches per solve).
+extern thread_local long long g_launch_count;
+#define IGA_LAUNCH_CHECK()                \
+  do {                                    \
+    ++::iga::g_launch_count;              \
+    IGA_CUDA_TRY(cudaGetLastError());     \
+  } while (0)
+
+// ---------------------------------------------------------------- device memory
+template <class T> struct DevBuf {
+  T *ptr = nullptr;
+  size_t count = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    count = 0;
+  }
+  void alloc(size_t n) {
+    if (n <= count && ptr) return;
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&ptr, n * sizeof(T));
+    if (e != cudaSuccess) {
+      ptr = nullptr;
+      (void)cudaGetLastError();
+      throw Error{IGA_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed"};
+    }
+    count = n;
+  }
+};
+
+// A pointer whose element offset is read on the device from an iteration counter:
+// base + (idx ? (*idx + off) : 0) * stride.  Lets one captured CUDA graph serve
+// every Arnoldi step (the step number lives in device memory).
+template <class T> struct IdxPtr {
+  T *base;
+  const int *idx;
+  int off;
+  long long stride;
+#ifdef __CUDACC__
+  __device__ __forceinline__ T *get() const {
+    return idx ? base + (long long)(*idx + off) * stride : base;
+  }
+#endif
+};
+template <class T> inline IdxPtr<T> plain_ptr(T *p) { return IdxPtr<T>{p, nullptr, 0, 0}; }
+
+// ---------------------------------------------------------------- 1D factors
+// Banded evaluation matrices of one direction: row i (collocation point tau_i)
+// has W = p+1 stored entries at interior columns start[i] .. start[i]+W-1;
+// band[o][i*W + t] = d^o B_{start[i]+t+1} / dxi^o (tau_i), zero where the
+// column is a dropped boundary function.
+struct Factor1D {
+  int n_elem = 0, p = 0, n = 0, W = 0;
+  std::vector<double> knots, tau;
+  std::vector<int> start;
+  std::vector<double> band[3];
+  std::vector<double> lam;      // n, ascending
+  std::vector<double> U, Vt;    // n x n row-major
+  // device copies
+  DevBuf<int> d_start;
+  DevBuf<double> d_band[3];
+  DevBuf<double> d_tau;
+  DevBuf<double> d_lam;
+  DevBuf<double> d_Vt, d_U;     // FP64 FD operands (row-major, ld = n)
+  DevBuf<float> d_Vt32, d_U32;  // TF32 FD operands (row-major, ld = kpad)
+  DevBuf<__nv_bfloat16> d_Vt16, d_U16;
+  int kpad = 0;                 // padded leading dimension for the TC operands
+  double cond_U = 0.0;
+};
+
+std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream);
+void build_basis_1d(Factor1D &f);  // host part (knots, tau, bands)
+
+// ---------------------------------------------------------------- geometry
+// Coefficient fields of L u_hat = sum_f q_f(x) * (derivative f of u_hat):
+// 2D: f = 11, 22, 12, 1, 2          3D: 11, 22, 33, 12, 13, 23, 1, 2, 3
+// q_aa = -G^{aa}, q_ab = -2 G^{ab} (a<b), q_c = -L_c.
+constexpr int kMaxFields = 9;
+struct FieldDesc {
+  int order[kMaxDim];  // derivative order per direction
+};
+int num_fields(int d);
+FieldDesc field_desc(int d, int f);
+
+// ---------------------------------------------------------------- launches
+struct BandDev {
+  const int *start;
+  const double *band0, *band1, *band2;
+  int n, W;
+};
+
+void launch_geometry_fields(int d, const iga_geometry &g, const double *tau1, const double *tau2,
+                            const double *tau3, int n1, int n2, int n3, double *fields,
+                            long long ldf, cudaStream_t s);
+
+// Banded mode product along direction dir (0-based) of an n1 x n2 x n3 tensor:
+// out[o] = B^{(order[o])}_dir applied along dir, for o < nout.
+template <class Tin>
+void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orders, int nout,
+                      int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s);
+
+// Final pass along direction 0 with contraction by the coefficient fields:
+// out = sum_t coef_t(x) * B^{(order_t)}_0 in[input_t].
+struct ContractTerm {
+  int input;  // index into ins
+  int order;  // derivative order along direction 0
+  const double *coef;
+};
+template <class Tin>
+void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *terms, int nterm,
+                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s);
+
+// FP64 mode-product GEMM with layout rotation:
+//   out[r + M*c] (+scale) = sum_k A[r*K + k] * Bt[c*K + k],  r < M, c < N(=K).
+// If lam != nullptr the result is divided by lam0[r % n0] + lam1[(r / n0) % n1] + lamc[c]
+// (the FD diagonal, eq. FD2D / FD3D).
+struct FdScale {
+  const double *lam_r0, *lam_r1, *lam_c;  // lam_r1 may be null (2D)
+  int n0;
+};
+template <class Tout>
+void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out, int M, int N,
+                      int K, const FdScale *scale, cudaStream_t s);
+
+// ---------------------------------------------------------------- Krylov kernels
+struct SolveState {
+  int k;            // completed Arnoldi steps
+  int done;         // loop finished
+  int flag;         // 0 running, 1 converged, 2 max_iter, 3 breakdown, 4 nan
+  int max_iter;
+  double tol;
+  double bnorm, beta;
+  double relres_true;
+};
+
+struct KrylovWs {
+  double *V;  long long ldv;     // (max_iter+1) x ldv
+  void *Z;    long long ldz;     // max_iter x ldz, FP64 or FP32
+  int z_fp32;
+  double *H;                     // (max_iter+1) x max_iter col-major, ld = max_iter+1
+  double *cs, *sn, *g, *y, *hist;
+  double *partials;              // nblk x (max_iter+2)
+  unsigned int *counter;         // last-block counters (4)
+  double *scal;                  // scalar scratch (8)
+  SolveState *st;
+  int nblk;
+  long long N;
+  int max_iter;
+};
+
+int reduce_blocks(long long N);
+void launch_dot(const double *x, const double *y, long long N, const KrylovWs &ws, double *out,
+                cudaStream_t s);
+void launch_init_solve(const KrylovWs &ws, const double *r, cudaGraphConditionalHandle cond,
+                       int has_cond, cudaStream_t s);
+void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s);
+void launch_givens(const KrylovWs &ws, cudaGraphConditionalHandle cond, int has_cond,
+                   cudaStream_t s);
+void launch_finish(const KrylovWs &ws, const double *x0, int use_x0, double *x, cudaStream_t s);
+void launch_residual_norm(const KrylovWs &ws, const double *b, const double *Ax, double *r,
+                          cudaStream_t s);
+void launch_axpby(const double *x, const double *y, double a, double b, double *out, long long N,
+                  cudaStream_t s);
+void launch_convert_f32(const float *x, double *out, long long N, cudaStream_t s);
+
+}  // namespace iga

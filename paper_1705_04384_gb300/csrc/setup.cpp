@@ -1,0 +1,369 @@
+// Host setup: open knot vectors, B-spline derivatives on the non-zero span,
+// Greville collocation points, banded collocation factors, and the FD eigen-
+// factors of each direction (computed with cuSOLVER on the device, FP64).
+//
+// Paper: Sec. 2.1 (open knots, basis), Sec. 2.2 eq. (greville) and
+// eq. (univariatecolloc) (M = B(tau), K = -B''(tau)), Sec. 4 eq. (eigendecomposition)
+// and V := (M U)^{-T}; Remark 1 (real spectrum, well-conditioned U) is checked.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <numeric>
+
+#include "iga_internal.h"
+
+namespace iga {
+
+// ------------------------------------------------------------------ basis (host)
+// Span index mu (0-based knot index) with t[mu] <= x < t[mu+1], p <= mu <= m-1;
+// the right end x = t[m] belongs to the last span.
+static int find_span(const std::vector<double> &t, int p, int m, double x) {
+  if (x >= t[m]) return m - 1;
+  int lo = p, hi = m;  // invariant: t[lo] <= x < t[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (x < t[mid]) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+// Values and first/second derivatives of the p+1 functions B_{mu-p..mu} that are
+// non-zero on span mu.  tab[q][r] holds B_{mu-q+r, q}(x) for degrees q <= p built
+// by the two-term recursion; derivatives of degree-p functions follow from the
+// derivative identity D B_{i,q} = q (B_{i,q-1}/(t_{i+q}-t_i) - B_{i+1,q-1}/(t_{i+q+1}-t_{i+1})),
+// applied once (D) or twice (D^2, through degree q-1 derivatives).
+static void span_basis(const std::vector<double> &t, int p, int mu, double x,
+                       double out[3][kMaxBand]) {
+  double tab[kMaxDeg + 1][kMaxBand] = {};
+  tab[0][0] = 1.0;
+  for (int q = 1; q <= p; ++q) {
+    for (int r = 0; r <= q; ++r) {
+      const int i = mu - q + r;
+      double v = 0.0;
+      if (r >= 1) {  // B_{i,q-1} = tab[q-1][r-1]
+        const double den = t[i + q] - t[i];
+        if (den > 0.0) v += (x - t[i]) / den * tab[q - 1][r - 1];
+      }
+      if (r <= q - 1) {  // B_{i+1,q-1} = tab[q-1][r]
+        const double den = t[i + q + 1] - t[i + 1];
+        if (den > 0.0) v += (t[i + q + 1] - x) / den * tab[q - 1][r];
+      }
+      tab[q][r] = v;
+    }
+  }
+  // D of degree-q functions from degree q-1 values: d1[q][r] for B_{mu-q+r,q}.
+  auto deriv_from = [&](const double *low, int q, double *dst) {
+    for (int r = 0; r <= q; ++r) {
+      const int i = mu - q + r;
+      double v = 0.0;
+      if (r >= 1) {
+        const double den = t[i + q] - t[i];
+        if (den > 0.0) v += q * low[r - 1] / den;
+      }
+      if (r <= q - 1) {
+        const double den = t[i + q + 1] - t[i + 1];
+        if (den > 0.0) v -= q * low[r] / den;
+      }
+      dst[r] = v;
+    }
+  };
+  double d1p[kMaxBand] = {}, d1pm1[kMaxBand] = {}, d2p[kMaxBand] = {};
+  deriv_from(tab[p - 1], p, d1p);
+  if (p >= 2) {
+    deriv_from(tab[p - 2], p - 1, d1pm1);
+    deriv_from(d1pm1, p, d2p);
+  }
+  for (int r = 0; r <= p; ++r) {
+    out[0][r] = tab[p][r];
+    out[1][r] = d1p[r];
+    out[2][r] = d2p[r];
+  }
+}
+
+void build_basis_1d(Factor1D &f) {
+  const int p = f.p, ne = f.n_elem;
+  const int m = ne + p;
+  f.n = m - 2;
+  f.W = p + 1;
+  f.knots.assign(m + p + 1, 0.0);
+  for (int k = 0; k < ne - 1; ++k) f.knots[p + 1 + k] = double(k + 1) / double(ne);
+  for (int k = 0; k <= p; ++k) f.knots[m + k] = 1.0;
+  // eq. (greville): tau_i = (1/p) sum_{j=1..p} xi_{i+j+1}, 1-based xi = t[.-1]
+  f.tau.resize(f.n);
+  for (int i = 1; i <= f.n; ++i) {
+    double s = 0.0;
+    for (int j = 1; j <= p; ++j) s += f.knots[i + j];
+    f.tau[i - 1] = s / p;
+  }
+  const int n = f.n, W = f.W;
+  f.start.assign(n, 0);
+  for (int o = 0; o < 3; ++o) f.band[o].assign((size_t)n * W, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double x = f.tau[i];
+    const int mu = find_span(f.knots, p, m, x);
+    double vals[3][kMaxBand];
+    span_basis(f.knots, p, mu, x, vals);
+    // basis index b = mu - p + r; interior column j = b - 1 in [0, n)
+    int st = mu - p - 1;
+    st = std::max(0, std::min(st, n - W));
+    f.start[i] = st;
+    for (int r = 0; r <= p; ++r) {
+      const int j = mu - p + r - 1;
+      if (j < 0 || j >= n) continue;  // dropped boundary function (eq. space)
+      const int tpos = j - st;
+      for (int o = 0; o < 3; ++o) f.band[o][(size_t)i * W + tpos] = vals[o][r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ eigen-factors
+#define CUSOLVER_TRY(expr)                                                          \
+  do {                                                                              \
+    cusolverStatus_t s_ = (expr);                                                   \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                              \
+      throw Error{IGA_ERR_CUDA, std::string(#expr) + " failed with status " + std::to_string((int)s_)}; \
+  } while (0)
+
+namespace {
+struct SolverHandle {
+  cusolverDnHandle_t h = nullptr;
+  cusolverDnParams_t prm = nullptr;
+  ~SolverHandle() {
+    if (prm) cusolverDnDestroyParams(prm);
+    if (h) cusolverDnDestroy(h);
+  }
+};
+
+// largest singular value of a dense row-major n x n matrix by power iteration on A^T A
+double norm2_est(const std::vector<double> &A, int n) {
+  std::vector<double> x(n, 1.0 / std::sqrt((double)n)), y(n), z(n);
+  double s = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    for (int i = 0; i < n; ++i) {
+      double a = 0.0;
+      for (int j = 0; j < n; ++j) a += A[(size_t)i * n + j] * x[j];
+      y[i] = a;
+    }
+    std::fill(z.begin(), z.end(), 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) z[j] += A[(size_t)i * n + j] * y[i];
+    double nz = 0.0;
+    for (double v : z) nz += v * v;
+    nz = std::sqrt(nz);
+    if (nz == 0.0) return 0.0;
+    s = std::sqrt(nz);
+    for (int j = 0; j < n; ++j) x[j] = z[j] / nz;
+  }
+  return s;
+}
+}  // namespace
+
+static void eigen_factors(Factor1D &f, cudaStream_t stream) {
+  const int n = f.n, W = f.W;
+  // dense column-major M and K
+  std::vector<double> Mc((size_t)n * n, 0.0), Kc((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int t = 0; t < W; ++t) {
+      const int j = f.start[i] + t;
+      Mc[i + (size_t)n * j] = f.band[0][(size_t)i * W + t];
+      Kc[i + (size_t)n * j] = -f.band[2][(size_t)i * W + t];
+    }
+  SolverHandle sh;
+  CUSOLVER_TRY(cusolverDnCreate(&sh.h));
+  CUSOLVER_TRY(cusolverDnSetStream(sh.h, stream));
+  CUSOLVER_TRY(cusolverDnCreateParams(&sh.prm));
+  DevBuf<double> dM, dA, dVR, dW, dX;
+  DevBuf<int64_t> dipiv;
+  DevBuf<int> dinfo;
+  dM.alloc((size_t)n * n);
+  dA.alloc((size_t)n * n);
+  dVR.alloc((size_t)n * n);
+  dW.alloc(2 * (size_t)n);
+  dX.alloc((size_t)n * n);
+  dipiv.alloc(n);
+  dinfo.alloc(1);
+  IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, Mc.data(), Mc.size() * 8, cudaMemcpyHostToDevice, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(dA.ptr, Kc.data(), Kc.size() * 8, cudaMemcpyHostToDevice, stream));
+  auto check_info = [&](const char *what) {
+    int info = 0;
+    IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (info != 0)
+      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
+  };
+  size_t dws = 0, hws = 0;
+  // A = M^{-1} K  (eq. eigendecomposition works with M^{-1} K)
+  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
+                                           &dws, &hws));
+  {
+    DevBuf<char> dbuf;
+    dbuf.alloc(std::max<size_t>(dws, 1));
+    std::vector<char> hbuf(std::max<size_t>(hws, 1));
+    CUSOLVER_TRY(cusolverDnXgetrf(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
+                                  dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
+    check_info("getrf(M)");
+  }
+  CUSOLVER_TRY(cusolverDnXgetrs(sh.h, sh.prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
+                                CUDA_R_64F, dA.ptr, n, dinfo.ptr));
+  check_info("getrs(M, K)");
+  // eigenvalues and right eigenvectors of A
+  CUSOLVER_TRY(cusolverDnXgeev_bufferSize(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR,
+                                          CUSOLVER_EIG_MODE_VECTOR, n, CUDA_R_64F, dA.ptr, n,
+                                          CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr, 1, CUDA_R_64F,
+                                          dVR.ptr, n, CUDA_R_64F, &dws, &hws));
+  {
+    DevBuf<char> dbuf;
+    dbuf.alloc(std::max<size_t>(dws, 1));
+    std::vector<char> hbuf(std::max<size_t>(hws, 1));
+    CUSOLVER_TRY(cusolverDnXgeev(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
+                                 n, CUDA_R_64F, dA.ptr, n, CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr,
+                                 1, CUDA_R_64F, dVR.ptr, n, CUDA_R_64F, dbuf.ptr, dws, hbuf.data(),
+                                 hws, dinfo.ptr));
+    check_info("geev(M^{-1}K)");
+  }
+  std::vector<double> Wc(2 * (size_t)n), VR((size_t)n * n);
+  IGA_CUDA_TRY(cudaMemcpyAsync(Wc.data(), dW.ptr, Wc.size() * 8, cudaMemcpyDeviceToHost, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(VR.data(), dVR.ptr, VR.size() * 8, cudaMemcpyDeviceToHost, stream));
+  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  // Remark 1: the eigenvalues must be real
+  for (int j = 0; j < n; ++j) {
+    const double re = Wc[2 * j], im = Wc[2 * j + 1];
+    const double mag = std::sqrt(re * re + im * im);
+    if (!std::isfinite(mag) || std::fabs(im) > 1e-10 * std::max(mag, 1e-300))
+      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, "complex eigenvalue of M^{-1}K (Remark 1)"};
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Wc[2 * a] < Wc[2 * b]; });
+  f.lam.resize(n);
+  f.U.assign((size_t)n * n, 0.0);
+  for (int jj = 0; jj < n; ++jj) {
+    const int j = order[jj];
+    f.lam[jj] = Wc[2 * j];
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) nrm += VR[i + (size_t)n * j] * VR[i + (size_t)n * j];
+    nrm = std::sqrt(nrm);
+    for (int i = 0; i < n; ++i) f.U[(size_t)i * n + jj] = VR[i + (size_t)n * j] / nrm;
+  }
+  // MU (banded M times dense U), then V^T = (M U)^{-1}
+  std::vector<double> MUc((size_t)n * n, 0.0), Ic((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int t = 0; t < W; ++t) {
+      const double mv = f.band[0][(size_t)i * W + t];
+      if (mv == 0.0) continue;
+      const int k = f.start[i] + t;
+      for (int j = 0; j < n; ++j) MUc[i + (size_t)n * j] += mv * f.U[(size_t)k * n + j];
+    }
+  for (int i = 0; i < n; ++i) Ic[i + (size_t)n * i] = 1.0;
+  IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, MUc.data(), MUc.size() * 8, cudaMemcpyHostToDevice, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(dX.ptr, Ic.data(), Ic.size() * 8, cudaMemcpyHostToDevice, stream));
+  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
+                                           &dws, &hws));
+  {
+    DevBuf<char> dbuf;
+    dbuf.alloc(std::max<size_t>(dws, 1));
+    std::vector<char> hbuf(std::max<size_t>(hws, 1));
+    CUSOLVER_TRY(cusolverDnXgetrf(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
+                                  dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
+    check_info("getrf(MU)");
+  }
+  CUSOLVER_TRY(cusolverDnXgetrs(sh.h, sh.prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
+                                CUDA_R_64F, dX.ptr, n, dinfo.ptr));
+  check_info("getrs(MU, I)");
+  std::vector<double> Xc((size_t)n * n);
+  IGA_CUDA_TRY(cudaMemcpyAsync(Xc.data(), dX.ptr, Xc.size() * 8, cudaMemcpyDeviceToHost, stream));
+  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  f.Vt.resize((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) f.Vt[(size_t)i * n + j] = Xc[i + (size_t)n * j];
+  // Remark 1: cond_2(U) = ||U|| ||U^{-1}||, with U^{-1} = V^T M
+  std::vector<double> Uinv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int r = 0; r < n; ++r) {
+      const double a = f.Vt[(size_t)i * n + r];
+      for (int t = 0; t < W; ++t)
+        Uinv[(size_t)i * n + f.start[r] + t] += a * f.band[0][(size_t)r * W + t];
+    }
+  f.cond_U = norm2_est(f.U, n) * norm2_est(Uinv, n);
+  if (!(f.cond_U <= 1e3))
+    throw Error{IGA_ERR_NOT_DIAGONALIZABLE,
+                "ill-conditioned eigenvector matrix, cond(U) ~ " + std::to_string(f.cond_U)};
+}
+
+// ------------------------------------------------------------------ device upload
+template <class T> static void upload(DevBuf<T> &d, const std::vector<T> &h, cudaStream_t s) {
+  d.alloc(h.size());
+  IGA_CUDA_TRY(cudaMemcpyAsync(d.ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+static void upload_factor(Factor1D &f, cudaStream_t s) {
+  upload(f.d_start, f.start, s);
+  for (int o = 0; o < 3; ++o) upload(f.d_band[o], f.band[o], s);
+  upload(f.d_tau, f.tau, s);
+  upload(f.d_lam, f.lam, s);
+  upload(f.d_Vt, f.Vt, s);
+  upload(f.d_U, f.U, s);
+  // tensor-core operands: row-major, leading dimension padded to a multiple of 8
+  const int n = f.n;
+  f.kpad = (n + 7) / 8 * 8;
+  std::vector<float> vt32((size_t)n * f.kpad, 0.f), u32((size_t)n * f.kpad, 0.f);
+  std::vector<__nv_bfloat16> vt16((size_t)n * f.kpad, __float2bfloat16(0.f)),
+      u16((size_t)n * f.kpad, __float2bfloat16(0.f));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      vt32[(size_t)i * f.kpad + j] = (float)f.Vt[(size_t)i * n + j];
+      u32[(size_t)i * f.kpad + j] = (float)f.U[(size_t)i * n + j];
+      vt16[(size_t)i * f.kpad + j] = __float2bfloat16((float)f.Vt[(size_t)i * n + j]);
+      u16[(size_t)i * f.kpad + j] = __float2bfloat16((float)f.U[(size_t)i * n + j]);
+    }
+  upload(f.d_Vt32, vt32, s);
+  upload(f.d_U32, u32, s);
+  upload(f.d_Vt16, vt16, s);
+  upload(f.d_U16, u16, s);
+  IGA_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------ factor cache
+std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, std::weak_ptr<Factor1D>> cache;
+  int dev = 0;
+  IGA_CUDA_TRY(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, n_elem, p);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    if (auto sp = it->second.lock()) return sp;
+  }
+  auto f = std::make_shared<Factor1D>();
+  f->n_elem = n_elem;
+  f->p = p;
+  build_basis_1d(*f);
+  eigen_factors(*f, stream);
+  upload_factor(*f, stream);
+  cache[key] = f;
+  return f;
+}
+
+// ------------------------------------------------------------------ fields
+int num_fields(int d) { return d == 2 ? 5 : 9; }
+
+FieldDesc field_desc(int d, int f) {
+  FieldDesc fd{{0, 0, 0}};
+  if (d == 2) {
+    static const int o[5][2] = {{2, 0}, {0, 2}, {1, 1}, {1, 0}, {0, 1}};
+    fd.order[0] = o[f][0];
+    fd.order[1] = o[f][1];
+  } else {
+    static const int o[9][3] = {{2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1},
+                                {0, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int l = 0; l < 3; ++l) fd.order[l] = o[f][l];
+  }
+  return fd;
+}
+
+}  // namespace iga

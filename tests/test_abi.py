@@ -1,0 +1,71 @@
+"""The C ABI library loads and exports every function include/iga_fd.h declares;
+argument validation runs on the host (no GPU needed for these calls)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def _declared_functions():
+    names = []
+    for fname in sorted(os.listdir(HEADER_DIR)):
+        if not fname.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, fname)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_]\w*\s*\**\s*(iga_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_04384_gb300 import _lib
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_1705_04384_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("iga_setup", "iga_precond_apply", "iga_solve", "iga_apply_operator",
+                     "iga_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_prototypes_cover_header(lib):
+    from paper_1705_04384_gb300 import _lib
+    assert set(_declared_functions()) <= set(_lib.PROTOTYPES)
+
+
+def test_status_strings(lib):
+    for s in range(9):
+        assert lib.iga_status_string(s)
+    assert lib.iga_status_string(0) == b"ok"
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    from paper_1705_04384_gb300._lib import Geometry
+    g = Geometry(1, 1.0, 2.0)
+    h = ctypes.c_void_p()
+    assert lib.iga_setup(4, 32, 3, ctypes.byref(g), 0, None, ctypes.byref(h)) == 1
+    assert b"d must be" in lib.iga_last_error()
+    assert lib.iga_setup(2, 32, 9, ctypes.byref(g), 0, None, ctypes.byref(h)) == 1
+    assert lib.iga_setup(2, 2, 3, ctypes.byref(g), 0, None, ctypes.byref(h)) == 1
+    bad = Geometry(1, 2.0, 1.0)
+    assert lib.iga_setup(2, 32, 3, ctypes.byref(bad), 0, None, ctypes.byref(h)) == 1
+    assert lib.iga_setup(2, 32, 3, ctypes.byref(g), 7, None, ctypes.byref(h)) == 1
+    assert lib.iga_setup(2, 32, 3, None, 0, None, ctypes.byref(h)) == 1
+    assert lib.iga_dims(None, None, None) == 1
+    assert lib.iga_solve(None, None, None, 0, 1e-8, 10, None, None, None) == 1
+    assert lib.iga_destroy(None) == 0

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (derived in DESIGN.md, "Tolerances"):
+* 1D factors, points: exact up to a few ulps (same formulas, different code);
+* operator: max |A_gpu u - A_oracle u| <= 1e-13 max |A_oracle u| (FP64 sums of <= 9
+  terms of W products; reordering error ~ 1e-15, margin for cancellation);
+* FD solve: ||s_gpu - s_oracle|| <= 1e-11 ||s_oracle|| (cond(U) <= 15 amplifies the
+  FP64 rounding of 2d mode products);
+* GMRES iterate at fixed k: relative difference <= 1e-10;
+* GMRES to tol 1e-8: iteration counts within +-1, true residual <= 1e-8.
+"""
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from tests.oracle_ref import ref
+
+pytestmark = pytest.mark.gpu
+
+CASES_OP = [
+    (2, 40, 3, "annulus"), (2, 23, 2, "annulus"), (2, 17, 5, "annulus"), (2, 30, 6, "annulus"),
+    (2, 19, 4, "identity"), (3, 8, 4, "annulus"), (3, 9, 3, "annulus"), (3, 6, 3, "revolved"),
+    (3, 7, 5, "identity"), (3, 11, 2, "annulus"), (3, 5, 6, "revolved"),
+]
+
+
+def _problem(d, ne, p, geometry="annulus", precision="fp64", r0=1.0, r1=2.0):
+    from paper_1705_04384_gb300.api import Problem
+    return Problem(d, ne, p, geometry=geometry, r_inner=r0, r_outer=r1, precision=precision)
+
+
+def _rand(N, seed):
+    return np.random.Generator(np.random.PCG64(seed)).standard_normal(N)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6])
+def test_factors_match_oracle(p):
+    R = ref(2, 21, p, assemble=False)
+    with _problem(2, 21, p) as P:
+        s = R.spaces[0]
+        assert np.max(np.abs(P.factor("tau") - s.tau)) <= 2e-16
+        assert np.max(np.abs(P.factor("M") - s.M)) <= 1e-14
+        assert np.max(np.abs(P.factor("B1") - s.B[1])) <= 1e-12
+        assert np.max(np.abs(P.factor("K") - s.K)) <= 1e-10 * np.max(np.abs(s.K))
+        lam = P.factor("lambda")
+        assert np.max(np.abs(lam - R.fd.lam[0]) / np.abs(R.fd.lam[0])) <= 1e-9
+        U, Uo = P.factor("U"), R.fd.U[0]
+        sign = np.sign(np.sum(U * Uo, axis=0))
+        assert np.max(np.abs(U * sign - Uo)) <= 1e-8
+        Vt = P.factor("Vt")
+        assert np.max(np.abs(Vt * sign[:, None] - R.fd.V[0].T)) <= 1e-8 * np.max(np.abs(Vt))
+
+
+@pytest.mark.parametrize("d,ne,p,geo", [(2, 12, 3, "annulus"), (3, 5, 4, "annulus"),
+                                         (3, 4, 3, "revolved"), (2, 9, 2, "identity")])
+def test_collocation_points_match_oracle(d, ne, p, geo):
+    R = ref(d, ne, p, geo, assemble=False)
+    with _problem(d, ne, p, geo) as P:
+        assert np.max(np.abs(P.collocation_points() - R.points)) <= 1e-14
+
+
+@pytest.mark.parametrize("d,ne,p,geo", CASES_OP)
+def test_operator_matches_oracle(d, ne, p, geo):
+    R = ref(d, ne, p, geo)
+    with _problem(d, ne, p, geo) as P:
+        for seed in (0, 1):
+            u = _rand(R.N, seed)
+            got = P.apply_operator(torch.from_numpy(u).cuda()).cpu().numpy()
+            want = R.A @ u
+            assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+def test_operator_ragged_annulus_radii():
+    R = ref(2, 37, 4, "annulus", 0.5, 1.5)
+    with _problem(2, 37, 4, "annulus", r0=0.5, r1=1.5) as P:
+        u = _rand(R.N, 3)
+        got = P.apply_operator(torch.from_numpy(u).cuda()).cpu().numpy()
+        want = R.A @ u
+        assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("d,ne,p", [(2, 40, 3), (2, 95, 5), (2, 150, 2), (3, 9, 3), (3, 14, 6),
+                                     (3, 20, 4)])
+def test_fd_matches_oracle(d, ne, p):
+    R = ref(d, ne, p, assemble=False)
+    with _problem(d, ne, p) as P:
+        b = _rand(R.N, 7)
+        got = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+        want = R.fd(b)
+        assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
+        assert np.linalg.norm(R.P_apply(got) - b) <= 1e-11 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("d,ne,p,k", [(2, 24, 3, 1), (2, 24, 3, 4), (2, 24, 3, 12),
+                                       (3, 8, 3, 6), (2, 60, 4, 9), (3, 13, 5, 5)])
+def test_gmres_iterate_at_fixed_k_matches(d, ne, p, k):
+    R = ref(d, ne, p)
+    b = R.manufactured_rhs(1e-3, 0)
+    o = R.gmres(b, tol=0.0, max_iter=k)
+    with _problem(d, ne, p) as P:
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=0.0, max_iter=k)
+        x = x.cpu().numpy()
+    assert info["iters"] == k == o["iters"]
+    assert np.linalg.norm(x - o["x"]) <= 1e-10 * np.linalg.norm(o["x"])
+    assert np.max(np.abs(info["hist"] - o["hist"]) / o["hist"]) <= 1e-8
+
+
+@pytest.mark.parametrize("d,ne,p,geo", [(2, 32, 3, "annulus"), (2, 64, 5, "annulus"),
+                                         (3, 10, 3, "annulus"), (3, 8, 4, "revolved")])
+def test_gmres_to_tolerance_matches(d, ne, p, geo):
+    R = ref(d, ne, p, geo)
+    b = R.manufactured_rhs(0.0) if geo == "annulus" else _rand(R.N, 11)
+    o = R.gmres(b, tol=1e-8, max_iter=300)
+    with _problem(d, ne, p, geo) as P:
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
+        x = x.cpu().numpy()
+    assert abs(info["iters"] - o["iters"]) <= 1
+    relres = np.linalg.norm(b - R.A @ x) / np.linalg.norm(b)
+    assert relres <= 1.05e-8
+    assert abs(relres - info["relres_true"]) <= 1e-12
+    assert np.linalg.norm(x - o["x"]) <= 1e-6 * np.linalg.norm(o["x"])
+    assert np.all(np.diff(info["hist"]) <= 1e-15)
+
+
+def test_unpreconditioned_matches_oracle():
+    R = ref(2, 32, 3)
+    b = R.manufactured_rhs(0.0)
+    o = R.gmres(b, M=None, tol=1e-8, max_iter=1000)
+    with _problem(2, 32, 3, precision="none") as P:
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=1000)
+        x = x.cpu().numpy()
+    assert abs(info["iters"] - o["iters"]) <= 2
+    assert np.linalg.norm(b - R.A @ x) / np.linalg.norm(b) <= 1.05e-8
+    # FD preconditioning cuts the count (Table 2 behaviour)
+    with _problem(2, 32, 3) as P:
+        _, info_fd = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
+    assert info_fd["iters"] < info["iters"] / 3
+
+
+def test_initial_guess_paths():
+    R = ref(2, 30, 3)
+    b = R.manufactured_rhs(0.0)
+    o = R.gmres(b, tol=1e-12, max_iter=300)
+    with _problem(2, 30, 3) as P:
+        bt = torch.from_numpy(b).cuda()
+        x, info = P.solve(bt, x0=torch.from_numpy(o["x"]).cuda(), tol=1e-8, max_iter=50)
+        assert info["iters"] == 0
+        assert np.array_equal(x.cpu().numpy(), o["x"])
+        x0 = _rand(R.N, 4)
+        x, info = P.solve(bt, x0=torch.from_numpy(x0).cuda(), tol=1e-8, max_iter=200)
+        x = x.cpu().numpy()
+        assert np.linalg.norm(b - R.A @ x) / np.linalg.norm(b) <= 1.05e-8
+
+
+def test_zero_and_nan_rhs():
+    from paper_1705_04384_gb300 import IgaError
+    with _problem(2, 12, 3) as P:
+        z = torch.zeros(P.N, dtype=torch.float64, device="cuda")
+        x, info = P.solve(z, tol=1e-8, max_iter=20)
+        assert info["iters"] == 0 and torch.count_nonzero(x).item() == 0
+        bad = torch.ones(P.N, dtype=torch.float64, device="cuda")
+        bad[5] = float("nan")
+        with pytest.raises(IgaError) as ei:
+            P.solve(bad, tol=1e-8, max_iter=20)
+        assert ei.value.status == 7
+        # the handle stays usable
+        x, info = P.solve(torch.ones_like(bad), tol=1e-8, max_iter=60)
+        assert info["relres_true"] <= 1.05e-8
+
+
+def test_max_iter_reports_no_convergence():
+    from paper_1705_04384_gb300 import IgaError
+    with _problem(2, 40, 3, precision="none") as P:
+        b = torch.ones(P.N, dtype=torch.float64, device="cuda")
+        with pytest.raises(IgaError) as ei:
+            P.solve(b, tol=1e-8, max_iter=5, allow_no_convergence=False)
+        assert ei.value.status == 5
+
+
+def test_graph_and_eager_bitwise_equal_and_deterministic():
+    R = ref(3, 9, 4, assemble=False)
+    b = torch.from_numpy(_rand(R.N, 21)).cuda()
+    with _problem(3, 9, 4) as P:
+        x1, i1 = P.solve(b, tol=1e-9, max_iter=100)
+        x2, i2 = P.solve(b, tol=1e-9, max_iter=100)
+        os.environ["IGA_EAGER"] = "1"
+        try:
+            x3, i3 = P.solve(b, tol=1e-9, max_iter=100)
+        finally:
+            del os.environ["IGA_EAGER"]
+    assert torch.equal(x1, x2) and torch.equal(x1, x3)
+    assert i1["iters"] == i2["iters"] == i3["iters"]
+    assert np.array_equal(i1["hist"], i3["hist"])
+
+
+def test_host_buffer_solve_matches_device_solve():
+    R = ref(2, 33, 4, assemble=False)
+    b = _rand(R.N, 5)
+    with _problem(2, 33, 4) as P:
+        xd, infod = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=100)
+        xh = np.zeros(R.N)
+        infoh = P.solve_host(np.ascontiguousarray(b), xh, tol=1e-8, max_iter=100)
+    assert infoh["iters"] == infod["iters"]
+    assert np.array_equal(xh, xd.cpu().numpy())
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+def test_full_size_3d_ne64(p):
+    """The bench workload (3D extruded annulus, 64 elements, manufactured f with the
+    seeded 1e-3 perturbation): sampled oracle rows of A_C, the full FD against the
+    oracle's FD, and the residual of the converged solution on sampled rows."""
+    import workload as W
+    R = ref(3, 64, p, assemble=False)
+    b = W.config_rhs("3d_annulus_ne64", R.points, p_index=p - 3)
+    rng = np.random.default_rng(p)
+    idx = np.unique(np.concatenate([[0, R.N - 1, R.N // 2],
+                                    rng.integers(0, R.N, 24)]))
+    rows = R.rows(idx)
+    with _problem(3, 64, p) as P:
+        u = _rand(R.N, 8)
+        Au = P.apply_operator(torch.from_numpy(u).cuda()).cpu().numpy()
+        want = rows @ u
+        assert np.max(np.abs(Au[idx] - want)) <= 1e-13 * np.max(np.abs(want))
+        s = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+        s_ref = R.fd(b)
+        assert np.linalg.norm(s - s_ref) <= 1e-11 * np.linalg.norm(s_ref)
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=200)
+        x = x.cpu().numpy()
+    assert info["status"] == 0 and info["relres_true"] <= 1e-8 * 1.05
+    assert info["iters"] <= 60
+    r = b[idx] - rows @ x
+    assert np.max(np.abs(r)) <= 1.05e-8 * np.linalg.norm(b)

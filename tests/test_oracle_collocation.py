@@ -177,3 +177,13 @@ def test_collocation_convergence_order(p):
         errs.append(np.max(np.abs(uh - W.manufactured_u(pts))))
     orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert orders[-1] >= p - 1 - 0.2, (errs, orders)
+
+
+@pytest.mark.parametrize("kind,d", [("annulus", 2), ("annulus", 3), ("revolved", 3)])
+def test_collocation_rows_match_assembly(kind, d):
+    fmap = Geo.make_map(kind, d)
+    spaces = [C.Space1D(4, 3) for _ in range(d)]
+    A = C.assemble_collocation(spaces, fmap).toarray()
+    rows = [0, 5, A.shape[0] - 1, A.shape[0] // 2]
+    R = C.collocation_rows(spaces, fmap, rows)
+    assert np.max(np.abs(R - A[rows])) < 1e-13 * np.max(np.abs(A))
