@@ -10,6 +10,13 @@
 
 Normalization reading (the paper leaves it free): columns of U have unit 2-norm and
 are sorted by ascending eigenvalue.  The FD result does not depend on either choice.
+
+Reflection reading (Remark 1's double "outlier" eigenvalue): on uniform knots the
+factors commute with the flip R (i -> n-1-i): R M R = M, R K R = K.  The pencil then
+splits exactly into an even part (v = R v) and an odd part (v = -R v), each solved
+by LAPACK on its own; the two outlier eigenvectors fall one in each part, so U stays
+well conditioned even though the two eigenvalues agree to rounding.  Pencils without
+this symmetry use one generalized eigensolve of the whole pencil.
 """
 
 import numpy as np
@@ -20,16 +27,50 @@ class NotDiagonalizable(RuntimeError):
     pass
 
 
-def eig_factors(K, M, imag_tol=1e-10, cond_max=1e3):
-    """Return (lam, U, V) with K U = M U diag(lam), unit-norm ascending columns and
-    V = (M U)^{-T}.  Raises NotDiagonalizable when Remark 1's assumptions fail."""
+def reflection_basis(n):
+    """Orthonormal E (even: v[i] = v[n-1-i]) and O (odd: v[i] = -v[n-1-i]) with [E O]
+    an orthogonal n x n matrix."""
+    h = n // 2
+    E = np.zeros((n, h + n % 2))
+    O = np.zeros((n, h))
+    c = 1.0 / np.sqrt(2.0)
+    for i in range(h):
+        E[i, i] = E[n - 1 - i, i] = c
+        O[i, i] = c
+        O[n - 1 - i, i] = -c
+    if n % 2:
+        E[h, h] = 1.0
+    return E, O
+
+
+def is_reflection_symmetric(A, rtol=1e-12):
+    return np.max(np.abs(A[::-1, ::-1] - A)) <= rtol * np.max(np.abs(A))
+
+
+def _eig_real(K, M, imag_tol):
     w, U = sla.eig(K, M)
     if np.any(~np.isfinite(w)):
         raise NotDiagonalizable("infinite generalized eigenvalue")
     if np.max(np.abs(w.imag) / np.maximum(np.abs(w), 1e-300)) > imag_tol:
         raise NotDiagonalizable("complex eigenvalues")
-    lam = w.real
-    U = U.real
+    return w.real, U.real
+
+
+def eig_factors(K, M, imag_tol=1e-10, cond_max=1e3):
+    """Return (lam, U, V) with K U = M U diag(lam), unit-norm ascending columns and
+    V = (M U)^{-T}.  Raises NotDiagonalizable when Remark 1's assumptions fail."""
+    if is_reflection_symmetric(K) and is_reflection_symmetric(M):
+        lams, Us = [], []
+        for Q in reflection_basis(K.shape[0]):
+            if Q.shape[1] == 0:
+                continue
+            w, Uq = _eig_real(Q.T @ K @ Q, Q.T @ M @ Q, imag_tol)
+            lams.append(w)
+            Us.append(Q @ Uq)
+        lam = np.concatenate(lams)
+        U = np.hstack(Us)
+    else:
+        lam, U = _eig_real(K, M, imag_tol)
     order = np.argsort(lam, kind="stable")
     lam = lam[order]
     U = U[:, order]

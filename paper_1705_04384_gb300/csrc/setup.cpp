@@ -162,6 +162,146 @@ double norm2_est(const std::vector<double> &A, int n) {
 }
 }  // namespace
 
+// Real eigenpairs of the m x m pencil (K, M) (column-major): A = M^{-1} K by LU,
+// then the eigenvalues and right eigenvectors of A.  Throws NOT_DIAGONALIZABLE for
+// complex eigenvalues (Remark 1).  lam: m values; U: m x m column-major.
+static void eig_pencil(SolverHandle &sh, const std::vector<double> &Kc,
+                       const std::vector<double> &Mc, int m, std::vector<double> &lam,
+                       std::vector<double> &U, cudaStream_t stream) {
+  DevBuf<double> dM, dA, dVR, dW;
+  DevBuf<int64_t> dipiv;
+  DevBuf<int> dinfo;
+  dM.alloc((size_t)m * m);
+  dA.alloc((size_t)m * m);
+  dVR.alloc((size_t)m * m);
+  dW.alloc(2 * (size_t)m);
+  dipiv.alloc(m);
+  dinfo.alloc(1);
+  IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, Mc.data(), Mc.size() * 8, cudaMemcpyHostToDevice, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(dA.ptr, Kc.data(), Kc.size() * 8, cudaMemcpyHostToDevice, stream));
+  auto check_info = [&](const char *what) {
+    int info = 0;
+    IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (info != 0)
+      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
+  };
+  size_t dws = 0, hws = 0;
+  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh.h, sh.prm, m, m, CUDA_R_64F, dM.ptr, m, CUDA_R_64F,
+                                           &dws, &hws));
+  {
+    DevBuf<char> dbuf;
+    dbuf.alloc(std::max<size_t>(dws, 1));
+    std::vector<char> hbuf(std::max<size_t>(hws, 1));
+    CUSOLVER_TRY(cusolverDnXgetrf(sh.h, sh.prm, m, m, CUDA_R_64F, dM.ptr, m, dipiv.ptr, CUDA_R_64F,
+                                  dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
+    check_info("getrf(M)");
+  }
+  CUSOLVER_TRY(cusolverDnXgetrs(sh.h, sh.prm, CUBLAS_OP_N, m, m, CUDA_R_64F, dM.ptr, m, dipiv.ptr,
+                                CUDA_R_64F, dA.ptr, m, dinfo.ptr));
+  check_info("getrs(M, K)");
+  CUSOLVER_TRY(cusolverDnXgeev_bufferSize(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR,
+                                          CUSOLVER_EIG_MODE_VECTOR, m, CUDA_R_64F, dA.ptr, m,
+                                          CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr, 1, CUDA_R_64F,
+                                          dVR.ptr, m, CUDA_R_64F, &dws, &hws));
+  {
+    DevBuf<char> dbuf;
+    dbuf.alloc(std::max<size_t>(dws, 1));
+    std::vector<char> hbuf(std::max<size_t>(hws, 1));
+    CUSOLVER_TRY(cusolverDnXgeev(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
+                                 m, CUDA_R_64F, dA.ptr, m, CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr,
+                                 1, CUDA_R_64F, dVR.ptr, m, CUDA_R_64F, dbuf.ptr, dws, hbuf.data(),
+                                 hws, dinfo.ptr));
+    check_info("geev(M^{-1}K)");
+  }
+  std::vector<double> Wc(2 * (size_t)m);
+  U.resize((size_t)m * m);
+  IGA_CUDA_TRY(cudaMemcpyAsync(Wc.data(), dW.ptr, Wc.size() * 8, cudaMemcpyDeviceToHost, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(U.data(), dVR.ptr, U.size() * 8, cudaMemcpyDeviceToHost, stream));
+  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  lam.resize(m);
+  for (int j = 0; j < m; ++j) {
+    const double re = Wc[2 * j], im = Wc[2 * j + 1];
+    const double mag = std::sqrt(re * re + im * im);
+    if (!std::isfinite(mag) || std::fabs(im) > 1e-10 * std::max(mag, 1e-300))
+      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, "complex eigenvalue of M^{-1}K (Remark 1)"};
+    lam[j] = re;
+  }
+}
+
+static bool reflection_symmetric(const std::vector<double> &A, int n) {
+  double mx = 0.0, diff = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double a = A[i + (size_t)n * j];
+      mx = std::max(mx, std::fabs(a));
+      diff = std::max(diff, std::fabs(A[(n - 1 - i) + (size_t)n * (n - 1 - j)] - a));
+    }
+  return diff <= 1e-12 * mx;
+}
+
+// Eigenvectors as columns of an n x n column-major matrix and eigenvalues (unsorted).
+// On uniform knots the factors commute with the flip i -> n-1-i, so the pencil is
+// solved separately on the even subspace (v_i = v_{n-1-i}) and the odd subspace
+// (v_i = -v_{n-1-i}); Remark 1's double outlier eigenvalue then has one eigenvector
+// in each half and U stays well conditioned.
+static void eig_all(SolverHandle &sh, const std::vector<double> &Kc, const std::vector<double> &Mc,
+                    int n, std::vector<double> &lam, std::vector<double> &Ucol,
+                    cudaStream_t stream) {
+  if (!(reflection_symmetric(Kc, n) && reflection_symmetric(Mc, n))) {
+    eig_pencil(sh, Kc, Mc, n, lam, Ucol, stream);
+    return;
+  }
+  const int h = n / 2, ne = h + n % 2, no = h;
+  const double c = 1.0 / std::sqrt(2.0);
+  // basis column q of the even (sgn=+1) / odd (sgn=-1) subspace, as (index, weight) pairs
+  auto basis = [&](int q, int sgn, int *idx, double *wt) -> int {
+    if (q < h) {
+      idx[0] = q;
+      wt[0] = c;
+      idx[1] = n - 1 - q;
+      wt[1] = sgn * c;
+      return 2;
+    }
+    idx[0] = h;  // middle entry (n odd, even part only)
+    wt[0] = 1.0;
+    return 1;
+  };
+  lam.clear();
+  Ucol.assign((size_t)n * n, 0.0);
+  int col = 0;
+  for (int part = 0; part < 2; ++part) {
+    const int m = part == 0 ? ne : no, sgn = part == 0 ? 1 : -1;
+    if (m == 0) continue;
+    std::vector<double> Kq((size_t)m * m), Mq((size_t)m * m);
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        int ia[2], ib[2];
+        double wa[2], wb[2];
+        const int na = basis(a, sgn, ia, wa), nb = basis(b, sgn, ib, wb);
+        double sk = 0.0, sm = 0.0;
+        for (int u = 0; u < na; ++u)
+          for (int v = 0; v < nb; ++v) {
+            sk += wa[u] * wb[v] * Kc[ia[u] + (size_t)n * ib[v]];
+            sm += wa[u] * wb[v] * Mc[ia[u] + (size_t)n * ib[v]];
+          }
+        Kq[a + (size_t)m * b] = sk;
+        Mq[a + (size_t)m * b] = sm;
+      }
+    std::vector<double> lq, Uq;
+    eig_pencil(sh, Kq, Mq, m, lq, Uq, stream);
+    for (int j = 0; j < m; ++j, ++col) {
+      lam.push_back(lq[j]);
+      for (int a = 0; a < m; ++a) {
+        int ia[2];
+        double wa[2];
+        const int na = basis(a, sgn, ia, wa);
+        for (int u = 0; u < na; ++u) Ucol[ia[u] + (size_t)n * col] += wa[u] * Uq[a + (size_t)m * j];
+      }
+    }
+  }
+}
+
 static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   const int n = f.n, W = f.W;
   // dense column-major M and K
@@ -176,18 +316,15 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   CUSOLVER_TRY(cusolverDnCreate(&sh.h));
   CUSOLVER_TRY(cusolverDnSetStream(sh.h, stream));
   CUSOLVER_TRY(cusolverDnCreateParams(&sh.prm));
-  DevBuf<double> dM, dA, dVR, dW, dX;
+  std::vector<double> lam_u, VR;
+  eig_all(sh, Kc, Mc, n, lam_u, VR, stream);
+  DevBuf<double> dM, dX;
   DevBuf<int64_t> dipiv;
   DevBuf<int> dinfo;
   dM.alloc((size_t)n * n);
-  dA.alloc((size_t)n * n);
-  dVR.alloc((size_t)n * n);
-  dW.alloc(2 * (size_t)n);
   dX.alloc((size_t)n * n);
   dipiv.alloc(n);
   dinfo.alloc(1);
-  IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, Mc.data(), Mc.size() * 8, cudaMemcpyHostToDevice, stream));
-  IGA_CUDA_TRY(cudaMemcpyAsync(dA.ptr, Kc.data(), Kc.size() * 8, cudaMemcpyHostToDevice, stream));
   auto check_info = [&](const char *what) {
     int info = 0;
     IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
@@ -196,54 +333,14 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
       throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
   };
   size_t dws = 0, hws = 0;
-  // A = M^{-1} K  (eq. eigendecomposition works with M^{-1} K)
-  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
-                                           &dws, &hws));
-  {
-    DevBuf<char> dbuf;
-    dbuf.alloc(std::max<size_t>(dws, 1));
-    std::vector<char> hbuf(std::max<size_t>(hws, 1));
-    CUSOLVER_TRY(cusolverDnXgetrf(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
-                                  dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
-    check_info("getrf(M)");
-  }
-  CUSOLVER_TRY(cusolverDnXgetrs(sh.h, sh.prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
-                                CUDA_R_64F, dA.ptr, n, dinfo.ptr));
-  check_info("getrs(M, K)");
-  // eigenvalues and right eigenvectors of A
-  CUSOLVER_TRY(cusolverDnXgeev_bufferSize(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR,
-                                          CUSOLVER_EIG_MODE_VECTOR, n, CUDA_R_64F, dA.ptr, n,
-                                          CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr, 1, CUDA_R_64F,
-                                          dVR.ptr, n, CUDA_R_64F, &dws, &hws));
-  {
-    DevBuf<char> dbuf;
-    dbuf.alloc(std::max<size_t>(dws, 1));
-    std::vector<char> hbuf(std::max<size_t>(hws, 1));
-    CUSOLVER_TRY(cusolverDnXgeev(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
-                                 n, CUDA_R_64F, dA.ptr, n, CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr,
-                                 1, CUDA_R_64F, dVR.ptr, n, CUDA_R_64F, dbuf.ptr, dws, hbuf.data(),
-                                 hws, dinfo.ptr));
-    check_info("geev(M^{-1}K)");
-  }
-  std::vector<double> Wc(2 * (size_t)n), VR((size_t)n * n);
-  IGA_CUDA_TRY(cudaMemcpyAsync(Wc.data(), dW.ptr, Wc.size() * 8, cudaMemcpyDeviceToHost, stream));
-  IGA_CUDA_TRY(cudaMemcpyAsync(VR.data(), dVR.ptr, VR.size() * 8, cudaMemcpyDeviceToHost, stream));
-  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
-  // Remark 1: the eigenvalues must be real
-  for (int j = 0; j < n; ++j) {
-    const double re = Wc[2 * j], im = Wc[2 * j + 1];
-    const double mag = std::sqrt(re * re + im * im);
-    if (!std::isfinite(mag) || std::fabs(im) > 1e-10 * std::max(mag, 1e-300))
-      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, "complex eigenvalue of M^{-1}K (Remark 1)"};
-  }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Wc[2 * a] < Wc[2 * b]; });
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam_u[a] < lam_u[b]; });
   f.lam.resize(n);
   f.U.assign((size_t)n * n, 0.0);
   for (int jj = 0; jj < n; ++jj) {
     const int j = order[jj];
-    f.lam[jj] = Wc[2 * j];
+    f.lam[jj] = lam_u[j];
     double nrm = 0.0;
     for (int i = 0; i < n; ++i) nrm += VR[i + (size_t)n * j] * VR[i + (size_t)n * j];
     nrm = std::sqrt(nrm);

@@ -1,0 +1,62 @@
+"""Time one operation of the library in isolation (CUDA events on the call stream).
+
+    python -m paper_1705_04384_gb300.kernel_bench --op fd|operator|solve \
+        --d 3 --ne 64 --p 3 --precision fp64 --reps 20
+
+Used to attribute time to kernels and as the small, self-contained command for
+ncu captures.  Prints one JSON line with the mean time per call.
+"""
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from .api import Problem
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="fd", choices=["fd", "operator", "solve"])
+    ap.add_argument("--d", type=int, default=3)
+    ap.add_argument("--ne", type=int, default=64)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--geometry", default="annulus")
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    a = ap.parse_args()
+    P = Problem(a.d, a.ne, a.p, geometry=a.geometry, precision=a.precision)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    b = torch.randn(P.N, dtype=torch.float64, generator=g).cuda()
+    out = torch.empty_like(b)
+    s = torch.cuda.current_stream()
+
+    def call():
+        if a.op == "fd":
+            P.precond_apply(b, out=out)
+        elif a.op == "operator":
+            P.apply_operator(b, out=out)
+        else:
+            P.solve(b, tol=1e-8, max_iter=200, out=out)
+
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times = []
+    for _ in range(a.reps):
+        e0.record(s)
+        call()
+        e1.record(s)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    print(json.dumps({"op": a.op, "d": a.d, "ne": a.ne, "p": a.p, "n": P.n, "N": P.N,
+                      "precision": a.precision, "us_mean": float(np.mean(times)),
+                      "us_min": float(np.min(times)), "reps": a.reps}))
+    P.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -47,11 +47,17 @@ def test_factors_match_oracle(p):
         assert np.max(np.abs(P.factor("K") - s.K)) <= 1e-10 * np.max(np.abs(s.K))
         lam = P.factor("lambda")
         assert np.max(np.abs(lam - R.fd.lam[0]) / np.abs(R.fd.lam[0])) <= 1e-9
-        U, Uo = P.factor("U"), R.fd.U[0]
+        U, Uo, Vt = P.factor("U"), R.fd.U[0], P.factor("Vt")
+        # eq. (eigendecomposition) holds for the GPU factors, and V^T = (M U)^{-1}
+        assert np.max(np.abs(s.K @ U - s.M @ U * lam)) <= 1e-10 * np.max(np.abs(s.K))
+        assert np.max(np.abs(Vt @ (s.M @ U) - np.eye(R.n))) <= 1e-10
+        # columns agree with LAPACK's up to sign where the eigenvalue is well separated;
+        # the near-double outlier pair of Remark 1 is fixed only up to ~eps/gap.
+        gap = np.array([np.min(np.abs(np.delete(lam, j) - lam[j])) / lam[j] for j in range(R.n)])
         sign = np.sign(np.sum(U * Uo, axis=0))
-        assert np.max(np.abs(U * sign - Uo)) <= 1e-8
-        Vt = P.factor("Vt")
-        assert np.max(np.abs(Vt * sign[:, None] - R.fd.V[0].T)) <= 1e-8 * np.max(np.abs(Vt))
+        ok = gap > 1e-4
+        assert np.max(np.abs(U * sign - Uo)[:, ok]) <= 1e-8
+        assert np.max(np.abs(Vt * sign[:, None] - R.fd.V[0].T)[ok, :]) <= 1e-8 * np.max(np.abs(Vt))
 
 
 @pytest.mark.parametrize("d,ne,p,geo", [(2, 12, 3, "annulus"), (3, 5, 4, "annulus"),

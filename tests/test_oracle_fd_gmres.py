@@ -34,6 +34,27 @@ def test_remark1_outlier_pair_and_conditioning(p):
     assert np.linalg.cond(U) < 100
 
 
+@pytest.mark.parametrize("ne,p", [(95, 5), (200, 6), (64, 5), (33, 4)])
+def test_outlier_pair_split_by_reflection_is_well_conditioned(ne, p):
+    s = C.Space1D(ne, p)
+    assert F.is_reflection_symmetric(s.K) and F.is_reflection_symmetric(s.M)
+    lam, U, V = F.eig_factors(s.K, s.M)
+    assert np.linalg.cond(U) < 50
+    # each eigenvector is even or odd under the flip, and solves the pencil
+    par = np.sum(U[::-1] * U, axis=0)
+    assert np.all(np.abs(np.abs(par) - 1.0) < 1e-12)
+    assert np.max(np.abs(s.K @ U - s.M @ U * lam)) <= 1e-11 * np.max(np.abs(s.K))
+    assert np.max(np.abs(V.T @ s.M @ U - np.eye(s.n))) < 1e-11
+
+
+def test_reflection_basis_is_orthogonal():
+    for n in (1, 2, 5, 8):
+        E, O = F.reflection_basis(n)
+        Q = np.hstack([E, O])
+        assert np.max(np.abs(Q.T @ Q - np.eye(n))) < 1e-15
+        assert np.allclose(E[::-1], E) and np.allclose(O[::-1], -O)
+
+
 def test_complex_pencil_is_rejected():
     K = np.array([[0.0, -1.0], [1.0, 0.0]])
     with pytest.raises(F.NotDiagonalizable):
