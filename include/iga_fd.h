@@ -160,6 +160,29 @@ iga_status iga_solve_host(iga_handle h, const double *rhs_host, double *x_host,
  * and one Arnoldi step); builds the graph if no solve has run yet.           */
 iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration);
 
+/* s = P^{-1} b by the same FP64 FD mode-product chain as iga_precond_apply, for
+ * callers that cannot allocate device memory when they apply the preconditioner
+ * (a fixed memory budget reserved up front, an allocator-free real-time loop, or a
+ * host whose own allocator owns the device).  The paper has no counterpart; this
+ * is a deployment variant.  No handle is needed and nothing is allocated: the two
+ * intermediate tensors live in a static device array of 2 x 2^21 doubles (32 MiB)
+ * inside the library, which each GPU that runs this call keeps until exit.
+ *   d          2 or 3;  n  DOFs per direction; N = n^d must be <= 2097152
+ *   Vt_dev     n x n row-major V^T = (M U)^{-1}   (iga_get_factor IGA_FACTOR_VT)
+ *   U_dev      n x n row-major U                  (iga_get_factor IGA_FACTOR_U)
+ *   lam_dev    n eigenvalues                      (iga_get_factor IGA_FACTOR_LAMBDA)
+ *   b_dev, s_dev  N doubles, must not overlap; all pointers are the caller's
+ *   stream     cudaStream_t (NULL = default stream); asynchronous, stream-ordered
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU (other
+ * streams, other host threads) race on it and give wrong results.  The array
+ * needs no clearing: every entry is written before it is read.
+ * Errors: INVALID_ARG (bad d, n, null pointer, N above the limit), CUDA.      */
+iga_status iga_precond_apply_noalloc(int d, int n, const double *Vt_dev, const double *U_dev,
+                                     const double *lam_dev, const double *b_dev, double *s_dev,
+                                     void *stream);
+
 /* Release everything the handle owns.  NULL is accepted. */
 iga_status iga_destroy(iga_handle h);
 

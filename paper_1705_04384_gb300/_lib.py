@@ -34,6 +34,9 @@ PROTOTYPES = {
                                       ctypes.c_double, ctypes.c_int, c_int_p, ctypes.c_void_p,
                                       c_double_p]),
     "iga_launch_counts": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p]),
+    "iga_precond_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p]),
     "iga_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "iga_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "iga_last_error": (ctypes.c_char_p, []),
