@@ -15,6 +15,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s)
 void tc_fd_apply(TcFd &fd, IdxPtr<const double> in, IdxPtr<float> out, cudaStream_t s);
 void tc_fd_apply_f64out(TcFd &fd, IdxPtr<const double> in, double *out, cudaStream_t s);
 void destroy_tc_fd(TcFd *fd);
+int *tc_fd_error_word(TcFd &fd);
 struct TcFdDeleter {
   void operator()(TcFd *p) const { destroy_tc_fd(p); }
 };

@@ -1,19 +1,486 @@
-// Placeholder for the tensor-core FD path.
+// FD solve (eq. FD2D / FD3D) with the mode products on the 5th-generation tensor
+// cores (tcgen05): TF32 or BF16 operands, FP32 accumulation in tensor memory.
+//
+// Each mode product is the GEMM D[M x N] = A[M x K] * B[K x N] of the layout-rotating
+// scheme used by the FP64 path (A: activation rows with the contracted index
+// contiguous; B: an n x n factor stored K-contiguous), M = n^{d-1}, N = K = n.
+// One CTA computes a 128-row tile:
+//   warp 0 / lane 0   TMA producer: 128-byte K-chunks of A and B (128B swizzle) into a
+//                     kStages-deep ring, one mbarrier per stage;
+//   warp 1 / lane 0   MMA issuer: tcgen05.mma (M = 128, N = n_tile, K = 8 / 16 per
+//                     instruction) into a TMEM accumulator; tcgen05.commit frees a
+//                     stage and finally signals the epilogue;
+//   warps 0..3        epilogue: tcgen05.ld of their 32 TMEM lanes, optional division by
+//                     lambda_i + mu_j (+ nu_k) (the FD diagonal), conversion, and stores
+//                     in the rotated layout (row index fastest, so stores coalesce).
+// Every wait is bounded (about one second); a wait that runs out records an error in
+// a device word that the host reads after the solve, and the CTA still releases its
+// tensor memory before it exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "context.h"
 
 namespace iga {
 
-struct TcFd {};
+constexpr int kTcThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kStages = 4;
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 
-TcFd *make_tc_fd(int, int, int, const Factor1D &, cudaStream_t) {
-  throw Error{IGA_ERR_UNSUPPORTED, "TF32/BF16 FD not built yet"};
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-void tc_fd_apply(TcFd &, IdxPtr<const double>, IdxPtr<float>, cudaStream_t) {
-  throw Error{IGA_ERR_UNSUPPORTED, "TF32/BF16 FD not built yet"};
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
 }
-void tc_fd_apply_f64out(TcFd &, IdxPtr<const double>, double *, cudaStream_t) {
-  throw Error{IGA_ERR_UNSUPPORTED, "TF32/BF16 FD not built yet"};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows 128 B apart,
+// 8-row groups 1024 B apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // LBO (not used for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // SBO
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                          uint32_t accum) {
+  if constexpr (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ------------------------------------------------------------------ GEMM kernel
+enum { kOutF32 = 0, kOutBF16 = 1, kOutF64 = 2 };
+
+struct TcEpi {
+  void *out;        // output base (element type by kind)
+  const int *oidx;  // optional device step index: out += (*oidx) * ostride elements
+  long long ostride;
+  int kind;         // kOutF32 / kOutBF16 / kOutF64
+  int tf32_round;   // round FP32 outputs to TF32 (operands of the next TF32 product)
+  int n;            // extent of the fastest component of a row index
+  int ld_out;       // stride of that component in the output
+  int nmid;         // M / n
+  const double *lam_r0, *lam_r1, *lam_c;  // FD diagonal (lam_r0 == nullptr: none)
+  int *err;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   int M, int N, int K, int n_tile, int tmem_cols, uint32_t idesc, TcEpi epi) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kStages];
+  __shared__ __align__(8) uint64_t empty_bar[kStages];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base;
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_bytes = kTileM * 128, b_bytes = (uint32_t)n_tile * 128;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kStages * a_bytes;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTileM, c0 = blockIdx.y * n_tile;
+  constexpr int kbox = KIND == 0 ? 32 : 64;  // elements per 128-byte row
+  constexpr int kmma = KIND == 0 ? 8 : 16;   // K per instruction (32 bytes)
+  const int nchunks = (K + kbox - 1) / kbox;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % kStages, use = c / kStages;
+      if (use > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+        atomicExch(epi.err, 1);
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], a_bytes + b_bytes);
+      tma_load_2d(sA + s * a_bytes, &mapA, &full_bar[s], c * kbox, m0);
+      tma_load_2d(sB + s * b_bytes, &mapB, &full_bar[s], c * kbox, c0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % kStages, use = c / kStages;
+      if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
+        atomicExch(epi.err, 2);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int rem = K - c * kbox;
+      const int ksteps = min(kbox / kmma, (rem + kmma - 1) / kmma);
+      const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+      for (int j = 0; j < ksteps; ++j)
+        mma_issue<KIND>(tmem, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc,
+                        (c > 0 || j > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[s]);
+    }
+    if (ok) mma_commit(&done_bar);
+  }
+  __syncwarp();
+
+  // epilogue (all four warps; warp w owns TMEM lanes 32w..32w+31 = rows m0+32w..)
+  // warp-uniform so that the .sync.aligned tensor-memory loads stay convergent
+  const bool have = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0) ? 1 : 0) != 0;
+  if (!have) {
+    if (lane == 0) atomicExch(epi.err, 3);
+  } else {
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    long long obase = 0;
+    double rsc = 0.0;
+    if (row < M) {
+      obase = (long long)(row % epi.n) + (long long)epi.ld_out * (row / epi.n);
+      if (epi.lam_r0) {
+        rsc = epi.lam_r0[row % epi.n];
+        if (epi.lam_r1) rsc += epi.lam_r1[row / epi.n];
+      }
+    }
+    const long long cstride = (long long)epi.ld_out * epi.nmid;
+    const long long off = epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0;
+    for (int cc = 0; cc < n_tile; cc += 16) {
+      uint32_t v[16];
+      tmem_ld16(tl + (uint32_t)cc, v);
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = c0 + cc + j;
+          if (col < N) {
+            float x = __uint_as_float(v[j]);
+            if (epi.lam_r0) x = (float)((double)x / (rsc + epi.lam_c[col]));
+            const long long o = off + obase + cstride * col;
+            if (epi.kind == kOutF32) {
+              ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
+            } else if (epi.kind == kOutBF16) {
+              ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
+            } else {
+              ((double *)epi.out)[o] = (double)x;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, (uint32_t)tmem_cols);
+}
+
+// FP64 vector (unpadded) -> TF32-rounded FP32 / BF16 tensor with padded fastest index.
+template <class T>
+__global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, long long N, int n,
+                            int ld) {
+  const double *in = inp.get();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = (i % n) + (long long)ld * (i / n);
+    if constexpr (sizeof(T) == 4) {
+      out[o] = round_tf32((float)in[i]);
+    } else {
+      out[o] = __float2bfloat16_rn((float)in[i]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct TcFd {
+  int d = 0, n = 0, prec = 0, kpad = 0, M = 0;
+  int esize = 4, n_tile = 0, n_ntiles = 0, tmem_cols = 0;
+  size_t smem = 0;
+  uint32_t idesc = 0;
+  DevBuf<uint8_t> P0, Ta, Tb;
+  DevBuf<int> err;
+  CUtensorMap mapP0{}, mapTa{}, mapTb{}, mapVt{}, mapU{};
+  const double *lam = nullptr;
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    IGA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                  cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled not available"};
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2D map over a row-major matrix: inner extent n_inner (elements read past it are
+// zero), rows, row pitch ld elements; box = one 128-byte row segment x box_rows.
+static void make_map(CUtensorMap &m, const void *base, int elem_bf16, long long n_inner,
+                     long long rows, long long ld, int box_rows) {
+  const int es = elem_bf16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)n_inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = tmap_encoder()(
+      &m, elem_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+      const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+}
+
+TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s) {
+  auto *t = new TcFd();
+  try {
+    t->d = d;
+    t->n = n;
+    t->prec = precision;
+    const bool bf = precision == IGA_PREC_BF16;
+    t->esize = bf ? 2 : 4;
+    t->kpad = f.kpad;
+    long long M = 1;
+    for (int l = 0; l < d - 1; ++l) M *= n;
+    t->M = (int)M;
+    t->n_tile = n <= 256 ? (n + 15) / 16 * 16 : 128;
+    t->n_ntiles = (n + t->n_tile - 1) / t->n_tile;
+    t->tmem_cols = 32;
+    while (t->tmem_cols < t->n_tile) t->tmem_cols *= 2;
+    t->smem = 1024 + (size_t)kStages * (kTileM * 128 + (size_t)t->n_tile * 128);
+    // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
+    const uint32_t fmt = bf ? 1u : 2u;
+    t->idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(t->n_tile >> 3) << 17) |
+               ((uint32_t)(kTileM >> 4) << 24);
+    const size_t bytes = (size_t)M * t->kpad * t->esize;
+    t->P0.alloc(bytes);
+    t->Ta.alloc(bytes);
+    t->Tb.alloc(bytes);
+    IGA_CUDA_TRY(cudaMemsetAsync(t->P0.ptr, 0, bytes, s));
+    IGA_CUDA_TRY(cudaMemsetAsync(t->Ta.ptr, 0, bytes, s));
+    IGA_CUDA_TRY(cudaMemsetAsync(t->Tb.ptr, 0, bytes, s));
+    t->err.alloc(1);
+    IGA_CUDA_TRY(cudaMemsetAsync(t->err.ptr, 0, sizeof(int), s));
+    make_map(t->mapP0, t->P0.ptr, bf, n, M, t->kpad, kTileM);
+    make_map(t->mapTa, t->Ta.ptr, bf, n, M, t->kpad, kTileM);
+    make_map(t->mapTb, t->Tb.ptr, bf, n, M, t->kpad, kTileM);
+    const void *vt = bf ? (const void *)f.d_Vt16.ptr : (const void *)f.d_Vt32.ptr;
+    const void *u = bf ? (const void *)f.d_U16.ptr : (const void *)f.d_U32.ptr;
+    make_map(t->mapVt, vt, bf, n, n, f.kpad, t->n_tile);
+    make_map(t->mapU, u, bf, n, n, f.kpad, t->n_tile);
+    t->lam = f.d_lam.ptr;
+    if (bf) {
+      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)t->smem));
+    } else {
+      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)t->smem));
+    }
+    IGA_CUDA_TRY(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete t;
+    throw;
+  }
+  return t;
+}
+
 void destroy_tc_fd(TcFd *fd) { delete fd; }
+
+static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi,
+                 cudaStream_t s) {
+  dim3 grid((t.M + kTileM - 1) / kTileM, t.n_ntiles);
+  if (t.prec == IGA_PREC_BF16)
+    tc_gemm_kernel<1><<<grid, kTcThreads, t.smem, s>>>(A, B, t.M, t.n, t.n, t.n_tile, t.tmem_cols,
+                                                       t.idesc, epi);
+  else
+    tc_gemm_kernel<0><<<grid, kTcThreads, t.smem, s>>>(A, B, t.M, t.n, t.n, t.n_tile, t.tmem_cols,
+                                                       t.idesc, epi);
+  IGA_LAUNCH_CHECK();
+}
+
+// The chain pack -> d forward products (the d-th fused with the FD diagonal) -> d
+// inverse products; the last writes `final` (fp32 or fp64, unpadded, step-indexed).
+static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, cudaStream_t s) {
+  const bool bf = t.prec == IGA_PREC_BF16;
+  const long long N = (long long)t.M * t.n;
+  const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
+  if (bf)
+    pack_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(in, (__nv_bfloat16 *)t.P0.ptr, N, t.n, t.kpad);
+  else
+    pack_kernel<float><<<blocks, 256, 0, s>>>(in, (float *)t.P0.ptr, N, t.n, t.kpad);
+  IGA_LAUNCH_CHECK();
+  TcEpi mid{};
+  mid.kind = bf ? kOutBF16 : kOutF32;
+  mid.tf32_round = bf ? 0 : 1;
+  mid.n = t.n;
+  mid.ld_out = t.kpad;
+  mid.nmid = t.M / t.n;
+  mid.err = t.err.ptr;
+  auto to = [&](DevBuf<uint8_t> &buf) {
+    TcEpi e = mid;
+    e.out = buf.ptr;
+    return e;
+  };
+  const CUtensorMap *cur = &t.mapP0;
+  DevBuf<uint8_t> *bufs[2] = {&t.Ta, &t.Tb};
+  const CUtensorMap *maps[2] = {&t.mapTa, &t.mapTb};
+  int which = 0;
+  const int total = 2 * t.d;
+  for (int g = 0; g < total; ++g) {
+    const bool fwd = g < t.d;
+    const CUtensorMap &B = fwd ? t.mapVt : t.mapU;
+    TcEpi e;
+    if (g == total - 1) {
+      e = final_epi;
+    } else {
+      e = to(*bufs[which]);
+    }
+    if (g == t.d - 1) {
+      e.lam_r0 = t.lam;
+      e.lam_r1 = t.d == 3 ? t.lam : nullptr;
+      e.lam_c = t.lam;
+    }
+    gemm(t, *cur, B, e, s);
+    if (g != total - 1) {
+      cur = maps[which];
+      which ^= 1;
+    }
+  }
+}
+
+void tc_fd_apply(TcFd &t, IdxPtr<const double> in, IdxPtr<float> out, cudaStream_t s) {
+  TcEpi e{};
+  e.out = out.base;
+  e.oidx = out.idx;
+  e.ostride = out.stride;
+  if (out.idx) e.ostride = out.stride;
+  e.kind = kOutF32;
+  e.tf32_round = 0;
+  e.n = t.n;
+  e.ld_out = t.n;
+  e.nmid = t.M / t.n;
+  e.err = t.err.ptr;
+  if (out.idx && out.off) throw Error{IGA_ERR_INVALID_ARG, "unsupported output offset"};
+  chain(t, in, e, s);
+}
+
+void tc_fd_apply_f64out(TcFd &t, IdxPtr<const double> in, double *out, cudaStream_t s) {
+  TcEpi e{};
+  e.out = out;
+  e.kind = kOutF64;
+  e.n = t.n;
+  e.ld_out = t.n;
+  e.nmid = t.M / t.n;
+  e.err = t.err.ptr;
+  chain(t, in, e, s);
+}
+
+int *tc_fd_error_word(TcFd &t) { return t.err.ptr; }
 
 }  // namespace iga

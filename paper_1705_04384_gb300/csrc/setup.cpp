@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <numeric>
@@ -397,6 +398,18 @@ template <class T> static void upload(DevBuf<T> &d, const std::vector<T> &h, cud
   IGA_CUDA_TRY(cudaMemcpyAsync(d.ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
 }
 
+// FP32 value rounded to the nearest TF32 (10-bit mantissa), ties to even.
+static float to_tf32(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0xfffu + ((u >> 13) & 1u);
+    u &= ~0x1fffu;
+  }
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+
 static void upload_factor(Factor1D &f, cudaStream_t s) {
   upload(f.d_start, f.start, s);
   for (int o = 0; o < 3; ++o) upload(f.d_band[o], f.band[o], s);
@@ -412,8 +425,8 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
       u16((size_t)n * f.kpad, __float2bfloat16(0.f));
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      vt32[(size_t)i * f.kpad + j] = (float)f.Vt[(size_t)i * n + j];
-      u32[(size_t)i * f.kpad + j] = (float)f.U[(size_t)i * n + j];
+      vt32[(size_t)i * f.kpad + j] = to_tf32((float)f.Vt[(size_t)i * n + j]);
+      u32[(size_t)i * f.kpad + j] = to_tf32((float)f.U[(size_t)i * n + j]);
       vt16[(size_t)i * f.kpad + j] = __float2bfloat16((float)f.Vt[(size_t)i * n + j]);
       u16[(size_t)i * f.kpad + j] = __float2bfloat16((float)f.U[(size_t)i * n + j]);
     }

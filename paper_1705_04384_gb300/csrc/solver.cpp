@@ -368,6 +368,15 @@ iga_status Ctx::solve(const double *rhs_dev, double *x_dev, int use_x0, double t
   IGA_CUDA_TRY(cudaMemcpyAsync(h_hist, ws.hist, (size_t)(max_iter + 1) * 8,
                                cudaMemcpyDeviceToHost, stream));
   IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (tc) {
+    int err = 0;
+    IGA_CUDA_TRY(cudaMemcpy(&err, tc_fd_error_word(*tc), sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      IGA_CUDA_TRY(cudaMemset(tc_fd_error_word(*tc), 0, sizeof(int)));
+      throw Error{IGA_ERR_DEVICE_TIMEOUT,
+                  "a tensor-core FD wait timed out (code " + std::to_string(err) + ")"};
+    }
+  }
   const SolveState &r_ = *h_st;
   if (iters) *iters = r_.k;
   if (hist_out) {

@@ -1,0 +1,75 @@
+"""Precision form: FD mode products on tcgen05 tensor cores (TF32 / BF16 operands,
+FP32 accumulation) inside flexible GMRES; operator, orthogonalization, least squares
+and eigen-factors stay FP64.
+
+Tolerances: one TF32 rounding has relative error <= 2^-11 (BF16: 2^-9); the FD solve
+rounds its input and each of the 2d - 1 intermediates, and cond(U) <= 15 amplifies
+that, so the preconditioner differs from the FP64 FD by ~1e-3 (TF32) / ~1e-2 (BF16);
+the tests bound it by 1e-2 / 6e-2 (an indexing error would give O(1)).  Flexible
+GMRES must still reach the FP64 true residual 1e-8, checked with the oracle's A_C.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from tests.oracle_ref import ref
+
+pytestmark = pytest.mark.gpu
+
+FD_TOL = {"tf32": 1e-2, "bf16": 6e-2}
+
+
+def _problem(d, ne, p, precision, geometry="annulus"):
+    from paper_1705_04384_gb300.api import Problem
+    return Problem(d, ne, p, geometry=geometry, precision=precision)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("d,ne,p", [(2, 40, 3), (2, 95, 5), (2, 300, 3), (3, 9, 3), (3, 20, 4),
+                                     (3, 64, 3)])
+def test_tensor_core_fd_close_to_oracle(prec, d, ne, p):
+    R = ref(d, ne, p, assemble=False)
+    b = np.random.Generator(np.random.PCG64(3)).standard_normal(R.N)
+    want = R.fd(b)
+    with _problem(d, ne, p, prec) as P:
+        got = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+        got2 = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.array_equal(got, got2)  # deterministic
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= FD_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("d,ne,p,geo", [(2, 32, 3, "annulus"), (2, 70, 5, "annulus"),
+                                         (3, 10, 3, "annulus"), (3, 8, 4, "revolved")])
+def test_flexible_gmres_reaches_fp64_residual(prec, d, ne, p, geo):
+    R = ref(d, ne, p, geo)
+    b = R.manufactured_rhs(0.0) if geo == "annulus" else \
+        np.random.Generator(np.random.PCG64(11)).standard_normal(R.N)
+    o = R.gmres(b, tol=1e-8, max_iter=300)
+    with _problem(d, ne, p, prec, geo) as P:
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
+        x = x.cpu().numpy()
+    relres = np.linalg.norm(b - R.A @ x) / np.linalg.norm(b)
+    assert info["status"] == 0
+    assert relres <= 1.05e-8, relres
+    assert abs(relres - info["relres_true"]) <= 1e-12
+    assert np.linalg.norm(x - o["x"]) <= 1e-6 * np.linalg.norm(o["x"])
+    # the outer iteration wins back the lost precision with a modest count increase
+    assert info["iters"] <= 2 * o["iters"] + 5
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_mixed_full_size_3d_ne64(prec):
+    import workload as W
+    R = ref(3, 64, 3, assemble=False)
+    b = W.config_rhs("3d_annulus_ne64", R.points, p_index=0)
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([[0, R.N - 1], rng.integers(0, R.N, 24)]))
+    rows = R.rows(idx)
+    with _problem(3, 64, 3, prec) as P:
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=200)
+        x = x.cpu().numpy()
+    assert info["status"] == 0 and info["relres_true"] <= 1.05e-8
+    assert np.max(np.abs(b[idx] - rows @ x)) <= 1.05e-8 * np.linalg.norm(b)
