@@ -148,6 +148,46 @@ iga_status iga_solve(iga_handle h, const double *rhs_dev, double *x_dev, int use
                      double tol, int max_iter, int *iters, double *res_hist_host,
                      double *true_relres);
 
+/* iga_solve for nrhs right-hand sides of the same problem at once.  Each right-hand
+ * side has its own Krylov space, rotations and stopping test (the same GMRES as
+ * iga_solve, bitwise identical per right-hand side); they advance in lockstep so
+ * that every operator pass and FD mode product serves all of them in one launch.
+ *   nrhs          1..1024
+ *   rhs_dev       nrhs x N doubles, right-hand side r at rhs_dev + r*N
+ *   x_dev         nrhs x N doubles (solutions; initial guesses if use_x0)
+ *   iters         (host, may be NULL) nrhs iteration counts
+ *   res_hist_host (host, may be NULL) nrhs x (max_iter + 1) residual estimates
+ *   true_relres   (host, may be NULL) nrhs FP64 true relative residuals
+ *   status        (host, may be NULL) nrhs per-right-hand-side iga_status values
+ * Returns IGA_ERR_NAN if any right-hand side hit a non-finite value, else
+ * IGA_ERR_NO_CONVERGENCE if any missed tol, else IGA_OK.  Synchronizes the stream. */
+iga_status iga_solve_multi(iga_handle h, int nrhs, const double *rhs_dev, double *x_dev,
+                           int use_x0, double tol, int max_iter, int *iters,
+                           double *res_hist_host, double *true_relres, int *status);
+
+/* Asynchronous form of iga_solve_multi: enqueues the whole solve (one CUDA graph
+ * launch plus copies) on the handle's stream and returns.  At most one solve per
+ * handle may be in flight; rhs_dev and x_dev must stay valid until it completes.
+ * iga_solve_ready sets *ready to 1 once the solve has finished (never blocks);
+ * iga_solve_collect waits for it and returns its results and status exactly as
+ * iga_solve_multi does.  Handles on different streams run concurrently.       */
+iga_status iga_solve_async(iga_handle h, int nrhs, const double *rhs_dev, double *x_dev,
+                           int use_x0, double tol, int max_iter);
+iga_status iga_solve_ready(iga_handle h, int *ready);
+iga_status iga_solve_collect(iga_handle h, int *iters, double *res_hist_host, double *true_relres,
+                             int *status);
+
+/* Batched form: nprob independent problems (distinct handles, ideally each on its
+ * own stream) with nrhs[q] right-hand sides each, x0 = 0.  All solves are enqueued
+ * first (one graph launch per problem, all right-hand sides of a problem in
+ * lockstep) and then collected, so the problems overlap on the device.
+ *   rhs_dev[q], x_dev[q]     nrhs[q] x N_q doubles (device)
+ *   iters, true_relres, status  (host, may be NULL) sum(nrhs) entries, problem-major
+ * Returns the worst status as iga_solve_multi does.                          */
+iga_status iga_solve_batched(int nprob, const iga_handle *handles, const int *nrhs,
+                             const double *const *rhs_dev, double *const *x_dev, double tol,
+                             int max_iter, int *iters, double *true_relres, int *status);
+
 /* iga_solve with host buffers: copies rhs_host (N doubles) to the device, solves
  * with x0 = 0, and copies the solution to x_host (N doubles).  Same outputs and
  * errors as iga_solve.  Synchronous.                                         */

@@ -139,3 +139,79 @@ class Problem:
         check(st, "iga_solve_host", (STATUS_NO_CONVERGENCE,))
         return dict(iters=iters.value, hist=hist[:iters.value + 1].copy(),
                     relres_true=rel.value, status=st)
+
+    # ---------------------------------------------------------------- many right-hand sides
+    def _block(self, v, nrhs):
+        v = torch.as_tensor(v, dtype=torch.float64, device=self.device).contiguous()
+        if v.numel() != nrhs * self.N:
+            raise ValueError(f"expected {nrhs} x {self.N} values, got {v.numel()}")
+        return v
+
+    def solve_multi(self, rhs, tol=1e-8, max_iter=200, x0=None, out=None):
+        """rhs: (nrhs, N).  Returns (x, info) with per-rhs lists."""
+        nrhs = rhs.shape[0] if hasattr(rhs, "shape") and len(rhs.shape) == 2 else 1
+        rhs = self._block(rhs, nrhs)
+        out = torch.empty_like(rhs) if out is None else out
+        use_x0 = 0
+        if x0 is not None:
+            out.copy_(self._block(x0, nrhs))
+            use_x0 = 1
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        stat = np.zeros(nrhs, dtype=np.int32)
+        hist = np.zeros((nrhs, max_iter + 1), dtype=np.float64)
+        st = self.lib.iga_solve_multi(self.h, nrhs, _ptr(rhs), _ptr(out), use_x0, float(tol),
+                                      int(max_iter), iters.ctypes.data_as(ctypes.c_void_p),
+                                      hist.ctypes.data_as(ctypes.c_void_p),
+                                      rel.ctypes.data_as(ctypes.c_void_p),
+                                      stat.ctypes.data_as(ctypes.c_void_p))
+        check(st, "iga_solve_multi", (STATUS_NO_CONVERGENCE,))
+        return out.view(nrhs, self.N), dict(iters=iters, relres_true=rel, status=stat,
+                                            hist=[hist[r, :iters[r] + 1].copy()
+                                                  for r in range(nrhs)])
+
+    def solve_async(self, rhs, out, tol=1e-8, max_iter=200):
+        """Enqueue a solve of rhs (nrhs x N, device) into out; returns immediately."""
+        nrhs = rhs.numel() // self.N
+        check(self.lib.iga_solve_async(self.h, nrhs, _ptr(rhs), _ptr(out), 0, float(tol),
+                                       int(max_iter)), "iga_solve_async")
+        self._pending = (nrhs, max_iter)
+
+    def ready(self):
+        r = ctypes.c_int()
+        check(self.lib.iga_solve_ready(self.h, ctypes.byref(r)), "iga_solve_ready")
+        return bool(r.value)
+
+    def collect(self):
+        nrhs, max_iter = self._pending
+        iters = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs, dtype=np.float64)
+        stat = np.zeros(nrhs, dtype=np.int32)
+        st = self.lib.iga_solve_collect(self.h, iters.ctypes.data_as(ctypes.c_void_p), None,
+                                        rel.ctypes.data_as(ctypes.c_void_p),
+                                        stat.ctypes.data_as(ctypes.c_void_p))
+        check(st, "iga_solve_collect", (STATUS_NO_CONVERGENCE,))
+        self._pending = None
+        return dict(iters=iters, relres_true=rel, status=stat)
+
+
+def solve_batched(problems, rhs, out, tol=1e-8, max_iter=200):
+    """Batched form: problems[q] (distinct Problems, ideally on distinct streams),
+    rhs[q] / out[q] device tensors (nrhs_q, N_q).  Returns per-rhs arrays
+    (problem-major) of iterations, true relative residuals and statuses."""
+    lib = _lib.load()
+    nprob = len(problems)
+    H = (ctypes.c_void_p * nprob)(*[P.h.value for P in problems])
+    nr = np.array([r.numel() // P.N for P, r in zip(problems, rhs)], dtype=np.int32)
+    R = (ctypes.c_void_p * nprob)(*[r.data_ptr() for r in rhs])
+    X = (ctypes.c_void_p * nprob)(*[x.data_ptr() for x in out])
+    tot = int(nr.sum())
+    iters = np.zeros(tot, dtype=np.int32)
+    rel = np.zeros(tot, dtype=np.float64)
+    stat = np.zeros(tot, dtype=np.int32)
+    st = lib.iga_solve_batched(nprob, H, nr.ctypes.data_as(ctypes.c_void_p), R, X, float(tol),
+                               int(max_iter), iters.ctypes.data_as(ctypes.c_void_p),
+                               rel.ctypes.data_as(ctypes.c_void_p),
+                               stat.ctypes.data_as(ctypes.c_void_p))
+    check(st, "iga_solve_batched", (STATUS_NO_CONVERGENCE,))
+    return dict(iters=iters, relres_true=rel, status=stat, nrhs=nr)

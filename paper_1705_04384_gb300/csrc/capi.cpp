@@ -2,6 +2,7 @@
 // exceptions into an iga_status and records a message for iga_last_error().
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -115,7 +116,7 @@ iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host) {
 iga_status iga_apply_operator(iga_handle h, const double *u_dev, double *Au_dev) {
   return guarded([&]() -> iga_status {
     if (!h || !u_dev || !Au_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
-    h->c.apply_operator<double>(iga::plain_ptr<const double>(u_dev), Au_dev, h->c.stream);
+    h->c.apply_operator<double>(iga::plain_ptr<const double>(u_dev), Au_dev, 1, h->c.stream);
     return IGA_OK;
   });
 }
@@ -128,20 +129,104 @@ iga_status iga_precond_apply(iga_handle h, const double *b_dev, double *s_dev) {
                                    h->c.stream));
       return IGA_OK;
     }
-    h->c.precond(iga::plain_ptr<const double>(b_dev), s_dev, h->c.stream);
+    h->c.precond(iga::plain_ptr<const double>(b_dev), s_dev, 1, h->c.stream);
     return IGA_OK;
   });
+}
+
+static void check_solve_args(int nrhs, int max_iter, double tol) {
+  if (nrhs < 1 || nrhs > 1024) throw iga::Error{IGA_ERR_INVALID_ARG, "nrhs must be in 1..1024"};
+  if (max_iter < 1 || max_iter > iga::kMaxIter)
+    throw iga::Error{IGA_ERR_INVALID_ARG, "max_iter must be in 1..4096"};
+  if (!(tol >= 0.0)) throw iga::Error{IGA_ERR_INVALID_ARG, "tol must be >= 0"};
 }
 
 iga_status iga_solve(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0, double tol,
                      int max_iter, int *iters, double *res_hist_host, double *true_relres) {
   return guarded([&]() -> iga_status {
     if (!h || !rhs_dev || !x_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
-    if (max_iter < 1 || max_iter > iga::kMaxIter)
-      throw iga::Error{IGA_ERR_INVALID_ARG, "max_iter must be in 1..4096"};
-    if (!(tol >= 0.0)) throw iga::Error{IGA_ERR_INVALID_ARG, "tol must be >= 0"};
-    return h->c.solve(rhs_dev, x_dev, use_x0 ? 1 : 0, tol, max_iter, iters, res_hist_host,
-                      true_relres);
+    check_solve_args(1, max_iter, tol);
+    h->c.enqueue(1, rhs_dev, x_dev, use_x0 ? 1 : 0, tol, max_iter);
+    return h->c.collect(iters, res_hist_host, true_relres, nullptr);
+  });
+}
+
+iga_status iga_solve_multi(iga_handle h, int nrhs, const double *rhs_dev, double *x_dev,
+                           int use_x0, double tol, int max_iter, int *iters,
+                           double *res_hist_host, double *true_relres, int *status) {
+  return guarded([&]() -> iga_status {
+    if (!h || !rhs_dev || !x_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    check_solve_args(nrhs, max_iter, tol);
+    h->c.enqueue(nrhs, rhs_dev, x_dev, use_x0 ? 1 : 0, tol, max_iter);
+    return h->c.collect(iters, res_hist_host, true_relres, status);
+  });
+}
+
+iga_status iga_solve_async(iga_handle h, int nrhs, const double *rhs_dev, double *x_dev,
+                           int use_x0, double tol, int max_iter) {
+  return guarded([&]() -> iga_status {
+    if (!h || !rhs_dev || !x_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    check_solve_args(nrhs, max_iter, tol);
+    h->c.enqueue(nrhs, rhs_dev, x_dev, use_x0 ? 1 : 0, tol, max_iter);
+    return IGA_OK;
+  });
+}
+
+iga_status iga_solve_ready(iga_handle h, int *ready) {
+  return guarded([&]() -> iga_status {
+    if (!h || !ready) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    *ready = h->c.ready() ? 1 : 0;
+    return IGA_OK;
+  });
+}
+
+iga_status iga_solve_collect(iga_handle h, int *iters, double *res_hist_host, double *true_relres,
+                             int *status) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    return h->c.collect(iters, res_hist_host, true_relres, status);
+  });
+}
+
+iga_status iga_solve_batched(int nprob, const iga_handle *handles, const int *nrhs,
+                             const double *const *rhs_dev, double *const *x_dev, double tol,
+                             int max_iter, int *iters, double *true_relres, int *status) {
+  return guarded([&]() -> iga_status {
+    if (nprob < 1 || !handles || !nrhs || !rhs_dev || !x_dev)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "bad batch arguments"};
+    for (int q = 0; q < nprob; ++q) {
+      if (!handles[q] || !rhs_dev[q] || !x_dev[q])
+        throw iga::Error{IGA_ERR_INVALID_ARG, "null entry in batch"};
+      check_solve_args(nrhs[q], max_iter, tol);
+      for (int q2 = 0; q2 < q; ++q2)
+        if (handles[q2] == handles[q])
+          throw iga::Error{IGA_ERR_INVALID_ARG, "a handle appears twice in one batch"};
+    }
+    // enqueue every problem on its own stream, then collect in order
+    int enq = 0;
+    iga_status overall = IGA_OK;
+    try {
+      for (; enq < nprob; ++enq)
+        handles[enq]->c.enqueue(nrhs[enq], rhs_dev[enq], x_dev[enq], 0, tol, max_iter);
+    } catch (...) {
+      for (int q = 0; q < enq; ++q) {
+        try {
+          handles[q]->c.collect(nullptr, nullptr, nullptr, nullptr);
+        } catch (...) {
+        }
+      }
+      throw;
+    }
+    long long off = 0;
+    for (int q = 0; q < nprob; ++q) {
+      const iga_status st = handles[q]->c.collect(iters ? iters + off : nullptr, nullptr,
+                                                  true_relres ? true_relres + off : nullptr,
+                                                  status ? status + off : nullptr);
+      if (st == IGA_ERR_NAN) overall = IGA_ERR_NAN;
+      else if (st != IGA_OK && overall == IGA_OK) overall = st;
+      off += nrhs[q];
+    }
+    return overall;
   });
 }
 
@@ -149,16 +234,14 @@ iga_status iga_solve_host(iga_handle h, const double *rhs_host, double *x_host, 
                           int max_iter, int *iters, double *res_hist_host, double *true_relres) {
   return guarded([&]() -> iga_status {
     if (!h || !rhs_host || !x_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
-    if (max_iter < 1 || max_iter > iga::kMaxIter)
-      throw iga::Error{IGA_ERR_INVALID_ARG, "max_iter must be in 1..4096"};
+    check_solve_args(1, max_iter, tol);
     iga::Ctx &c = h->c;
+    c.ensure_ws(max_iter, 1);
     IGA_CUDA_TRY(cudaMemcpyAsync(c.r.ptr, rhs_host, c.N * 8, cudaMemcpyHostToDevice, c.stream));
-    // solve reads rhs from c.r into c.b before using c.r as scratch
-    const iga_status st = c.solve(c.r.ptr, c.x0.ptr, 0, tol, max_iter, iters, res_hist_host,
-                                  true_relres);
+    // the solve copies rhs from c.r into c.b before it uses c.r as scratch
+    c.enqueue(1, c.r.ptr, c.x0.ptr, 0, tol, max_iter);
     IGA_CUDA_TRY(cudaMemcpyAsync(x_host, c.x.ptr, c.N * 8, cudaMemcpyDeviceToHost, c.stream));
-    IGA_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    return st;
+    return c.collect(iters, res_hist_host, true_relres, nullptr);
   });
 }
 
@@ -166,12 +249,10 @@ iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration) {
   return guarded([&]() -> iga_status {
     if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
     iga::Ctx &c = h->c;
-    if (!c.gexec) {
-      c.ensure_ws(1);
-      c.build_graph(c.ws_max_iter, 0);
-    }
-    if (fixed) *fixed = c.launches_fixed;
-    if (per_iteration) *per_iteration = c.launches_iter;
+    c.ensure_ws(std::max(c.ws_max_iter, 1), 1);
+    iga::SolveGraph &g = c.graph_for(1, 0);
+    if (fixed) *fixed = g.launches_fixed;
+    if (per_iteration) *per_iteration = g.launches_iter;
     return IGA_OK;
   });
 }

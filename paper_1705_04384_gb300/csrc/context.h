@@ -1,6 +1,9 @@
 // Problem context behind an iga_handle: factors, geometry fields, operator plan,
-// FD buffers, Krylov workspace and the captured solve graph.
+// FD buffers, Krylov workspace and the captured solve graphs.
 #pragma once
+
+#include <map>
+#include <utility>
 
 #include "iga_internal.h"
 
@@ -11,9 +14,9 @@ void launch_field_maxabs(const double *fields, long long ldf, long long N, int n
 
 // tcgen05 FD (TF32 / BF16) -- defined in kernels_fd_tc.cu
 struct TcFd;
-TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s);
-void tc_fd_apply(TcFd &fd, IdxPtr<const double> in, IdxPtr<float> out, cudaStream_t s);
-void tc_fd_apply_f64out(TcFd &fd, IdxPtr<const double> in, double *out, cudaStream_t s);
+TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s, int R_max);
+void tc_fd_apply(TcFd &fd, IdxPtr<const double> in, IdxPtr<float> out, int R, cudaStream_t s);
+void tc_fd_apply_f64out(TcFd &fd, IdxPtr<const double> in, double *out, int R, cudaStream_t s);
 void destroy_tc_fd(TcFd *fd);
 int *tc_fd_error_word(TcFd &fd);
 struct TcFdDeleter {
@@ -28,6 +31,12 @@ struct OpPlan {
   int B_ord[6] = {0, 0, 0, 0, 0, 0};
   int nterm = 0;
   ContractTerm terms[kMaxFields];
+};
+
+struct SolveGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches_fixed = 0, launches_iter = 0;
 };
 
 struct Ctx {
@@ -46,40 +55,52 @@ struct Ctx {
   int nactive = 0;
   double field_maxabs[kMaxFields] = {};
   OpPlan plan;
-  DevBuf<double> op_scratch;  // (nA + nB) x N
-  DevBuf<double> fd_scratch;  // 2 x N
-  std::unique_ptr<TcFd, TcFdDeleter> tc;
 
+  // buffers sized for R_max right-hand sides
+  int R_max = 0;
+  DevBuf<double> op_scratch;  // (nA + nB) x R_max x N
+  DevBuf<double> fd_scratch;  // 2 x R_max x N
+  std::unique_ptr<TcFd, TcFdDeleter> tc;
   DevBuf<double> b, x, x0, w, r;
 
-  // Krylov workspace
-  int ws_max_iter = 0;
+  // Krylov workspace for (ws_max_iter, ws_R)
+  int ws_max_iter = 0, ws_R = 0;
   DevBuf<double> V, Zd, H, cs, sn, g, y, hist, partials, scal;
   DevBuf<float> Zf;
   DevBuf<unsigned int> counter;
   DevBuf<SolveState> st;
+  DevBuf<RhsState> rs;
   KrylovWs ws{};
   SolveState *h_st = nullptr;  // pinned
-  double *h_hist = nullptr;    // pinned, max_iter + 2
+  RhsState *h_rs = nullptr;    // pinned, R
+  double *h_hist = nullptr;    // pinned, R x (max_iter + 2)
 
-  // captured solve graph
-  cudaGraphExec_t gexec = nullptr;
-  cudaGraph_t graph = nullptr;
-  int g_max_iter = -1, g_use_x0 = -1;
-  int launches_fixed = 0, launches_iter = 0;  // kernels in the captured graph
+  // captured solve graphs keyed by (R, use_x0)
+  std::map<std::pair<int, int>, SolveGraph> graphs;
+
+  // the solve in flight (enqueue ... collect)
+  bool pending = false;
+  int pend_R = 0, pend_max_iter = 0;
+  double pend_tol = 0.0;
+  cudaEvent_t done_ev = nullptr;
 
   ~Ctx();
   void setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_);
-  template <class Tin> void apply_operator(IdxPtr<const Tin> in, double *out, cudaStream_t s);
-  void precond(IdxPtr<const double> in, double *out, cudaStream_t s);  // FP64 result
-  void ensure_ws(int max_iter);
+  void ensure_capacity(int R);
+  template <class Tin>
+  void apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t s);
+  void precond(IdxPtr<const double> in, double *out, int R, cudaStream_t s);  // FP64 result
+  void ensure_ws(int max_iter, int R);
   void launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
   void launch_solve_prologue(int use_x0, cudaGraphConditionalHandle cond, int has_cond,
                              cudaStream_t s);
   void launch_solve_epilogue(int use_x0, cudaStream_t s);
-  void build_graph(int max_iter, int use_x0);
-  iga_status solve(const double *rhs_dev, double *x_dev, int use_x0, double tol, int max_iter,
-                   int *iters, double *hist_out, double *relres);
+  SolveGraph &graph_for(int R, int use_x0);
+  void drop_graphs();
+  void enqueue(int R, const double *rhs_dev, double *x_dev, int use_x0, double tol,
+               int max_iter);
+  bool ready();
+  iga_status collect(int *iters, double *hist_out, double *relres, int *status_out);
   void collocation_points(double *xyz) const;
 };
 

@@ -134,9 +134,11 @@ void launch_geometry_fields(int d, const iga_geometry &g, const double *tau1, co
 
 // Banded mode product along direction dir (0-based) of an n1 x n2 x n3 tensor:
 // out[o] = B^{(order[o])}_dir applied along dir, for o < nout.
+// nrhs tensors stacked back to back (slowest index).
 template <class Tin>
 void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orders, int nout,
-                      int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s);
+                      int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
+                      int nrhs = 1);
 
 // Final pass along direction 0 with contraction by the coefficient fields:
 // out = sum_t coef_t(x) * B^{(order_t)}_0 in[input_t].
@@ -147,7 +149,8 @@ struct ContractTerm {
 };
 template <class Tin>
 void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *terms, int nterm,
-                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s);
+                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
+                          int nrhs = 1);
 
 // FP64 mode-product GEMM with layout rotation:
 //   out[r + M*c] (+scale) = sum_k A[r*K + k] * Bt[c*K + k],  r < M, c < N(=K).
@@ -157,41 +160,53 @@ struct FdScale {
   const double *lam_r0, *lam_r1, *lam_c;  // lam_r1 may be null (2D)
   int n0;
 };
+// nrhs right-hand sides stacked as the slowest index (M = nrhs * rows per rhs).
 template <class Tout>
 void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out, int M, int N,
-                      int K, const FdScale *scale, cudaStream_t s);
+                      int K, const FdScale *scale, cudaStream_t s, int nrhs = 1);
 
 // ---------------------------------------------------------------- Krylov kernels
-struct SolveState {
-  int k;            // completed Arnoldi steps
-  int done;         // loop finished
-  int flag;         // 0 running, 1 converged, 2 max_iter, 3 breakdown, 4 nan
-  int max_iter;
-  double tol;
+struct RhsState {
+  int done;         // this right-hand side has stopped iterating
+  int flag;         // 0 running, 1 converged, 2 max_iter, 3 breakdown, 4 non-finite
+  int kconv;        // Arnoldi steps taken by this right-hand side
+  int pad;
   double bnorm, beta;
   double relres_true;
+  double pad2;
 };
 
-struct KrylovWs {
-  double *V;  long long ldv;     // (max_iter+1) x ldv
-  void *Z;    long long ldz;     // max_iter x ldz, FP64 or FP32
-  int z_fp32;
-  double *H;                     // (max_iter+1) x max_iter col-major, ld = max_iter+1
-  double *cs, *sn, *g, *y, *hist;
-  double *partials;              // nblk x (max_iter+2)
-  unsigned int *counter;         // last-block counters (4)
-  double *scal;                  // scalar scratch (8)
-  SolveState *st;
-  int nblk;
-  long long N;
+struct SolveState {
+  int k;            // Arnoldi step shared by all right-hand sides
+  int active;       // right-hand sides still iterating
   int max_iter;
+  int R;
+  double tol;
+};
+
+// Vectors of all right-hand sides are stored back to back: vector j of rhs r at
+// V + (j R + r) N (same for Z); per-rhs small arrays at a fixed stride.
+struct KrylovWs {
+  double *V;
+  void *Z;
+  int z_fp32;
+  double *H;                     // rhs r: H + r*hstride, (max_iter+1) x max_iter col-major
+  long long hstride;
+  double *cs, *sn;               // r * (max_iter + 1)
+  double *g, *y, *hist;          // r * (max_iter + 2)
+  double *partials;              // r * pstride, pstride = nblk * (max_iter + 2)
+  long long pstride;
+  unsigned int *counter;         // R last-block counters
+  double *scal;                  // 8 per rhs
+  SolveState *st;
+  RhsState *rs;                  // R
+  int nblk, R, max_iter;
+  long long N;
 };
 
 int reduce_blocks(long long N);
-void launch_dot(const double *x, const double *y, long long N, const KrylovWs &ws, double *out,
-                cudaStream_t s);
-void launch_init_solve(const KrylovWs &ws, const double *r, cudaGraphConditionalHandle cond,
-                       int has_cond, cudaStream_t s);
+void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
+                       cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
 void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s);
 void launch_givens(const KrylovWs &ws, cudaGraphConditionalHandle cond, int has_cond,
                    cudaStream_t s);
@@ -200,6 +215,5 @@ void launch_residual_norm(const KrylovWs &ws, const double *b, const double *Ax,
                           cudaStream_t s);
 void launch_axpby(const double *x, const double *y, double a, double b, double *out, long long N,
                   cudaStream_t s);
-void launch_convert_f32(const float *x, double *out, long long N, cudaStream_t s);
 
 }  // namespace iga

@@ -4,6 +4,8 @@
 // product with W^T writes out[r + M c] = sum_k A[r][k] W[k][c].  The output's
 // fastest index is therefore (i_2, i_3) and the next mode product again contracts
 // the contiguous index.  After d products the original order is restored.
+// Several right-hand sides stacked as the slowest index stay slowest: with
+// P = rows per right-hand side, row = rl + P r writes out[rl + P (c + n r)].
 // The diagonal solve of (sum_l I (x) D_l (x) I) is fused into the epilogue of the
 // d-th forward product.
 #include "iga_internal.h"
@@ -15,7 +17,7 @@ constexpr int kTM = 32, kTN = 64, kKC = 32, kThreads = 256;
 template <class Tout>
 __global__ void __launch_bounds__(kThreads)
     gemm_fp64_kernel(IdxPtr<const double> Ap, const double *__restrict__ Bt, IdxPtr<Tout> Op,
-                     int M, int N, int K, FdScale sc, int has_scale) {
+                     int M, int N, int K, int rows_per, FdScale sc, int has_scale) {
   __shared__ double As[kTM][kKC + 1];
   __shared__ double Bs[kTN][kKC + 1];
   const double *__restrict__ A = Ap.get();
@@ -66,13 +68,14 @@ __global__ void __launch_bounds__(kThreads)
       for (int q = 0; q < 4; ++q) {
         const int row = row0 + 4 * rg + q;
         if (4 * rg + q < tm) {
+          const int rl = row % rows_per, rr = row / rows_per;
           double v = acc[j][q];
           if (has_scale) {
-            double den = sc.lam_r0[row % sc.n0] + sc.lam_c[col];
-            if (sc.lam_r1) den += sc.lam_r1[row / sc.n0];
+            double den = sc.lam_r0[rl % sc.n0] + sc.lam_c[col];
+            if (sc.lam_r1) den += sc.lam_r1[rl / sc.n0];
             v = v / den;
           }
-          O[row + (long long)M * col] = (Tout)v;
+          O[rl + (long long)rows_per * (col + (long long)N * rr)] = (Tout)v;
         }
       }
     }
@@ -81,16 +84,17 @@ __global__ void __launch_bounds__(kThreads)
 
 template <class Tout>
 void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out, int M, int N,
-                      int K, const FdScale *scale, cudaStream_t s) {
+                      int K, const FdScale *scale, cudaStream_t s, int nrhs) {
   dim3 grid((M + kTM - 1) / kTM, (N + kTN - 1) / kTN);
   FdScale sc = scale ? *scale : FdScale{nullptr, nullptr, nullptr, 1};
-  gemm_fp64_kernel<Tout><<<grid, kThreads, 0, s>>>(A, Bt, out, M, N, K, sc, scale ? 1 : 0);
+  gemm_fp64_kernel<Tout><<<grid, kThreads, 0, s>>>(A, Bt, out, M, N, K, M / nrhs, sc,
+                                                   scale ? 1 : 0);
   IGA_LAUNCH_CHECK();
 }
 
 template void launch_gemm_fp64<double>(IdxPtr<const double>, const double *, IdxPtr<double>, int,
-                                       int, int, const FdScale *, cudaStream_t);
+                                       int, int, const FdScale *, cudaStream_t, int);
 template void launch_gemm_fp64<float>(IdxPtr<const double>, const double *, IdxPtr<float>, int,
-                                      int, int, const FdScale *, cudaStream_t);
+                                      int, int, const FdScale *, cudaStream_t, int);
 
 }  // namespace iga

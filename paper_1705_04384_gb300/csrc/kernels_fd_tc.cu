@@ -158,7 +158,7 @@ struct TcEpi {
   int tf32_round;   // round FP32 outputs to TF32 (operands of the next TF32 product)
   int n;            // extent of the fastest component of a row index
   int ld_out;       // stride of that component in the output
-  int nmid;         // M / n
+  int nmid;         // rows per right-hand side / n  (n^{d-2})
   const double *lam_r0, *lam_r1, *lam_c;  // FD diagonal (lam_r0 == nullptr: none)
   int *err;
 };
@@ -236,15 +236,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) atomicExch(epi.err, 3);
   } else {
     tc_fence_after();
+    // row = a + n (m + nmid r): a = fastest component, m = middle, r = right-hand side;
+    // output index a + ld_out (m + nmid col + nmid N r) keeps r slowest
     const int row = m0 + warp * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     long long obase = 0;
     double rsc = 0.0;
     if (row < M) {
-      obase = (long long)(row % epi.n) + (long long)epi.ld_out * (row / epi.n);
+      const int a = row % epi.n, rest = row / epi.n;
+      const int m = rest % epi.nmid, rr = rest / epi.nmid;
+      obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
       if (epi.lam_r0) {
-        rsc = epi.lam_r0[row % epi.n];
-        if (epi.lam_r1) rsc += epi.lam_r1[row / epi.n];
+        rsc = epi.lam_r0[a];
+        if (epi.lam_r1) rsc += epi.lam_r1[m];
       }
     }
     const long long cstride = (long long)epi.ld_out * epi.nmid;
@@ -295,7 +299,8 @@ __global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, long 
 
 // ------------------------------------------------------------------ host side
 struct TcFd {
-  int d = 0, n = 0, prec = 0, kpad = 0, M = 0;
+  int d = 0, n = 0, prec = 0, kpad = 0, M = 0;  // M = rows of one right-hand side (n^{d-1})
+  int R_max = 1;
   int esize = 4, n_tile = 0, n_ntiles = 0, tmem_cols = 0;
   size_t smem = 0;
   uint32_t idesc = 0;
@@ -337,7 +342,7 @@ static void make_map(CUtensorMap &m, const void *base, int elem_bf16, long long 
     throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
 }
 
-TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s) {
+TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s, int R_max) {
   auto *t = new TcFd();
   try {
     t->d = d;
@@ -349,6 +354,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s)
     long long M = 1;
     for (int l = 0; l < d - 1; ++l) M *= n;
     t->M = (int)M;
+    t->R_max = R_max;
     t->n_tile = n <= 256 ? (n + 15) / 16 * 16 : 128;
     t->n_ntiles = (n + t->n_tile - 1) / t->n_tile;
     t->tmem_cols = 32;
@@ -358,7 +364,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s)
     const uint32_t fmt = bf ? 1u : 2u;
     t->idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(t->n_tile >> 3) << 17) |
                ((uint32_t)(kTileM >> 4) << 24);
-    const size_t bytes = (size_t)M * t->kpad * t->esize;
+    const size_t bytes = (size_t)R_max * M * t->kpad * t->esize;
     t->P0.alloc(bytes);
     t->Ta.alloc(bytes);
     t->Tb.alloc(bytes);
@@ -367,20 +373,25 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s)
     IGA_CUDA_TRY(cudaMemsetAsync(t->Tb.ptr, 0, bytes, s));
     t->err.alloc(1);
     IGA_CUDA_TRY(cudaMemsetAsync(t->err.ptr, 0, sizeof(int), s));
-    make_map(t->mapP0, t->P0.ptr, bf, n, M, t->kpad, kTileM);
-    make_map(t->mapTa, t->Ta.ptr, bf, n, M, t->kpad, kTileM);
-    make_map(t->mapTb, t->Tb.ptr, bf, n, M, t->kpad, kTileM);
+    make_map(t->mapP0, t->P0.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
+    make_map(t->mapTa, t->Ta.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
+    make_map(t->mapTb, t->Tb.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
     const void *vt = bf ? (const void *)f.d_Vt16.ptr : (const void *)f.d_Vt32.ptr;
     const void *u = bf ? (const void *)f.d_U16.ptr : (const void *)f.d_U32.ptr;
     make_map(t->mapVt, vt, bf, n, n, f.kpad, t->n_tile);
     make_map(t->mapU, u, bf, n, n, f.kpad, t->n_tile);
     t->lam = f.d_lam.ptr;
-    if (bf) {
-      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)t->smem));
-    } else {
-      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)t->smem));
+    // One process-wide limit, the largest any tile shape needs: the attribute belongs
+    // to the kernel, not to this problem, so a smaller per-problem value would
+    // invalidate launches already captured by other problems.
+    static bool smem_set = false;
+    if (!smem_set) {
+      const int max_smem = 1024 + kStages * (kTileM * 128 + 256 * 128);
+      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+      smem_set = true;
     }
     IGA_CUDA_TRY(cudaStreamSynchronize(s));
   } catch (...) {
@@ -392,23 +403,26 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s)
 
 void destroy_tc_fd(TcFd *fd) { delete fd; }
 
-static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi,
+static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi, int R,
                  cudaStream_t s) {
-  dim3 grid((t.M + kTileM - 1) / kTileM, t.n_ntiles);
+  const int M = R * t.M;
+  dim3 grid((M + kTileM - 1) / kTileM, t.n_ntiles);
   if (t.prec == IGA_PREC_BF16)
-    tc_gemm_kernel<1><<<grid, kTcThreads, t.smem, s>>>(A, B, t.M, t.n, t.n, t.n_tile, t.tmem_cols,
+    tc_gemm_kernel<1><<<grid, kTcThreads, t.smem, s>>>(A, B, M, t.n, t.n, t.n_tile, t.tmem_cols,
                                                        t.idesc, epi);
   else
-    tc_gemm_kernel<0><<<grid, kTcThreads, t.smem, s>>>(A, B, t.M, t.n, t.n, t.n_tile, t.tmem_cols,
+    tc_gemm_kernel<0><<<grid, kTcThreads, t.smem, s>>>(A, B, M, t.n, t.n, t.n_tile, t.tmem_cols,
                                                        t.idesc, epi);
   IGA_LAUNCH_CHECK();
 }
 
 // The chain pack -> d forward products (the d-th fused with the FD diagonal) -> d
 // inverse products; the last writes `final` (fp32 or fp64, unpadded, step-indexed).
-static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, cudaStream_t s) {
+static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, int R,
+                  cudaStream_t s) {
+  if (R < 1 || R > t.R_max) throw Error{IGA_ERR_INVALID_ARG, "too many right-hand sides"};
   const bool bf = t.prec == IGA_PREC_BF16;
-  const long long N = (long long)t.M * t.n;
+  const long long N = (long long)R * t.M * t.n;
   const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
   if (bf)
     pack_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(in, (__nv_bfloat16 *)t.P0.ptr, N, t.n, t.kpad);
@@ -446,7 +460,7 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, cuda
       e.lam_r1 = t.d == 3 ? t.lam : nullptr;
       e.lam_c = t.lam;
     }
-    gemm(t, *cur, B, e, s);
+    gemm(t, *cur, B, e, R, s);
     if (g != total - 1) {
       cur = maps[which];
       which ^= 1;
@@ -454,7 +468,7 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, cuda
   }
 }
 
-void tc_fd_apply(TcFd &t, IdxPtr<const double> in, IdxPtr<float> out, cudaStream_t s) {
+void tc_fd_apply(TcFd &t, IdxPtr<const double> in, IdxPtr<float> out, int R, cudaStream_t s) {
   TcEpi e{};
   e.out = out.base;
   e.oidx = out.idx;
@@ -467,10 +481,10 @@ void tc_fd_apply(TcFd &t, IdxPtr<const double> in, IdxPtr<float> out, cudaStream
   e.nmid = t.M / t.n;
   e.err = t.err.ptr;
   if (out.idx && out.off) throw Error{IGA_ERR_INVALID_ARG, "unsupported output offset"};
-  chain(t, in, e, s);
+  chain(t, in, e, R, s);
 }
 
-void tc_fd_apply_f64out(TcFd &t, IdxPtr<const double> in, double *out, cudaStream_t s) {
+void tc_fd_apply_f64out(TcFd &t, IdxPtr<const double> in, double *out, int R, cudaStream_t s) {
   TcEpi e{};
   e.out = out;
   e.kind = kOutF64;
@@ -478,7 +492,7 @@ void tc_fd_apply_f64out(TcFd &t, IdxPtr<const double> in, double *out, cudaStrea
   e.ld_out = t.n;
   e.nmid = t.M / t.n;
   e.err = t.err.ptr;
-  chain(t, in, e, s);
+  chain(t, in, e, R, s);
 }
 
 int *tc_fd_error_word(TcFd &t) { return t.err.ptr; }

@@ -180,8 +180,9 @@ template <class Tin, int W>
 __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, double *out0,
                                                         double *out1, double *out2, int ord0,
                                                         int ord1, int ord2, int nout, int dir,
-                                                        int n1, int n2, int n3, BandDev b) {
-  const long long N = (long long)n1 * n2 * n3;
+                                                        int n1, int n2, int n3, int nrhs,
+                                                        BandDev b) {
+  const long long N = (long long)n1 * n2 * n3 * nrhs;
   const Tin *in = inp.get();
   const long long stride = dir == 0 ? 1 : (dir == 1 ? n1 : (long long)n1 * n2);
   const double *bands[3] = {b.band0, b.band1, b.band2};
@@ -189,7 +190,8 @@ __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, d
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const int c = dir == 0 ? (int)(i % n1)
-                           : (dir == 1 ? (int)((i / n1) % n2) : (int)(i / ((long long)n1 * n2)));
+                           : (dir == 1 ? (int)((i / n1) % n2)
+                                       : (int)((i / ((long long)n1 * n2)) % n3));
     const int st = __ldg(b.start + c);
     const Tin *src = in + i + (long long)(st - c) * stride;
     double v[W];
@@ -218,15 +220,16 @@ static int grid_for(long long N, int threads) {
 
 template <class Tin>
 void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orders, int nout,
-                      int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s) {
-  const long long N = (long long)n1 * n2 * n3;
+                      int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
+                      int nrhs) {
+  const long long N = (long long)n1 * n2 * n3 * nrhs;
   const int threads = 256, blocks = grid_for(N, threads);
   double *o0 = outs[0], *o1 = nout > 1 ? outs[1] : nullptr, *o2 = nout > 2 ? outs[2] : nullptr;
   const int r0 = orders[0], r1 = nout > 1 ? orders[1] : 0, r2 = nout > 2 ? orders[2] : 0;
 #define IGA_BAND_CASE(WW)                                                                     \
   case WW:                                                                                    \
     band_pass_kernel<Tin, WW><<<blocks, threads, 0, s>>>(in, o0, o1, o2, r0, r1, r2, nout, dir, \
-                                                         n1, n2, n3, b);                      \
+                                                         n1, n2, n3, nrhs, b);                \
     break;
   switch (b.W) {
     IGA_BAND_CASE(3)
@@ -242,14 +245,6 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
 }
 
 // ------------------------------------------------------------------ contraction pass
-struct ContractArgs {
-  IdxPtr<const double> in[6];
-  int term_input[kMaxFields];
-  int term_order[kMaxFields];
-  const double *term_coef[kMaxFields];
-  int nterm;
-};
-
 template <class Tin> struct ContractArgsT {
   IdxPtr<const Tin> in[6];
   int term_input[kMaxFields];
@@ -260,8 +255,10 @@ template <class Tin> struct ContractArgsT {
 
 template <class Tin, int W>
 __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a, double *out,
-                                                            int n1, int n2, int n3, BandDev b) {
-  const long long N = (long long)n1 * n2 * n3;
+                                                            int n1, int n2, int n3, int nrhs,
+                                                            BandDev b) {
+  const long long N1 = (long long)n1 * n2 * n3;
+  const long long N = N1 * nrhs;
   const double *bands[3] = {b.band0, b.band1, b.band2};
   const Tin *ins[6];
 #pragma unroll
@@ -278,7 +275,7 @@ __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a
       double s = 0.0;
 #pragma unroll
       for (int q = 0; q < W; ++q) s = fma(__ldg(B + q), ld_val(src + q), s);
-      acc = fma(__ldg(a.term_coef[t] + i), s, acc);
+      acc = fma(__ldg(a.term_coef[t] + i % N1), s, acc);
     }
     out[i] = acc;
   }
@@ -286,7 +283,8 @@ __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a
 
 template <class Tin>
 void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *terms, int nterm,
-                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s) {
+                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
+                          int nrhs) {
   ContractArgsT<Tin> a{};
   int maxin = 0;
   for (int t = 0; t < nterm; ++t) {
@@ -297,11 +295,11 @@ void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *term
   }
   for (int q = 0; q < 6; ++q) a.in[q] = q < maxin ? ins[q] : IdxPtr<const Tin>{nullptr, nullptr, 0, 0};
   a.nterm = nterm;
-  const long long N = (long long)n1 * n2 * n3;
+  const long long N = (long long)n1 * n2 * n3 * nrhs;
   const int threads = 256, blocks = grid_for(N, threads);
-#define IGA_CON_CASE(WW)                                                                  \
-  case WW:                                                                                \
-    contract_pass_kernel<Tin, WW><<<blocks, threads, 0, s>>>(a, out, n1, n2, n3, b);      \
+#define IGA_CON_CASE(WW)                                                                   \
+  case WW:                                                                                 \
+    contract_pass_kernel<Tin, WW><<<blocks, threads, 0, s>>>(a, out, n1, n2, n3, nrhs, b); \
     break;
   switch (b.W) {
     IGA_CON_CASE(3)
@@ -317,13 +315,15 @@ void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *term
 }
 
 template void launch_band_pass<double>(IdxPtr<const double>, double *const *, const int *, int,
-                                       int, int, int, int, const BandDev &, cudaStream_t);
+                                       int, int, int, int, const BandDev &, cudaStream_t, int);
 template void launch_band_pass<float>(IdxPtr<const float>, double *const *, const int *, int, int,
-                                      int, int, int, const BandDev &, cudaStream_t);
+                                      int, int, int, const BandDev &, cudaStream_t, int);
 template void launch_contract_pass<double>(IdxPtr<const double> const *, const ContractTerm *, int,
-                                           double *, int, int, int, const BandDev &, cudaStream_t);
+                                           double *, int, int, int, const BandDev &, cudaStream_t,
+                                           int);
 template void launch_contract_pass<float>(IdxPtr<const float> const *, const ContractTerm *, int,
-                                          double *, int, int, int, const BandDev &, cudaStream_t);
+                                          double *, int, int, int, const BandDev &, cudaStream_t,
+                                          int);
 
 // ------------------------------------------------------------------ max |field|
 __global__ void field_maxabs_kernel(const double *fields, long long ldf, long long N, int nf,

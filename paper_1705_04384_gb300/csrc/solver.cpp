@@ -1,6 +1,9 @@
 // Host orchestration: setup of a problem, the matrix-free operator plan, the FD
 // chain of mode products, and GMRES as one CUDA graph whose Arnoldi loop is a
-// device-side `while` conditional node (the Givens kernel ends the loop).
+// device-side `while` conditional node (the Givens kernel ends the loop).  R right-
+// hand sides of one problem iterate in lockstep in the same graph: their vectors are
+// stacked as the slowest index, so every operator pass and FD mode product serves all
+// of them in one launch (coefficients and factors are read once for all R).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,11 +16,21 @@
 namespace iga {
 
 Ctx::~Ctx() {
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
+  if (pending && done_ev) cudaEventSynchronize(done_ev);
+  drop_graphs();
+  if (done_ev) cudaEventDestroy(done_ev);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (h_st) cudaFreeHost(h_st);
+  if (h_rs) cudaFreeHost(h_rs);
   if (h_hist) cudaFreeHost(h_hist);
+}
+
+void Ctx::drop_graphs() {
+  for (auto &kv : graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  graphs.clear();
 }
 
 // ------------------------------------------------------------------ setup
@@ -35,6 +48,7 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   band = BandDev{fac->d_start.ptr, fac->d_band[0].ptr, fac->d_band[1].ptr, fac->d_band[2].ptr, n,
                  fac->W};
   IGA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  IGA_CUDA_TRY(cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
 
   // geometry coefficient fields at the collocation points
   const int nf = num_fields(d);
@@ -92,27 +106,42 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
     }
     plan.terms[plan.nterm++] = ContractTerm{input, fd.order[0], fields.ptr + active[a] * ldf};
   }
-  op_scratch.alloc((size_t)(plan.nA + plan.nB) * N);
-  fd_scratch.alloc(2 * (size_t)N);
-  b.alloc(N);
-  x.alloc(N);
-  x0.alloc(N);
-  w.alloc(N);
-  r.alloc(N);
-  if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16)
-    tc.reset(make_tc_fd(d, n, prec, *fac, stream));
+  ensure_capacity(1);
   IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+}
+
+// Buffers whose size scales with the number of right-hand sides.
+void Ctx::ensure_capacity(int R) {
+  if (R <= R_max) return;
+  if (pending) throw Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
+  drop_graphs();
+  ws_max_iter = 0;  // the Krylov workspace is rebuilt for the new capacity
+  ws_R = 0;
+  op_scratch.alloc((size_t)(plan.nA + plan.nB) * R * N);
+  fd_scratch.alloc(2 * (size_t)R * N);
+  b.alloc((size_t)R * N);
+  x.alloc((size_t)R * N);
+  x0.alloc((size_t)R * N);
+  w.alloc((size_t)R * N);
+  r.alloc((size_t)R * N);
+  if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) {
+    tc.reset();
+    R_max = 0;  // until the new tensor-core context exists
+    tc.reset(make_tc_fd(d, n, prec, *fac, stream, R));
+  }
+  R_max = R;
 }
 
 // ------------------------------------------------------------------ operator
 template <class Tin>
-void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, cudaStream_t s) {
+void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t s) {
   double *TA[3], *TB[6];
-  for (int q = 0; q < plan.nA; ++q) TA[q] = op_scratch.ptr + (size_t)q * N;
-  for (int q = 0; q < plan.nB; ++q) TB[q] = op_scratch.ptr + (size_t)(plan.nA + q) * N;
+  const size_t blk = (size_t)R * N;
+  for (int q = 0; q < plan.nA; ++q) TA[q] = op_scratch.ptr + q * blk;
+  for (int q = 0; q < plan.nB; ++q) TB[q] = op_scratch.ptr + (plan.nA + q) * blk;
   const int n3 = d == 3 ? n : 1;
   // first pass along the slowest direction (d-1) reads the input
-  launch_band_pass<Tin>(in, TA, plan.ordA, plan.nA, d - 1, n, n, n3, band, s);
+  launch_band_pass<Tin>(in, TA, plan.ordA, plan.nA, d - 1, n, n, n3, band, s, R);
   IdxPtr<const double> ins[6];
   if (d == 2) {
     for (int q = 0; q < plan.nA; ++q) ins[q] = plain_ptr<const double>(TA[q]);
@@ -128,131 +157,148 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, cudaStream_t s) {
         }
       if (cnt)
         launch_band_pass<double>(plain_ptr<const double>(TA[a]), outs, ords, cnt, 1, n, n, n3,
-                                 band, s);
+                                 band, s, R);
     }
     for (int q = 0; q < plan.nB; ++q) ins[q] = plain_ptr<const double>(TB[q]);
   }
-  launch_contract_pass<double>(ins, plan.terms, plan.nterm, out, n, n, n3, band, s);
+  launch_contract_pass<double>(ins, plan.terms, plan.nterm, out, n, n, n3, band, s, R);
 }
 
-template void Ctx::apply_operator<double>(IdxPtr<const double>, double *, cudaStream_t);
-template void Ctx::apply_operator<float>(IdxPtr<const float>, double *, cudaStream_t);
+template void Ctx::apply_operator<double>(IdxPtr<const double>, double *, int, cudaStream_t);
+template void Ctx::apply_operator<float>(IdxPtr<const float>, double *, int, cudaStream_t);
 
 // ------------------------------------------------------------------ FD (FP64)
 template <class Tout>
-static void fd_chain_fp64(const Ctx &c, IdxPtr<const double> in, IdxPtr<Tout> out, cudaStream_t s) {
+static void fd_chain_fp64(const Ctx &c, IdxPtr<const double> in, IdxPtr<Tout> out, int R,
+                          cudaStream_t s) {
   const Factor1D &f = *c.fac;
   const int n = c.n;
-  double *t0 = c.fd_scratch.ptr, *t1 = c.fd_scratch.ptr + c.N;
-  const int M = (int)(c.N / n);
+  double *t0 = c.fd_scratch.ptr, *t1 = c.fd_scratch.ptr + (size_t)R * c.N;
+  const int M = (int)(R * (c.N / n));
   auto P = [](double *p) { return plain_ptr<double>(p); };
   auto Pc = [](const double *p) { return plain_ptr<const double>(p); };
   if (c.d == 2) {
     FdScale sc{f.d_lam.ptr, nullptr, f.d_lam.ptr, n};
-    launch_gemm_fp64<double>(in, f.d_Vt.ptr, P(t0), M, n, n, nullptr, s);
-    launch_gemm_fp64<double>(Pc(t0), f.d_Vt.ptr, P(t1), M, n, n, &sc, s);
-    launch_gemm_fp64<double>(Pc(t1), f.d_U.ptr, P(t0), M, n, n, nullptr, s);
-    launch_gemm_fp64<Tout>(Pc(t0), f.d_U.ptr, out, M, n, n, nullptr, s);
+    launch_gemm_fp64<double>(in, f.d_Vt.ptr, P(t0), M, n, n, nullptr, s, R);
+    launch_gemm_fp64<double>(Pc(t0), f.d_Vt.ptr, P(t1), M, n, n, &sc, s, R);
+    launch_gemm_fp64<double>(Pc(t1), f.d_U.ptr, P(t0), M, n, n, nullptr, s, R);
+    launch_gemm_fp64<Tout>(Pc(t0), f.d_U.ptr, out, M, n, n, nullptr, s, R);
   } else {
     FdScale sc{f.d_lam.ptr, f.d_lam.ptr, f.d_lam.ptr, n};
-    launch_gemm_fp64<double>(in, f.d_Vt.ptr, P(t0), M, n, n, nullptr, s);
-    launch_gemm_fp64<double>(Pc(t0), f.d_Vt.ptr, P(t1), M, n, n, nullptr, s);
-    launch_gemm_fp64<double>(Pc(t1), f.d_Vt.ptr, P(t0), M, n, n, &sc, s);
-    launch_gemm_fp64<double>(Pc(t0), f.d_U.ptr, P(t1), M, n, n, nullptr, s);
-    launch_gemm_fp64<double>(Pc(t1), f.d_U.ptr, P(t0), M, n, n, nullptr, s);
-    launch_gemm_fp64<Tout>(Pc(t0), f.d_U.ptr, out, M, n, n, nullptr, s);
+    launch_gemm_fp64<double>(in, f.d_Vt.ptr, P(t0), M, n, n, nullptr, s, R);
+    launch_gemm_fp64<double>(Pc(t0), f.d_Vt.ptr, P(t1), M, n, n, nullptr, s, R);
+    launch_gemm_fp64<double>(Pc(t1), f.d_Vt.ptr, P(t0), M, n, n, &sc, s, R);
+    launch_gemm_fp64<double>(Pc(t0), f.d_U.ptr, P(t1), M, n, n, nullptr, s, R);
+    launch_gemm_fp64<double>(Pc(t1), f.d_U.ptr, P(t0), M, n, n, nullptr, s, R);
+    launch_gemm_fp64<Tout>(Pc(t0), f.d_U.ptr, out, M, n, n, nullptr, s, R);
   }
 }
 
-void Ctx::precond(IdxPtr<const double> in, double *out, cudaStream_t s) {
+void Ctx::precond(IdxPtr<const double> in, double *out, int R, cudaStream_t s) {
+  ensure_capacity(R);
   if (prec == IGA_PREC_NONE) {
     throw Error{IGA_ERR_INVALID_ARG, "precond on an unpreconditioned handle"};
   } else if (prec == IGA_PREC_FP64) {
-    fd_chain_fp64<double>(*this, in, plain_ptr<double>(out), s);
+    fd_chain_fp64<double>(*this, in, plain_ptr<double>(out), R, s);
   } else {
-    tc_fd_apply_f64out(*tc, in, out, s);
+    if (!tc) throw Error{IGA_ERR_CUDA, "tensor-core FD context missing"};
+    tc_fd_apply_f64out(*tc, in, out, R, s);
   }
 }
 
 // ------------------------------------------------------------------ Krylov workspace
-void Ctx::ensure_ws(int max_iter) {
-  if (max_iter <= ws_max_iter) return;
-  const long long ld = (N + 31) / 32 * 32;
+void Ctx::ensure_ws(int max_iter, int R) {
+  ensure_capacity(R);
+  if (max_iter <= ws_max_iter && R <= ws_R) {
+    ws.R = R;
+    return;
+  }
+  if (pending) throw Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
+  drop_graphs();
+  const int mi = std::max(max_iter, ws_max_iter);
+  const int Rc = std::max(R_max, std::max(R, ws_R));
   const int nblk = reduce_blocks(N);
-  V.alloc((size_t)(max_iter + 1) * ld);
-  if (prec == IGA_PREC_FP64) Zd.alloc((size_t)max_iter * ld);
-  if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) Zf.alloc((size_t)max_iter * ld);
-  H.alloc((size_t)(max_iter + 1) * max_iter);
-  cs.alloc(max_iter + 1);
-  sn.alloc(max_iter + 1);
-  g.alloc(max_iter + 2);
-  y.alloc(max_iter + 2);
-  hist.alloc(max_iter + 2);
-  partials.alloc((size_t)nblk * (max_iter + 2));
-  scal.alloc(8);
-  counter.alloc(4);
+  const size_t vecs = (size_t)Rc * N;
+  V.alloc((size_t)(mi + 1) * vecs);
+  IGA_CUDA_TRY(cudaMemsetAsync(V.ptr, 0, (size_t)(mi + 1) * vecs * 8, stream));
+  if (prec == IGA_PREC_FP64) Zd.alloc((size_t)mi * vecs);
+  if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) Zf.alloc((size_t)mi * vecs);
+  const long long hstride = (long long)(mi + 1) * mi;
+  H.alloc((size_t)Rc * hstride);
+  cs.alloc((size_t)Rc * (mi + 1));
+  sn.alloc((size_t)Rc * (mi + 1));
+  g.alloc((size_t)Rc * (mi + 2));
+  y.alloc((size_t)Rc * (mi + 2));
+  hist.alloc((size_t)Rc * (mi + 2));
+  const long long pstride = (long long)nblk * (mi + 2);
+  partials.alloc((size_t)Rc * pstride);
+  scal.alloc((size_t)8 * Rc);
+  counter.alloc(Rc);
   st.alloc(1);
-  IGA_CUDA_TRY(cudaMemsetAsync(counter.ptr, 0, 4 * sizeof(unsigned int), stream));
-  IGA_CUDA_TRY(cudaMemsetAsync(H.ptr, 0, (size_t)(max_iter + 1) * max_iter * 8, stream));
-  IGA_CUDA_TRY(cudaMemsetAsync(hist.ptr, 0, (size_t)(max_iter + 2) * 8, stream));
+  rs.alloc(Rc);
+  IGA_CUDA_TRY(cudaMemsetAsync(counter.ptr, 0, Rc * sizeof(unsigned int), stream));
+  IGA_CUDA_TRY(cudaMemsetAsync(H.ptr, 0, (size_t)Rc * hstride * 8, stream));
+  IGA_CUDA_TRY(cudaMemsetAsync(hist.ptr, 0, (size_t)Rc * (mi + 2) * 8, stream));
   if (h_st) cudaFreeHost(h_st);
+  if (h_rs) cudaFreeHost(h_rs);
   if (h_hist) cudaFreeHost(h_hist);
   h_st = nullptr;
+  h_rs = nullptr;
   h_hist = nullptr;
   IGA_CUDA_TRY(cudaMallocHost(&h_st, sizeof(SolveState)));
-  IGA_CUDA_TRY(cudaMallocHost(&h_hist, (size_t)(max_iter + 2) * 8));
+  IGA_CUDA_TRY(cudaMallocHost(&h_rs, Rc * sizeof(RhsState)));
+  IGA_CUDA_TRY(cudaMallocHost(&h_hist, (size_t)Rc * (mi + 2) * 8));
   ws = KrylovWs{};
   ws.V = V.ptr;
-  ws.ldv = ld;
   if (prec == IGA_PREC_FP64) {
     ws.Z = Zd.ptr;
-    ws.ldz = ld;
     ws.z_fp32 = 0;
   } else if (prec == IGA_PREC_NONE) {
     ws.Z = V.ptr;  // P = I: z_k = v_k
-    ws.ldz = ld;
     ws.z_fp32 = 0;
   } else {
     ws.Z = Zf.ptr;
-    ws.ldz = ld;
     ws.z_fp32 = 1;
   }
   ws.H = H.ptr;
+  ws.hstride = hstride;
   ws.cs = cs.ptr;
   ws.sn = sn.ptr;
   ws.g = g.ptr;
   ws.y = y.ptr;
   ws.hist = hist.ptr;
   ws.partials = partials.ptr;
+  ws.pstride = pstride;
   ws.counter = counter.ptr;
   ws.scal = scal.ptr;
   ws.st = st.ptr;
+  ws.rs = rs.ptr;
   ws.nblk = nblk;
   ws.N = N;
-  ws.max_iter = max_iter;
-  ws_max_iter = max_iter;
-  // the graph refers to the old buffers
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
-  gexec = nullptr;
-  graph = nullptr;
-  g_max_iter = -1;
+  ws.max_iter = mi;
+  ws.R = R;
+  ws_max_iter = mi;
+  ws_R = Rc;
 }
 
 // ------------------------------------------------------------------ GMRES steps
+// (ws.R is the number of right-hand sides of the graph being built or run)
 void Ctx::launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s) {
+  const int R = ws.R;
+  const long long blk = (long long)R * N;
   const int *kptr = &ws.st->k;
-  IdxPtr<const double> vk{ws.V, kptr, 0, ws.ldv};
+  IdxPtr<const double> vk{ws.V, kptr, 0, blk};
   if (prec == IGA_PREC_NONE) {
-    apply_operator<double>(vk, w.ptr, s);
+    apply_operator<double>(vk, w.ptr, R, s);
   } else if (prec == IGA_PREC_FP64) {
-    IdxPtr<double> zk{(double *)ws.Z, kptr, 0, ws.ldz};
-    fd_chain_fp64<double>(*this, vk, zk, s);
-    apply_operator<double>(IdxPtr<const double>{(const double *)ws.Z, kptr, 0, ws.ldz}, w.ptr, s);
+    IdxPtr<double> zk{(double *)ws.Z, kptr, 0, blk};
+    fd_chain_fp64<double>(*this, vk, zk, R, s);
+    apply_operator<double>(IdxPtr<const double>{(const double *)ws.Z, kptr, 0, blk}, w.ptr, R, s);
   } else {
-    IdxPtr<float> zk{(float *)ws.Z, kptr, 0, ws.ldz};
-    tc_fd_apply(*tc, vk, zk, s);
-    apply_operator<float>(IdxPtr<const float>{(const float *)ws.Z, kptr, 0, ws.ldz}, w.ptr, s);
+    if (!tc) throw Error{IGA_ERR_CUDA, "tensor-core FD context missing"};
+    IdxPtr<float> zk{(float *)ws.Z, kptr, 0, blk};
+    tc_fd_apply(*tc, vk, zk, R, s);
+    apply_operator<float>(IdxPtr<const float>{(const float *)ws.Z, kptr, 0, blk}, w.ptr, R, s);
   }
   launch_cgs2(ws, w.ptr, s);
   launch_givens(ws, cond, has_cond, s);
@@ -260,35 +306,34 @@ void Ctx::launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaSt
 
 void Ctx::launch_solve_prologue(int use_x0, cudaGraphConditionalHandle cond, int has_cond,
                                 cudaStream_t s) {
+  const int R = ws.R;
   const double *r0 = b.ptr;
   if (use_x0) {
-    apply_operator<double>(plain_ptr<const double>(x0.ptr), w.ptr, s);
-    launch_axpby(b.ptr, w.ptr, 1.0, -1.0, r.ptr, N, s);
+    apply_operator<double>(plain_ptr<const double>(x0.ptr), w.ptr, R, s);
+    launch_axpby(b.ptr, w.ptr, 1.0, -1.0, r.ptr, (long long)R * N, s);
     r0 = r.ptr;
   }
-  launch_dot(b.ptr, b.ptr, N, ws, ws.scal + 0, s);
-  launch_dot(r0, r0, N, ws, ws.scal + 1, s);
-  launch_init_solve(ws, r0, cond, has_cond, s);
+  launch_init_solve(ws, b.ptr, r0, cond, has_cond, s);
 }
 
 void Ctx::launch_solve_epilogue(int use_x0, cudaStream_t s) {
+  const int R = ws.R;
   launch_finish(ws, x0.ptr, use_x0, x.ptr, s);
-  apply_operator<double>(plain_ptr<const double>(x.ptr), w.ptr, s);
+  apply_operator<double>(plain_ptr<const double>(x.ptr), w.ptr, R, s);
   launch_residual_norm(ws, b.ptr, w.ptr, r.ptr, s);
 }
 
-void Ctx::build_graph(int max_iter, int use_x0) {
-  // max_iter and tol live in device state, so one graph serves every solve
-  if (gexec && g_use_x0 == use_x0) return;
-  if (gexec) cudaGraphExecDestroy(gexec);
-  if (graph) cudaGraphDestroy(graph);
-  gexec = nullptr;
-  graph = nullptr;
+SolveGraph &Ctx::graph_for(int R, int use_x0) {
+  const auto key = std::make_pair(R, use_x0);
+  auto it = graphs.find(key);
+  if (it != graphs.end()) return it->second;
+  ws.R = R;
+  SolveGraph sg;
   cudaStream_t s = cap_stream;
-  IGA_CUDA_TRY(cudaGraphCreate(&graph, 0));
+  IGA_CUDA_TRY(cudaGraphCreate(&sg.graph, 0));
   cudaGraphConditionalHandle cond;
-  IGA_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
-  IGA_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
+  IGA_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, sg.graph, 1, cudaGraphCondAssignDefault));
+  IGA_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, sg.graph, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
   cudaGraph_t body = nullptr;
   const long long c0 = g_launch_count;
@@ -313,9 +358,10 @@ void Ctx::build_graph(int max_iter, int use_x0) {
   } catch (...) {
     cudaGraph_t dummy;
     cudaStreamEndCapture(s, &dummy);
+    cudaGraphDestroy(sg.graph);
     throw;
   }
-  IGA_CUDA_TRY(cudaStreamEndCapture(s, &graph));
+  IGA_CUDA_TRY(cudaStreamEndCapture(s, &sg.graph));
   const long long c1 = g_launch_count;
   IGA_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeThreadLocal));
@@ -324,14 +370,14 @@ void Ctx::build_graph(int max_iter, int use_x0) {
   } catch (...) {
     cudaGraph_t dummy;
     cudaStreamEndCapture(s, &dummy);
+    cudaGraphDestroy(sg.graph);
     throw;
   }
   IGA_CUDA_TRY(cudaStreamEndCapture(s, &body));
-  launches_fixed = (int)(c1 - c0);
-  launches_iter = (int)(g_launch_count - c1);
-  IGA_CUDA_TRY(cudaGraphInstantiate(&gexec, graph, 0));
-  g_max_iter = max_iter;
-  g_use_x0 = use_x0;
+  sg.launches_fixed = (int)(c1 - c0);
+  sg.launches_iter = (int)(g_launch_count - c1);
+  IGA_CUDA_TRY(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
+  return graphs[key] = sg;
 }
 
 static bool eager_mode() {
@@ -339,35 +385,60 @@ static bool eager_mode() {
   return e && e[0] == '1';
 }
 
-iga_status Ctx::solve(const double *rhs_dev, double *x_dev, int use_x0, double tol, int max_iter,
-                      int *iters, double *hist_out, double *relres) {
-  ensure_ws(max_iter);
+void Ctx::enqueue(int R, const double *rhs_dev, double *x_dev, int use_x0, double tol,
+                  int max_iter) {
+  if (pending) throw Error{IGA_ERR_INVALID_ARG, "a solve is already in flight on this handle"};
+  ensure_ws(max_iter, R);
   SolveState hs{};
   hs.tol = tol;
   hs.max_iter = max_iter;
+  hs.R = R;
   *h_st = hs;
+  const size_t bytes = (size_t)R * N * 8;
   IGA_CUDA_TRY(cudaMemcpyAsync(ws.st, h_st, sizeof(SolveState), cudaMemcpyHostToDevice, stream));
-  IGA_CUDA_TRY(cudaMemcpyAsync(b.ptr, rhs_dev, N * 8, cudaMemcpyDeviceToDevice, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(b.ptr, rhs_dev, bytes, cudaMemcpyDeviceToDevice, stream));
   if (use_x0)
-    IGA_CUDA_TRY(cudaMemcpyAsync(x0.ptr, x_dev, N * 8, cudaMemcpyDeviceToDevice, stream));
+    IGA_CUDA_TRY(cudaMemcpyAsync(x0.ptr, x_dev, bytes, cudaMemcpyDeviceToDevice, stream));
   if (!eager_mode()) {
-    build_graph(max_iter, use_x0);
-    IGA_CUDA_TRY(cudaGraphLaunch(gexec, stream));
+    SolveGraph &sg = graph_for(R, use_x0);
+    IGA_CUDA_TRY(cudaGraphLaunch(sg.exec, stream));
   } else {
+    ws.R = R;
     launch_solve_prologue(use_x0, 0, 0, stream);
     for (int it = 0; it <= max_iter; ++it) {
       IGA_CUDA_TRY(cudaMemcpyAsync(h_st, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream));
       IGA_CUDA_TRY(cudaStreamSynchronize(stream));
-      if (h_st->done) break;
+      if (h_st->active == 0) break;
       launch_iteration(0, 0, stream);
     }
     launch_solve_epilogue(use_x0, stream);
   }
-  IGA_CUDA_TRY(cudaMemcpyAsync(x_dev, x.ptr, N * 8, cudaMemcpyDeviceToDevice, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(x_dev, x.ptr, bytes, cudaMemcpyDeviceToDevice, stream));
   IGA_CUDA_TRY(cudaMemcpyAsync(h_st, ws.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream));
-  IGA_CUDA_TRY(cudaMemcpyAsync(h_hist, ws.hist, (size_t)(max_iter + 1) * 8,
+  IGA_CUDA_TRY(cudaMemcpyAsync(h_rs, ws.rs, R * sizeof(RhsState), cudaMemcpyDeviceToHost, stream));
+  IGA_CUDA_TRY(cudaMemcpyAsync(h_hist, ws.hist, (size_t)R * (ws_max_iter + 2) * 8,
                                cudaMemcpyDeviceToHost, stream));
-  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  IGA_CUDA_TRY(cudaEventRecord(done_ev, stream));
+  pending = true;
+  pend_R = R;
+  pend_max_iter = max_iter;
+  pend_tol = tol;
+}
+
+bool Ctx::ready() {
+  if (!pending) return true;
+  const cudaError_t e = cudaEventQuery(done_ev);
+  if (e == cudaSuccess) return true;
+  if (e == cudaErrorNotReady) return false;
+  IGA_CUDA_TRY(e);
+  return false;
+}
+
+// Per right-hand side: iters[r], hist_out[r*(max_iter+1) + j], relres[r], status_out[r].
+iga_status Ctx::collect(int *iters, double *hist_out, double *relres, int *status_out) {
+  if (!pending) throw Error{IGA_ERR_INVALID_ARG, "no solve in flight on this handle"};
+  pending = false;
+  IGA_CUDA_TRY(cudaEventSynchronize(done_ev));
   if (tc) {
     int err = 0;
     IGA_CUDA_TRY(cudaMemcpy(&err, tc_fd_error_word(*tc), sizeof(int), cudaMemcpyDeviceToHost));
@@ -377,16 +448,25 @@ iga_status Ctx::solve(const double *rhs_dev, double *x_dev, int use_x0, double t
                   "a tensor-core FD wait timed out (code " + std::to_string(err) + ")"};
     }
   }
-  const SolveState &r_ = *h_st;
-  if (iters) *iters = r_.k;
-  if (hist_out) {
-    for (int j = 0; j <= r_.k && j <= max_iter; ++j) hist_out[j] = h_hist[j];
-    for (int j = r_.k + 1; j <= max_iter; ++j) hist_out[j] = 0.0;
+  const int R = pend_R, mi = pend_max_iter;
+  iga_status overall = IGA_OK;
+  for (int q = 0; q < R; ++q) {
+    const RhsState &s = h_rs[q];
+    if (iters) iters[q] = s.kconv;
+    if (hist_out) {
+      const double *h = h_hist + (size_t)q * (ws_max_iter + 2);
+      double *o = hist_out + (size_t)q * (mi + 1);
+      for (int j = 0; j <= mi; ++j) o[j] = j <= s.kconv ? h[j] : 0.0;
+    }
+    if (relres) relres[q] = s.relres_true;
+    iga_status st_q = IGA_OK;
+    if (s.flag == 4 || !std::isfinite(s.relres_true)) st_q = IGA_ERR_NAN;
+    else if (s.flag == 2 && pend_tol > 0.0) st_q = IGA_ERR_NO_CONVERGENCE;
+    if (status_out) status_out[q] = st_q;
+    if (st_q == IGA_ERR_NAN) overall = IGA_ERR_NAN;
+    else if (st_q != IGA_OK && overall == IGA_OK) overall = st_q;
   }
-  if (relres) *relres = r_.relres_true;
-  if (r_.flag == 4 || !std::isfinite(r_.relres_true)) return IGA_ERR_NAN;
-  if (r_.flag == 2 && tol > 0.0) return IGA_ERR_NO_CONVERGENCE;
-  return IGA_OK;
+  return overall;
 }
 
 // ------------------------------------------------------------------ points (host)
@@ -401,8 +481,8 @@ void Ctx::collocation_points(double *xyz) const {
         const double xi = tau[i1], eta = tau[i2], zeta = d == 3 ? tau[i3] : 0.0;
         double P[3] = {xi, eta, zeta};
         if (geom.kind != IGA_GEOM_IDENTITY) {
-          const double r = r0 + (r1 - r0) * xi;
-          const double X = r * std::cos(w_ * eta), Y = r * std::sin(w_ * eta);
+          const double rr = r0 + (r1 - r0) * xi;
+          const double X = rr * std::cos(w_ * eta), Y = rr * std::sin(w_ * eta);
           P[0] = X;
           P[1] = Y;
           if (geom.kind == IGA_GEOM_REVOLVED_ANNULUS) {
