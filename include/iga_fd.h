@@ -223,6 +223,11 @@ iga_status iga_precond_apply_noalloc(int d, int n, const double *Vt_dev, const d
                                      const double *lam_dev, const double *b_dev, double *s_dev,
                                      void *stream);
 
+/* Allocate the Krylov workspace for nrhs right-hand sides and max_iter steps and
+ * capture the solve graph now, so that the first solve of that size does no setup.
+ * Synchronous; must not be called while a solve is in flight on the handle.  */
+iga_status iga_prepare(iga_handle h, int nrhs, int max_iter);
+
 /* Release everything the handle owns.  NULL is accepted. */
 iga_status iga_destroy(iga_handle h);
 

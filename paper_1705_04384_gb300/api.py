@@ -79,6 +79,10 @@ class Problem:
                                       out.ctypes.data_as(ctypes.c_void_p)), "iga_get_factor")
         return out
 
+    def prepare(self, nrhs=1, max_iter=200):
+        """Allocate the solve workspace and capture the solve graph ahead of time."""
+        check(self.lib.iga_prepare(self.h, int(nrhs), int(max_iter)), "iga_prepare")
+
     def launch_counts(self):
         """(fixed, per_iteration): kernel launches of one solve = fixed + per_iteration * iters."""
         f, it = ctypes.c_int(), ctypes.c_int()

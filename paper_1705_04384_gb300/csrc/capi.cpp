@@ -257,6 +257,19 @@ iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration) {
   });
 }
 
+iga_status iga_prepare(iga_handle h, int nrhs, int max_iter) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    check_solve_args(nrhs, max_iter, 0.0);
+    iga::Ctx &c = h->c;
+    if (c.pending) throw iga::Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
+    c.ensure_ws(max_iter, nrhs);
+    c.graph_for(nrhs, 0);
+    IGA_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return IGA_OK;
+  });
+}
+
 iga_status iga_destroy(iga_handle h) {
   return guarded([&]() -> iga_status {
     delete h;

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -109,6 +110,19 @@ struct Factor1D {
 
 std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream);
 void build_basis_1d(Factor1D &f);  // host part (knots, tau, bands)
+
+// Operations that touch device-wide state -- stream capture of a solve graph, the
+// cuSOLVER eigensolves (which load library code on first use) and kernel attribute
+// changes -- are serialized by one process-wide lock, so that setups on several host
+// threads never disturb another thread's capture.  Every kernel of the library is
+// loaded once per device before the first problem is set up, so no code is loaded
+// while a capture is in progress.
+std::mutex &device_mutex();
+void ensure_kernels_loaded();
+void preload_kernels_fd64();
+void preload_kernels_fd_tc();
+void preload_kernels_geom_op();
+void preload_kernels_krylov();
 
 // ---------------------------------------------------------------- geometry
 // Coefficient fields of L u_hat = sum_f q_f(x) * (derivative f of u_hat):

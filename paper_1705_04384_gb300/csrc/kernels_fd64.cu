@@ -97,4 +97,10 @@ template void launch_gemm_fp64<double>(IdxPtr<const double>, const double *, Idx
 template void launch_gemm_fp64<float>(IdxPtr<const double>, const double *, IdxPtr<float>, int,
                                       int, int, const FdScale *, cudaStream_t, int);
 
+void preload_kernels_fd64() {
+  cudaFuncAttributes a;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_kernel<double>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_kernel<float>));
+}
+
 }  // namespace iga

@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "context.h"
 
@@ -311,7 +312,9 @@ struct TcFd {
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static std::mutex mu;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
   if (!fn) {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -381,17 +384,22 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     make_map(t->mapVt, vt, bf, n, n, f.kpad, t->n_tile);
     make_map(t->mapU, u, bf, n, n, f.kpad, t->n_tile);
     t->lam = f.d_lam.ptr;
-    // One process-wide limit, the largest any tile shape needs: the attribute belongs
+    // One limit per device, the largest any tile shape needs: the attribute belongs
     // to the kernel, not to this problem, so a smaller per-problem value would
     // invalidate launches already captured by other problems.
-    static bool smem_set = false;
-    if (!smem_set) {
-      const int max_smem = 1024 + kStages * (kTileM * 128 + 256 * 128);
-      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-      IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-      smem_set = true;
+    {
+      static bool smem_set[64] = {};
+      int dev = 0;
+      IGA_CUDA_TRY(cudaGetDevice(&dev));
+      std::lock_guard<std::mutex> lk(device_mutex());
+      if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+        const int max_smem = 1024 + kStages * (kTileM * 128 + 256 * 128);
+        IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        smem_set[dev] = true;
+      }
     }
     IGA_CUDA_TRY(cudaStreamSynchronize(s));
   } catch (...) {
@@ -496,5 +504,13 @@ void tc_fd_apply_f64out(TcFd &t, IdxPtr<const double> in, double *out, int R, cu
 }
 
 int *tc_fd_error_word(TcFd &t) { return t.err.ptr; }
+
+void preload_kernels_fd_tc() {
+  cudaFuncAttributes a;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<0>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<1>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<float>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<__nv_bfloat16>));
+}
 
 }  // namespace iga

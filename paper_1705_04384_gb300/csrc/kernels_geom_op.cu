@@ -345,4 +345,26 @@ void launch_field_maxabs(const double *fields, long long ldf, long long N, int n
   IGA_LAUNCH_CHECK();
 }
 
+template <class Tin, int W> static void preload_op_w() {
+  cudaFuncAttributes a;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_kernel<Tin, W>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, contract_pass_kernel<Tin, W>));
+}
+
+void preload_kernels_geom_op() {
+  cudaFuncAttributes a;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, geometry_fields_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, field_maxabs_kernel));
+  preload_op_w<double, 3>();
+  preload_op_w<double, 4>();
+  preload_op_w<double, 5>();
+  preload_op_w<double, 6>();
+  preload_op_w<double, 7>();
+  preload_op_w<float, 3>();
+  preload_op_w<float, 4>();
+  preload_op_w<float, 5>();
+  preload_op_w<float, 6>();
+  preload_op_w<float, 7>();
+}
+
 }  // namespace iga

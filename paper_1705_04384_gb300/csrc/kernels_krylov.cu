@@ -484,4 +484,21 @@ void launch_axpby(const double *x, const double *y, double a, double b, double *
   IGA_LAUNCH_CHECK();
 }
 
+void preload_kernels_krylov() {
+  cudaFuncAttributes a;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, init_norms_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, init_finalize_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, scale_v0_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass2_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass3_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, normalize_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, givens_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, backsolve_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, update_x_kernel<double>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, update_x_kernel<float>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, residual_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, axpby_kernel));
+}
+
 }  // namespace iga

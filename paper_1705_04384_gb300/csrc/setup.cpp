@@ -437,6 +437,25 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
   IGA_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
+// ------------------------------------------------------------------ device-wide lock
+std::mutex &device_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+void ensure_kernels_loaded() {
+  static bool loaded[64] = {};
+  int dev = 0;
+  IGA_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(device_mutex());
+  if (dev < 0 || dev >= 64 || loaded[dev]) return;
+  preload_kernels_fd64();
+  preload_kernels_fd_tc();
+  preload_kernels_geom_op();
+  preload_kernels_krylov();
+  loaded[dev] = true;
+}
+
 // ------------------------------------------------------------------ factor cache
 std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream) {
   static std::mutex mu;
@@ -444,17 +463,29 @@ std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream) {
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
   const auto key = std::make_tuple(dev, n_elem, p);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      if (auto sp = it->second.lock()) return sp;
+    }
+  }
+  // computed without the lock so that setups of different shapes on different host
+  // threads overlap; if two threads race on one shape, the first to publish wins
+  auto f = std::make_shared<Factor1D>();
+  f->n_elem = n_elem;
+  f->p = p;
+  build_basis_1d(*f);
+  {
+    std::lock_guard<std::mutex> dlk(device_mutex());
+    eigen_factors(*f, stream);
+  }
+  upload_factor(*f, stream);
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it != cache.end()) {
     if (auto sp = it->second.lock()) return sp;
   }
-  auto f = std::make_shared<Factor1D>();
-  f->n_elem = n_elem;
-  f->p = p;
-  build_basis_1d(*f);
-  eigen_factors(*f, stream);
-  upload_factor(*f, stream);
   cache[key] = f;
   return f;
 }

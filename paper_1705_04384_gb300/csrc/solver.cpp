@@ -41,6 +41,7 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   geom = g_;
   prec = prec_;
   stream = s_;
+  ensure_kernels_loaded();
   fac = get_factor(n_elem, p, stream);
   n = fac->n;
   N = 1;
@@ -327,6 +328,7 @@ SolveGraph &Ctx::graph_for(int R, int use_x0) {
   const auto key = std::make_pair(R, use_x0);
   auto it = graphs.find(key);
   if (it != graphs.end()) return it->second;
+  std::lock_guard<std::mutex> dlk(device_mutex());
   ws.R = R;
   SolveGraph sg;
   cudaStream_t s = cap_stream;
