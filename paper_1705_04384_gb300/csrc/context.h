@@ -14,7 +14,8 @@ void launch_field_maxabs(const double *fields, long long ldf, long long N, int n
 
 // tcgen05 FD (TF32 / BF16) -- defined in kernels_fd_tc.cu
 struct TcFd;
-TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s, int R_max);
+TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s, int R_max,
+                 const float *dinv32);
 void tc_fd_apply(TcFd &fd, IdxPtr<const double> in, IdxPtr<float> out, int R, cudaStream_t s);
 void tc_fd_apply_f64out(TcFd &fd, IdxPtr<const double> in, double *out, int R, cudaStream_t s);
 void destroy_tc_fd(TcFd *fd);
@@ -55,6 +56,8 @@ struct Ctx {
   int nactive = 0;
   double field_maxabs[kMaxFields] = {};
   OpPlan plan;
+  DevBuf<double> dinv;   // reciprocal FD diagonal 1/(lambda_i + mu_j (+ nu_k)), DOF order
+  DevBuf<float> dinv32;  // the same in FP32 (tensor-core FD)
 
   // buffers sized for R_max right-hand sides
   int R_max = 0;

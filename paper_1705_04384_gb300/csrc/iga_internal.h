@@ -106,7 +106,18 @@ struct Factor1D {
   DevBuf<__nv_bfloat16> d_Vt16, d_U16;
   int kpad = 0;                 // padded leading dimension for the TC operands
   double cond_U = 0.0;
+  // Folded form of the FD factors (eigenvectors even or odd under i -> n-1-i): the
+  // eigen-index reordered [even | odd], Bf (n x n, forward, block diagonal in the
+  // folded basis), Bi (ne x n, inverse, pairs a / n-1-a), eigenvalues in that order.
+  bool folded = false;
+  int ne = 0;
+  DevBuf<double> d_Bf, d_Bi, d_lam_fold;
 };
+
+struct FdScale;
+template <class Tout>
+void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
+                           int M, int n, int ne, const FdScale *scale, cudaStream_t s, int nrhs);
 
 std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream);
 void build_basis_1d(Factor1D &f);  // host part (knots, tau, bands)
@@ -170,10 +181,19 @@ void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *term
 //   out[r + M*c] (+scale) = sum_k A[r*K + k] * Bt[c*K + k],  r < M, c < N(=K).
 // If lam != nullptr the result is divided by lam0[r % n0] + lam1[(r / n0) % n1] + lamc[c]
 // (the FD diagonal, eq. FD2D / FD3D).
+// The FD diagonal solve fused into a GEMM epilogue: either multiply by the
+// precomputed reciprocal diagonal dinv (indexed like one right-hand side's output,
+// i.e. the original DOF order), or divide by lam_r0[rl % n0] (+ lam_r1[rl / n0]) +
+// lam_c[col] when dinv is null.
 struct FdScale {
   const double *lam_r0, *lam_r1, *lam_c;  // lam_r1 may be null (2D)
   int n0;
+  const double *dinv = nullptr;
 };
+// dinv[i] = 1 / (lambda_{i1} + lambda_{i2} (+ lambda_{i3})) for i in DOF order, in FP64
+// and (if dinv32 != nullptr) FP32.
+void launch_fd_diag_inverse(const double *lam, int n, int d, double *dinv, float *dinv32,
+                            cudaStream_t s);
 // nrhs right-hand sides stacked as the slowest index (M = nrhs * rows per rhs).
 template <class Tout>
 void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out, int M, int N,

@@ -160,7 +160,7 @@ struct TcEpi {
   int n;            // extent of the fastest component of a row index
   int ld_out;       // stride of that component in the output
   int nmid;         // rows per right-hand side / n  (n^{d-2})
-  const double *lam_r0, *lam_r1, *lam_c;  // FD diagonal (lam_r0 == nullptr: none)
+  const float *dinv;  // reciprocal FD diagonal in DOF order (nullptr: no scaling)
   int *err;
 };
 
@@ -242,17 +242,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int row = m0 + warp * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     long long obase = 0;
-    double rsc = 0.0;
+    const float *dinv_row = nullptr;  // the FD diagonal in DOF order: a + n (m + nmid col)
     if (row < M) {
       const int a = row % epi.n, rest = row / epi.n;
       const int m = rest % epi.nmid, rr = rest / epi.nmid;
       obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
-      if (epi.lam_r0) {
-        rsc = epi.lam_r0[a];
-        if (epi.lam_r1) rsc += epi.lam_r1[m];
-      }
+      if (epi.dinv) dinv_row = epi.dinv + a + (long long)epi.n * m;
     }
     const long long cstride = (long long)epi.ld_out * epi.nmid;
+    const long long dstride = (long long)epi.n * epi.nmid;
     const long long off = epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0;
     for (int cc = 0; cc < n_tile; cc += 16) {
       uint32_t v[16];
@@ -263,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int col = c0 + cc + j;
           if (col < N) {
             float x = __uint_as_float(v[j]);
-            if (epi.lam_r0) x = (float)((double)x / (rsc + epi.lam_c[col]));
+            if (dinv_row) x *= __ldg(dinv_row + dstride * col);
             const long long o = off + obase + cstride * col;
             if (epi.kind == kOutF32) {
               ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
@@ -308,7 +306,7 @@ struct TcFd {
   DevBuf<uint8_t> P0, Ta, Tb;
   DevBuf<int> err;
   CUtensorMap mapP0{}, mapTa{}, mapTb{}, mapVt{}, mapU{};
-  const double *lam = nullptr;
+  const float *dinv32 = nullptr;
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
@@ -345,7 +343,8 @@ static void make_map(CUtensorMap &m, const void *base, int elem_bf16, long long 
     throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
 }
 
-TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s, int R_max) {
+TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s, int R_max,
+                 const float *dinv32) {
   auto *t = new TcFd();
   try {
     t->d = d;
@@ -383,7 +382,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     const void *u = bf ? (const void *)f.d_U16.ptr : (const void *)f.d_U32.ptr;
     make_map(t->mapVt, vt, bf, n, n, f.kpad, t->n_tile);
     make_map(t->mapU, u, bf, n, n, f.kpad, t->n_tile);
-    t->lam = f.d_lam.ptr;
+    t->dinv32 = dinv32;
     // One limit per device, the largest any tile shape needs: the attribute belongs
     // to the kernel, not to this problem, so a smaller per-problem value would
     // invalidate launches already captured by other problems.
@@ -464,9 +463,7 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, int 
       e = to(*bufs[which]);
     }
     if (g == t.d - 1) {
-      e.lam_r0 = t.lam;
-      e.lam_r1 = t.d == 3 ? t.lam : nullptr;
-      e.lam_c = t.lam;
+      e.dinv = t.dinv32;
     }
     gemm(t, *cur, B, e, R, s);
     if (g != total - 1) {

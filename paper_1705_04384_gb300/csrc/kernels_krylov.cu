@@ -21,10 +21,13 @@ constexpr int kRT = 256;  // threads per reduction block
 constexpr int kWarps = kRT / 32;
 constexpr int kJC = 8;    // vectors per register chunk
 
+// GB300 runs FP64 at 2 FMAs per SM and clock, so the FP64 work of a reduction tree
+// matters as much as that of the dot products: blocks are sized so that each thread
+// accumulates about 8 rows before any reduction, one block per SM at most.
 int reduce_blocks(long long N) {
   long long b = (N + 2047) / 2048;
   if (b < 1) b = 1;
-  if (b > 304) b = 304;
+  if (b > 152) b = 152;
   return (int)b;
 }
 
@@ -40,16 +43,41 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp reduction of 8 accumulators at once by halving exchange: at offsets 16, 8, 4
+// each lane keeps half of its remaining values and adds the partner's matching half,
+// then offsets 2 and 1 finish the sum.  9 FP64 adds per lane instead of 8 x 5.  On
+// return lane l holds the warp total of accumulator ((l>>4)&1)*4 + ((l>>3)&1)*2 +
+// ((l>>2)&1).
+__device__ __forceinline__ double warp_reduce8(const double (&a)[kJC]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double b4[4], b2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double keep = h16 ? a[q + 4] : a[q];
+    const double send = h16 ? a[q] : a[q + 4];
+    b4[q] = keep + __shfl_xor_sync(full, send, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double keep = h8 ? b4[q + 2] : b4[q];
+    const double send = h8 ? b4[q] : b4[q + 2];
+    b2[q] = keep + __shfl_xor_sync(full, send, 8);
+  }
+  double v = (h4 ? b2[1] : b2[0]) + __shfl_xor_sync(full, h4 ? b2[0] : b2[1], 4);
+  v += __shfl_xor_sync(full, v, 2);
+  v += __shfl_xor_sync(full, v, 1);
+  return v;
+}
+
 // Block-reduce acc[0..cnt) and store partial[(j0+q)*nblk + blockIdx.x].
 __device__ __forceinline__ void block_store_partials(double (&acc)[kJC], int cnt, int j0,
                                                      double *partial, int nblk,
                                                      double (*red)[kJC]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kJC; ++q) acc[q] = warp_sum(acc[q]);
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < kJC; ++q) red[warp][q] = acc[q];
+  const double v = warp_reduce8(acc);
+  if ((lane & 3) == 0) red[warp][((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1)] = v;
   __syncthreads();
   if (threadIdx.x < cnt) {
     double s = 0.0;
@@ -180,6 +208,82 @@ void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
 }
 
 // ------------------------------------------------------------------ CGS2
+// Dots of vectors V_r[j0 .. j0+cnt) with u over this block's rows, two rows per step
+// so that the loads of both are in flight together; block-reduced into partials.
+__device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, int cnt,
+                                           const double *__restrict__ u, long long lo,
+                                           long long hi, double *part, double (*red)[kJC]) {
+  const double *vb[kJC];
+#pragma unroll
+  for (int q = 0; q < kJC; ++q) vb[q] = Vvec(ws, j0 + min(q, cnt - 1), r);
+  double acc[kJC] = {};
+  long long i = lo + threadIdx.x;
+  for (; i + kRT < hi; i += 2 * kRT) {
+    const double u0 = u[i], u1 = u[i + kRT];
+    double a0[kJC], a1[kJC];
+#pragma unroll
+    for (int q = 0; q < kJC; ++q)
+      if (q < cnt) {
+        a0[q] = vb[q][i];
+        a1[q] = vb[q][i + kRT];
+      }
+#pragma unroll
+    for (int q = 0; q < kJC; ++q)
+      if (q < cnt) acc[q] = fma(a1[q], u1, fma(a0[q], u0, acc[q]));
+  }
+  if (i < hi) {
+    const double u0 = u[i];
+#pragma unroll
+    for (int q = 0; q < kJC; ++q)
+      if (q < cnt) acc[q] = fma(vb[q][i], u0, acc[q]);
+  }
+  block_store_partials(acc, cnt, j0, part, gridDim.x, red);
+}
+
+// u_r[i] -= sum_j V_r[j][i] h[j] for this block's rows, two rows per step with two
+// partial sums each (independent FMA chains).
+__device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
+                                              const double *__restrict__ h, double *u,
+                                              long long lo, long long hi, double *norm2) {
+  long long i = lo + threadIdx.x;
+  double nn = 0.0;
+  for (; i + kRT < hi; i += 2 * kRT) {
+    double s0a = 0.0, s0b = 0.0, s1a = 0.0, s1b = 0.0;
+    int j = 0;
+    for (; j + 1 < nv; j += 2) {
+      const double h0 = __ldg(h + j), h1 = __ldg(h + j + 1);
+      const double *v0 = Vvec(ws, j, r), *v1 = Vvec(ws, j + 1, r);
+      s0a = fma(v0[i], h0, s0a);
+      s1a = fma(v0[i + kRT], h0, s1a);
+      s0b = fma(v1[i], h1, s0b);
+      s1b = fma(v1[i + kRT], h1, s1b);
+    }
+    if (j < nv) {
+      const double hj = __ldg(h + j);
+      const double *v0 = Vvec(ws, j, r);
+      s0a = fma(v0[i], hj, s0a);
+      s1a = fma(v0[i + kRT], hj, s1a);
+    }
+    const double x0 = u[i] - (s0a + s0b), x1 = u[i + kRT] - (s1a + s1b);
+    u[i] = x0;
+    u[i + kRT] = x1;
+    nn = fma(x1, x1, fma(x0, x0, nn));
+  }
+  if (i < hi) {
+    double sa = 0.0, sb = 0.0;
+    int j = 0;
+    for (; j + 1 < nv; j += 2) {
+      sa = fma(Vvec(ws, j, r)[i], __ldg(h + j), sa);
+      sb = fma(Vvec(ws, j + 1, r)[i], __ldg(h + j + 1), sb);
+    }
+    if (j < nv) sa = fma(Vvec(ws, j, r)[i], __ldg(h + j), sa);
+    const double x0 = u[i] - (sa + sb);
+    u[i] = x0;
+    nn = fma(x0, x0, nn);
+  }
+  if (norm2) *norm2 = nn;
+}
+
 // pass 1: h1 = V_r^T w_r -> H_r[0..k, k]
 __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const double *__restrict__ w) {
   __shared__ double red[kWarps][kJC];
@@ -190,20 +294,7 @@ __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const doubl
   double *part = ws.partials + r * ws.pstride;
   long long lo, hi;
   row_range(ws.N, lo, hi);
-  for (int j0 = 0; j0 < nv; j0 += kJC) {
-    const int cnt = min(kJC, nv - j0);
-    const double *vb[kJC];
-#pragma unroll
-    for (int q = 0; q < kJC; ++q) vb[q] = Vvec(ws, j0 + min(q, cnt - 1), r);
-    double acc[kJC] = {};
-    for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
-      const double wv = wr[i];
-#pragma unroll
-      for (int q = 0; q < kJC; ++q)
-        if (q < cnt) acc[q] = fma(vb[q][i], wv, acc[q]);
-    }
-    block_store_partials(acc, cnt, j0, part, gridDim.x, red);
-  }
+  for (int j0 = 0; j0 < nv; j0 += kJC) chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
   if (!arrive_last(ws.counter + r)) return;
   last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 0, nullptr);
   __syncthreads();
@@ -221,25 +312,8 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
   double *part = ws.partials + r * ws.pstride;
   long long lo, hi;
   row_range(ws.N, lo, hi);
-  for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s = fma(Vvec(ws, j, r)[i], __ldg(h1 + j), s);
-    wr[i] -= s;
-  }
-  for (int j0 = 0; j0 < nv; j0 += kJC) {
-    const int cnt = min(kJC, nv - j0);
-    const double *vb[kJC];
-#pragma unroll
-    for (int q = 0; q < kJC; ++q) vb[q] = Vvec(ws, j0 + min(q, cnt - 1), r);
-    double acc[kJC] = {};
-    for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
-      const double wv = wr[i];
-#pragma unroll
-      for (int q = 0; q < kJC; ++q)
-        if (q < cnt) acc[q] = fma(vb[q][i], wv, acc[q]);
-    }
-    block_store_partials(acc, cnt, j0, part, gridDim.x, red);
-  }
+  subtract_proj(ws, r, nv, h1, wr, lo, hi, nullptr);
+  for (int j0 = 0; j0 < nv; j0 += kJC) chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
   if (!arrive_last(ws.counter + r)) return;
   last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, ws.y + r * (ws.max_iter + 2));
   __syncthreads();
@@ -258,13 +332,7 @@ __global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, double *__r
   long long lo, hi;
   row_range(ws.N, lo, hi);
   double acc[kJC] = {};
-  for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
-    double s = 0.0;
-    for (int j = 0; j < nv; ++j) s = fma(Vvec(ws, j, r)[i], __ldg(h2 + j), s);
-    const double v = wr[i] - s;
-    wr[i] = v;
-    acc[0] = fma(v, v, acc[0]);
-  }
+  subtract_proj(ws, r, nv, h2, wr, lo, hi, &acc[0]);
   block_store_partials(acc, 1, 0, part, gridDim.x, red);
   if (!arrive_last(ws.counter + r)) return;
   last_block_reduce(part, gridDim.x, 1, ws.scal + 8 * r + 2, 0, nullptr);
@@ -317,32 +385,54 @@ __device__ void givens_cs(double a, double b, double &c, double &s) {
   }
 }
 
-// For every live right-hand side: rotate column k of H by the previous rotations,
-// build rotation k, update g and the residual estimate, decide convergence.  Then
-// advance k and continue the loop while any right-hand side is live.
+constexpr int kGC = 128;  // rotations staged in shared memory per pass
+
+// For every live right-hand side (one warp each): rotate column k of H by the previous
+// rotations, build rotation k, update g and the residual estimate, decide convergence.
+// Then advance k and continue the loop while any right-hand side is live.  The
+// rotations and the column are staged in shared memory by the whole warp first, so
+// the sequential recurrence (carried in a register) waits on no global loads.
 __global__ void givens_kernel(KrylovWs ws, cudaGraphConditionalHandle cond, int has_cond) {
   __shared__ int active;
+  __shared__ double sh_cs[4][kGC], sh_sn[4][kGC], sh_b[4][kGC];
   SolveState *st = ws.st;
   const int k = st->k;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
   if (threadIdx.x == 0) active = 0;
   __syncthreads();
-  for (int r = threadIdx.x; r < ws.R; r += blockDim.x) {
+  for (int r = warp; r < ws.R; r += nwarps) {
     RhsState &q = ws.rs[r];
     if (q.done) continue;
     double *col = Hcol(ws, r, k);
     double *cs = ws.cs + r * (ws.max_iter + 1), *sn = ws.sn + r * (ws.max_iter + 1);
     double *g = ws.g + r * (ws.max_iter + 2);
     const double hk1 = col[k + 1];
-    for (int i = 0; i < k; ++i) {
-      const double a = col[i], b = col[i + 1];
-      col[i] = cs[i] * a + sn[i] * b;
-      col[i + 1] = -sn[i] * a + cs[i] * b;
+    // t carries the rotated entry i (the "a" of rotation i); b = original entry i+1
+    double t = col[0];
+    for (int base = 0; base < k; base += kGC) {
+      const int m = min(kGC, k - base);
+      for (int e = lane; e < m; e += 32) {
+        sh_cs[warp][e] = cs[base + e];
+        sh_sn[warp][e] = sn[base + e];
+        sh_b[warp][e] = col[base + 1 + e];
+      }
+      __syncwarp();
+      if (lane == 0) {
+        for (int e = 0; e < m; ++e) {
+          const double c = sh_cs[warp][e], s = sh_sn[warp][e], b = sh_b[warp][e];
+          col[base + e] = c * t + s * b;
+          t = -s * t + c * b;
+        }
+      }
+      __syncwarp();
     }
+    if (lane != 0) continue;
     double c, s;
-    givens_cs(col[k], col[k + 1], c, s);
+    givens_cs(t, hk1, c, s);
     cs[k] = c;
     sn[k] = s;
-    col[k] = c * col[k] + s * col[k + 1];
+    col[k] = c * t + s * hk1;
     col[k + 1] = 0.0;
     const double gk = g[k];
     g[k + 1] = -s * gk;
@@ -378,7 +468,7 @@ __global__ void givens_kernel(KrylovWs ws, cudaGraphConditionalHandle cond, int 
 
 void launch_givens(const KrylovWs &ws, cudaGraphConditionalHandle cond, int has_cond,
                    cudaStream_t s) {
-  givens_kernel<<<1, ws.R <= 32 ? 32 : 128, 0, s>>>(ws, cond, has_cond);
+  givens_kernel<<<1, ws.R == 1 ? 32 : 128, 0, s>>>(ws, cond, has_cond);
   IGA_LAUNCH_CHECK();
 }
 

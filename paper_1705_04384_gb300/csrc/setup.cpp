@@ -410,6 +410,49 @@ static float to_tf32(float x) {
   return x;
 }
 
+// Folded FD factors.  Each eigenvector u_j is even (u_{n-1-i} = u_i) or odd
+// (u_{n-1-i} = -u_i) when the pencil was solved on its reflection halves; then V^T and
+// U are block diagonal in the basis of sums / differences of mirrored entries, and the
+// blocks are the left halves of their rows.  Order the eigen-index [even | odd] (by
+// eigenvalue within each part):
+//   Bf[c][f] (forward):  even c: Vt[j][f] for f < ne (f = h is the middle entry);
+//                        odd c:  Vt[j][a] at f = ne + a, a < h;          j = perm[c]
+//   Bi[a][k] (inverse):  U[a][perm[k]] for a < ne, and 0 for odd k at the middle row.
+// Left unset (dense products used) when some eigenvector has no parity.
+static void build_folded(Factor1D &f, cudaStream_t s) {
+  const int n = f.n, h = n / 2;
+  std::vector<int> even, odd;
+  for (int j = 0; j < n; ++j) {
+    double par = 0.0;
+    for (int i = 0; i < n; ++i) par += f.U[(size_t)i * n + j] * f.U[(size_t)(n - 1 - i) * n + j];
+    if (std::fabs(par - 1.0) < 1e-9) even.push_back(j);
+    else if (std::fabs(par + 1.0) < 1e-9) odd.push_back(j);
+    else return;
+  }
+  const int ne = (int)even.size();
+  if (ne != h + n % 2 || (int)odd.size() != h) return;
+  std::vector<int> perm(even);
+  perm.insert(perm.end(), odd.begin(), odd.end());
+  std::vector<double> Bf((size_t)n * n, 0.0), Bi((size_t)ne * n, 0.0), lamf(n);
+  for (int c = 0; c < n; ++c) {
+    const int j = perm[c];
+    lamf[c] = f.lam[j];
+    if (c < ne) {
+      for (int q = 0; q < ne; ++q) Bf[(size_t)c * n + q] = f.Vt[(size_t)j * n + q];
+    } else {
+      for (int a = 0; a < h; ++a) Bf[(size_t)c * n + ne + a] = f.Vt[(size_t)j * n + a];
+    }
+  }
+  for (int a = 0; a < ne; ++a)
+    for (int k = 0; k < n; ++k)
+      if (k < ne || a < h) Bi[(size_t)a * n + k] = f.U[(size_t)a * n + perm[k]];
+  upload(f.d_Bf, Bf, s);
+  upload(f.d_Bi, Bi, s);
+  upload(f.d_lam_fold, lamf, s);
+  f.ne = ne;
+  f.folded = true;
+}
+
 static void upload_factor(Factor1D &f, cudaStream_t s) {
   upload(f.d_start, f.start, s);
   for (int o = 0; o < 3; ++o) upload(f.d_band[o], f.band[o], s);
@@ -434,6 +477,7 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
   upload(f.d_U32, u32, s);
   upload(f.d_Vt16, vt16, s);
   upload(f.d_U16, u16, s);
+  build_folded(f, s);
   IGA_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
