@@ -19,8 +19,13 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "context.h"
 
@@ -307,7 +312,106 @@ struct TcFd {
   DevBuf<int> err;
   CUtensorMap mapP0{}, mapTa{}, mapTb{}, mapVt{}, mapU{};
   const float *dinv32 = nullptr;
+  const void *vt_dev = nullptr, *u_dev = nullptr;
 };
+
+static void make_map(CUtensorMap &m, const void *base, int elem_bf16, long long n_inner,
+                     long long rows, long long ld, int box_rows);
+static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi, int R,
+                 cudaStream_t s);
+
+// Column-tile shape of the mode products: N = n_tile output columns per CTA (a
+// multiple of 16, <= 256), the factor's TMA box and the instruction descriptor follow.
+static void set_tile(TcFd &t, int n_tile) {
+  const bool bf = t.prec == IGA_PREC_BF16;
+  t.n_tile = n_tile;
+  t.n_ntiles = (t.n + n_tile - 1) / n_tile;
+  t.tmem_cols = 32;
+  while (t.tmem_cols < n_tile) t.tmem_cols *= 2;
+  t.smem = 1024 + (size_t)kStages * (kTileM * 128 + (size_t)n_tile * 128);
+  // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
+  const uint32_t fmt = bf ? 1u : 2u;
+  t.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n_tile >> 3) << 17) |
+            ((uint32_t)(kTileM >> 4) << 24);
+  make_map(t.mapVt, t.vt_dev, bf, t.n, t.n, t.kpad, n_tile);
+  make_map(t.mapU, t.u_dev, bf, t.n, t.n, t.kpad, n_tile);
+}
+
+// Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
+// candidate column tile -- the whole padded width, or 2, 3, 4 ... narrower tiles that
+// put more CTAs on the GPU at the cost of re-reading the row tile -- and keep the
+// fastest.  The choice is cached per (device, d, n, precision, R_max) so that every
+// problem of one shape runs the same kernels.
+static void autotune(TcFd &t, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, int> cache;
+  int dev = 0;
+  IGA_CUDA_TRY(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, t.d, t.n, t.prec, t.R_max);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      set_tile(t, it->second);
+      return;
+    }
+  }
+  std::vector<int> cand;
+  if (t.n <= 256) {
+    for (int parts = 1; parts <= 6; ++parts) {
+      const int nt = ((t.n + parts - 1) / parts + 15) / 16 * 16;
+      if (std::find(cand.begin(), cand.end(), nt) == cand.end()) cand.push_back(nt);
+    }
+  } else {
+    cand = {256, 128, 64};
+  }
+  int best = cand[0];
+  if (cand.size() > 1) {
+    std::lock_guard<std::mutex> dlk(device_mutex());
+    cudaEvent_t e0, e1;
+    IGA_CUDA_TRY(cudaEventCreate(&e0));
+    IGA_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    for (int nt : cand) {
+      set_tile(t, nt);
+      TcEpi e{};
+      e.kind = t.prec == IGA_PREC_BF16 ? kOutBF16 : kOutF32;
+      e.n = t.n;
+      e.ld_out = t.kpad;
+      e.nmid = t.M / t.n;
+      e.err = t.err.ptr;
+      auto chain_once = [&]() {
+        for (int g = 0; g < 2 * t.d; ++g) {
+          e.out = (g & 1) ? t.Tb.ptr : t.Ta.ptr;
+          gemm(t, (g & 1) ? t.mapTa : t.mapP0, g < t.d ? t.mapVt : t.mapU, e, t.R_max, s);
+        }
+      };
+      chain_once();
+      IGA_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 3; ++rep) chain_once();
+      IGA_CUDA_TRY(cudaEventRecord(e1, s));
+      IGA_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      IGA_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = nt;
+      }
+      const char *verbose = std::getenv("IGA_VERBOSE");
+      if (verbose && verbose[0] == '1')
+        std::fprintf(stderr, "iga autotune d=%d n=%d prec=%d R=%d n_tile=%d: %.1f us/apply\n",
+                     t.d, t.n, t.prec, t.R_max, nt, 1000.f * ms / 3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    IGA_CUDA_TRY(cudaMemsetAsync(t.err.ptr, 0, sizeof(int), s));
+  }
+  set_tile(t, best);
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = best;
+}
+
+int tc_fd_tile(const TcFd &t) { return t.n_tile; }
 
 static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static std::mutex mu;
@@ -357,15 +461,8 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     for (int l = 0; l < d - 1; ++l) M *= n;
     t->M = (int)M;
     t->R_max = R_max;
-    t->n_tile = n <= 256 ? (n + 15) / 16 * 16 : 128;
-    t->n_ntiles = (n + t->n_tile - 1) / t->n_tile;
-    t->tmem_cols = 32;
-    while (t->tmem_cols < t->n_tile) t->tmem_cols *= 2;
-    t->smem = 1024 + (size_t)kStages * (kTileM * 128 + (size_t)t->n_tile * 128);
-    // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
-    const uint32_t fmt = bf ? 1u : 2u;
-    t->idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(t->n_tile >> 3) << 17) |
-               ((uint32_t)(kTileM >> 4) << 24);
+    t->vt_dev = bf ? (const void *)f.d_Vt16.ptr : (const void *)f.d_Vt32.ptr;
+    t->u_dev = bf ? (const void *)f.d_U16.ptr : (const void *)f.d_U32.ptr;
     const size_t bytes = (size_t)R_max * M * t->kpad * t->esize;
     t->P0.alloc(bytes);
     t->Ta.alloc(bytes);
@@ -378,10 +475,6 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     make_map(t->mapP0, t->P0.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
     make_map(t->mapTa, t->Ta.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
     make_map(t->mapTb, t->Tb.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
-    const void *vt = bf ? (const void *)f.d_Vt16.ptr : (const void *)f.d_Vt32.ptr;
-    const void *u = bf ? (const void *)f.d_U16.ptr : (const void *)f.d_U32.ptr;
-    make_map(t->mapVt, vt, bf, n, n, f.kpad, t->n_tile);
-    make_map(t->mapU, u, bf, n, n, f.kpad, t->n_tile);
     t->dinv32 = dinv32;
     // One limit per device, the largest any tile shape needs: the attribute belongs
     // to the kernel, not to this problem, so a smaller per-problem value would
@@ -400,6 +493,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
         smem_set[dev] = true;
       }
     }
+    autotune(*t, s);
     IGA_CUDA_TRY(cudaStreamSynchronize(s));
   } catch (...) {
     delete t;
