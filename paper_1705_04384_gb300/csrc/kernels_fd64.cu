@@ -10,6 +10,7 @@
 // d-th forward product.
 #include "iga_internal.h"
 
+
 namespace iga {
 
 constexpr int kTM = 32, kTN = 64, kKC = 32, kThreads = 256;
@@ -95,123 +96,204 @@ __global__ void __launch_bounds__(kThreads)
 //   inverse (DIR 1):  pe_a = sum_{k < ne} Bi[a][k] y_k,  po_a = sum_{k >= ne} Bi[a][k] y_k,
 //                     z_a = pe_a + po_a, z_{n-1-a} = pe_a - po_a (a < h), z_h = pe_h.
 // Both need n^2 / 2 FMAs per row instead of n^2 (the 1/sqrt(2) of the basis is folded
-// into Bf and Bi at setup).  Column tiles of DIR 0 never straddle the two blocks.
+// into Bf and Bi at setup).
+//
+// The products run on the FP64 tensor path (mma.sync m8n8k4 .f64).  On GB300 it has the
+// FP64 rate of the CUDA cores (about 2 FMAs per clock per SM), but one warp instruction
+// carries 256 FMAs instead of 32, so the kernel is bound by the FP64 pipe rather than by
+// instruction issue and load latency.  The work is a list of items (row tile of 8 rows,
+// parity block, group of 8 output columns), ordered row-tile-major, and every warp of a
+// grid sized to the SM count takes an equal contiguous range of it: each SM sub-partition
+// receives the same number of FMAs whatever M and n are.  A warp forms the folded
+// A-fragment of a k-step once and feeds up to kMmaNGB column groups of the same row tile
+// and block with it.  A block's last group, when it has fewer than 8 columns, runs on
+// FP64 FMAs with the k-steps split over the four lanes of a fragment row and a
+// two-step shuffle reduction.  Each output is written by one lane, in a fixed order:
+// the results are bitwise reproducible.
+constexpr int kMmaWarps = 4, kMmaRows = 8, kMmaNGB = 4;
+
+__device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, double b) {
+  asm("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+      : "+d"(c0), "+d"(c1)
+      : "d"(a), "d"(b));
+}
+
+// One run: column groups cg .. cg+len-1 of block blk for the 8 rows of row tile rt.
 template <class Tout, int DIR>
-__global__ void __launch_bounds__(kThreads)
-    gemm_fp64_fold_kernel(IdxPtr<const double> Ap, const double *__restrict__ Bt, IdxPtr<Tout> Op,
-                          int M, int n, int ne, int tiles_e, int rows_per, FdScale sc,
-                          int has_scale) {
-  __shared__ double As[kTM][kKC + 1];
-  __shared__ double Bs[kTN][kKC + 1];
-  const double *__restrict__ A = Ap.get();
-  Tout *__restrict__ O = Op.get();
+__device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
+                                             const double *__restrict__ Bt, Tout *__restrict__ O,
+                                             int M, int n, int ne, int rt, int blk, int cg,
+                                             int len, int Nb, int rows_per, const FdScale &sc,
+                                             int has_scale) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const int h = n / 2, no = n - ne;
-  const int row0 = blockIdx.x * kTM;
-  int col0, cend, kbeg, kend;
-  if (DIR == 0) {
-    const bool even = (int)blockIdx.y < tiles_e;
-    col0 = even ? blockIdx.y * kTN : ne + (blockIdx.y - tiles_e) * kTN;
-    cend = even ? ne : n;
-    kbeg = even ? 0 : ne;
-    kend = even ? ne : n;
-  } else {
-    col0 = blockIdx.y * kTN;  // pair index a
-    cend = ne;
-    kbeg = 0;
-    kend = n;
-  }
-  const int tm = min(kTM, M - row0), tn = min(kTN, cend - col0);
-  const int tid = threadIdx.x;
-  constexpr int kRG = kTM / 4;
-  const int nitems = kRG * tn;
-  double acc[2][4][2];
+  const int row = rt * kMmaRows + g;
+  const bool rv = row < M;
+  const double *__restrict__ x = A + (long long)(rv ? row : 0) * n;
+  const int c0 = cg * 8;                         // first block-local column of the run
+  const int brow0 = (DIR == 0 && blk) ? ne : 0;  // factor row of block-local column 0
+  double acc[2][kMmaNGB][2];
 #pragma unroll
-  for (int j = 0; j < 2; ++j)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[j][q][0] = acc[j][q][1] = 0.0;
-  for (int k0 = kbeg; k0 < kend; k0 += kKC) {
-    const int kc = min(kKC, kend - k0);
-    for (int e = tid; e < kTM * kKC; e += kThreads) {
-      const int r = e / kKC, kk = e % kKC;
-      double v = 0.0;
-      if (r < tm && kk < kc) {
-        const double *x = A + (long long)(row0 + r) * n;
-        const int f = k0 + kk;
-        if (DIR == 1) {
-          v = x[f];
-        } else if (f < h) {
-          v = x[f] + x[n - 1 - f];
-        } else if (f < ne) {
-          v = x[h];
-        } else {
-          v = x[f - ne] - x[n - 1 - (f - ne)];
-        }
+    for (int j = 0; j < kMmaNGB; ++j) acc[u][j][0] = acc[u][j][1] = 0.0;
+#pragma unroll
+  for (int u = 0; u < (DIR == 0 ? 1 : 2); ++u) {
+    // DIR 0: one contraction of length Nb over the block's folded entries;
+    // DIR 1: pe over k < ne (u = 0), po over k >= ne (u = 1)
+    const int kb = DIR == 0 ? (blk ? ne : 0) : (u ? ne : 0);
+    const int K = DIR == 0 ? Nb : (u ? no : ne);
+#pragma unroll 2
+    for (int s = 0; s < K; s += 4) {
+      const int k = s + t;
+      const bool kv = k < K;
+      double a = 0.0;
+      if (rv && kv) {
+        if (DIR == 1) a = x[kb + k];
+        else if (!blk) a = k < h ? x[k] + x[n - 1 - k] : x[h];
+        else a = x[k] - x[n - 1 - k];
       }
-      As[r][kk] = v;
-    }
-    for (int e = tid; e < kTN * kKC; e += kThreads) {
-      const int c = e / kKC, kk = e % kKC;
-      Bs[c][kk] = (c < tn && kk < kc) ? __ldg(Bt + (long long)(col0 + c) * n + k0 + kk) : 0.0;
-    }
-    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int it = tid + j * kThreads;
-      if (it < nitems) {
-        const int rg = it % kRG, c = it / kRG;
-        for (int kk = 0; kk < kc; ++kk) {
-          const double b = Bs[c][kk];
-          const int half = (DIR == 1 && k0 + kk >= ne) ? 1 : 0;
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            acc[j][q][half] = fma(As[4 * rg + q][kk], b, acc[j][q][half]);
+      for (int j = 0; j < kMmaNGB; ++j) {
+        if (j < len) {
+          // columns past the block's end (its last group may be partial) multiply zeros
+          const int cl = c0 + 8 * j + g;
+          const double b =
+              (kv && cl < Nb) ? __ldg(Bt + (long long)(brow0 + cl) * n + kb + k) : 0.0;
+          dmma_m8n8k4(acc[u][j][0], acc[u][j][1], a, b);
         }
       }
     }
-    __syncthreads();
   }
+  if (!rv) return;
+  const int rl = row % rows_per, rr = row / rows_per;
+  const long long base = rl + (long long)rows_per * (long long)n * rr;
+  // lane (g, t) holds row g, columns 2t and 2t+1 of each 8 x 8 tile
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int it = tid + j * kThreads;
-    if (it < nitems) {
-      const int rg = it % kRG, c = it / kRG;
-      const int col = col0 + c;
+  for (int j = 0; j < kMmaNGB; ++j) {
+    if (j >= len) continue;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (4 * rg + q >= tm) continue;
-        const int row = row0 + 4 * rg + q;
-        const int rl = row % rows_per, rr = row / rows_per;
-        const long long base = rl + (long long)rows_per * (long long)n * rr;
-        if (DIR == 0) {
-          double v = acc[j][q][0];
-          if (has_scale) v *= __ldg(sc.dinv + rl + (long long)rows_per * col);
-          O[base + (long long)rows_per * col] = (Tout)v;
+    for (int i = 0; i < 2; ++i) {
+      const int cl = c0 + 8 * j + 2 * t + i;
+      if (cl >= Nb) continue;
+      if (DIR == 0) {
+        const int col = brow0 + cl;
+        double v = acc[0][j][i];
+        if (has_scale) v *= __ldg(sc.dinv + rl + (long long)rows_per * col);
+        O[base + (long long)rows_per * col] = (Tout)v;
+      } else {
+        const double pe = acc[0][j][i], po = acc[1][j][i];
+        if (cl < h) {
+          O[base + (long long)rows_per * cl] = (Tout)(pe + po);
+          O[base + (long long)rows_per * (n - 1 - cl)] = (Tout)(pe - po);
         } else {
-          const double pe = acc[j][q][0], po = acc[j][q][1];
-          if (col < h) {
-            O[base + (long long)rows_per * col] = (Tout)(pe + po);
-            O[base + (long long)rows_per * (n - 1 - col)] = (Tout)(pe - po);
-          } else {
-            O[base + (long long)rows_per * col] = (Tout)pe;  // middle index, n odd
-          }
+          O[base + (long long)rows_per * cl] = (Tout)pe;  // middle index, n odd
         }
       }
     }
   }
 }
 
+// Cost of column group j of a row tile, in units of 1/8 of one m8n8k4 MMA: a full group
+// takes one MMA per k-step, a partial group of r columns r FP64 FMAs and one add per
+// k-step, each 1/8 of an MMA on the FP64 pipe.
+__device__ __forceinline__ int fold_group_cost(int DIR, int j, int n, int ne, int g0) {
+  const int no = n - ne;
+  const int blk = j >= g0 ? 1 : 0;
+  const int Nb = (DIR == 0 && blk) ? no : ne;
+  return DIR == 0 ? (Nb + 3) / 4 : (ne + 3) / 4 + (no + 3) / 4;
+}
+
+// First item of the cost share `target` (0 <= target <= total): the smallest item i with
+// prefix cost(i) >= target, items ordered row-tile-major.
+__device__ long long fold_item_at(int DIR, long long target, long long C, int gpr, int n, int ne,
+                                  int g0) {
+  const long long rt = target / C;
+  long long r = target - rt * C;
+  int j = 0;
+  while (r > 0 && j < gpr) r -= fold_group_cost(DIR, j++, n, ne, g0);
+  return rt * gpr + j;
+}
+
+// Virtual warp v = (SM sub-partition slot) * wps + (warp of that slot): the wps warps that
+// share an SM sub-partition take adjacent cost shares, so every sub-partition receives
+// the same FP64 work (up to one item) whatever the item costs are.
+template <class Tout, int DIR>
+__global__ void __launch_bounds__(kMmaWarps * 32 * 4)
+    fd_fold_mma_kernel(IdxPtr<const double> Ap, const double *__restrict__ Bt, IdxPtr<Tout> Op,
+                       int M, int n, int ne, int g0, int g1, long long nrt, int rows_per,
+                       FdScale sc, int has_scale) {
+  // programmatic dependent launch: the next mode product of the chain may be scheduled
+  // at once (its blocks wait in griddepcontrol.wait until this grid has completed), and
+  // this grid computes its work split before waiting for the previous product's output
+  asm volatile("griddepcontrol.launch_dependents;");
+  const int wpb = blockDim.x >> 5, wps = wpb / kMmaWarps, wi = threadIdx.x >> 5;
+  const long long W = (long long)gridDim.x * wpb;
+  const long long v = ((long long)blockIdx.x * kMmaWarps + wi % kMmaWarps) * wps + wi / kMmaWarps;
+  const int gpr = g0 + g1;  // column groups per row tile
+  long long C = 0;          // cost of one row tile
+  for (int j = 0; j < gpr; ++j) C += fold_group_cost(DIR, j, n, ne, g0);
+  const long long total = C * nrt;
+  long long it = fold_item_at(DIR, total * v / W, C, gpr, n, ne, g0);
+  const long long iend =
+      fold_item_at(DIR, total * (v + 1) / W, C, gpr, n, ne, g0);
+  const int no = n - ne;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const double *__restrict__ A = Ap.get();
+  Tout *__restrict__ O = Op.get();
+  while (it < iend) {  // warp-uniform
+    const int rt = (int)(it / gpr);
+    int cg = (int)(it - (long long)rt * gpr);
+    const int blk = cg >= g0 ? 1 : 0;
+    if (blk) cg -= g0;
+    const int Nb = (DIR == 0 && blk) ? no : ne;
+    const long long blk_end = (long long)rt * gpr + (blk ? gpr : g0);
+    const int len = (int)min((long long)kMmaNGB, min(iend, blk_end) - it);
+    fold_mma_run<Tout, DIR>(A, Bt, O, M, n, ne, rt, blk, cg, len, Nb, rows_per, sc, has_scale);
+    it += len;
+  }
+}
+
+static int num_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  IGA_CUDA_TRY(cudaGetDevice(&dev));
+  int nsm = (dev >= 0 && dev < 64) ? sms[dev] : 0;
+  if (nsm == 0) {
+    IGA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (dev >= 0 && dev < 64) sms[dev] = nsm;
+  }
+  return nsm;
+}
+
 template <class Tout>
 void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
                            int M, int n, int ne, const FdScale *scale, cudaStream_t s, int nrhs) {
-  const int tiles_e = (ne + kTN - 1) / kTN, tiles_o = (n - ne + kTN - 1) / kTN;
-  const dim3 grid((M + kTM - 1) / kTM, dir == 0 ? tiles_e + tiles_o : tiles_e);
+  const int no = n - ne;
+  // column groups per row tile: DIR 0 has the even (ne) and odd (no) blocks, DIR 1 the
+  // ne pairs (g1 = 0)
+  const int g0 = (ne + 7) / 8, g1 = dir == 0 ? (no + 7) / 8 : 0;
+  const long long nrt = (M + kMmaRows - 1) / kMmaRows;
+  // two warps per SM sub-partition: while one waits on its loads the other keeps the
+  // sub-partition's FP64 MMA unit busy
+  constexpr int wps = 2;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(num_sms());
+  cfg.blockDim = dim3(32 * kMmaWarps * wps);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   FdScale sc = scale ? *scale : FdScale{nullptr, nullptr, nullptr, 1};
   if (dir == 0)
-    gemm_fp64_fold_kernel<Tout, 0><<<grid, kThreads, 0, s>>>(A, Bt, out, M, n, ne, tiles_e,
-                                                             M / nrhs, sc, scale ? 1 : 0);
+    IGA_CUDA_TRY(cudaLaunchKernelEx(&cfg, fd_fold_mma_kernel<Tout, 0>, A, Bt, out, M, n, ne, g0,
+                                    g1, nrt, M / nrhs, sc, scale ? 1 : 0));
   else
-    gemm_fp64_fold_kernel<Tout, 1><<<grid, kThreads, 0, s>>>(A, Bt, out, M, n, ne, tiles_e,
-                                                             M / nrhs, sc, 0);
+    IGA_CUDA_TRY(cudaLaunchKernelEx(&cfg, fd_fold_mma_kernel<Tout, 1>, A, Bt, out, M, n, ne, g0,
+                                    g1, nrt, M / nrhs, sc, 0));
   IGA_LAUNCH_CHECK();
 }
 
@@ -263,10 +345,10 @@ void preload_kernels_fd64() {
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_kernel<double>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_kernel<float>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_diag_inverse_kernel));
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_fold_kernel<double, 0>));
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_fold_kernel<double, 1>));
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_fold_kernel<float, 1>));
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_fold_kernel<float, 0>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<double, 0>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<double, 1>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<float, 0>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<float, 1>));
 }
 
 }  // namespace iga

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Tolerances"):
+Tolerances, each derived from the arithmetic it covers:
 * 1D factors, points: exact up to a few ulps (same formulas, different code);
 * operator: max |A_gpu u - A_oracle u| <= 1e-13 max |A_oracle u| (FP64 sums of <= 9
   terms of W products; reordering error ~ 1e-15, margin for cancellation);
