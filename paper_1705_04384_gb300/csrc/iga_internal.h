@@ -41,6 +41,42 @@ extern thread_local long long g_launch_count;
     IGA_CUDA_TRY(cudaGetLastError());     \
   } while (0)
 
+// ---------------------------------------------------------------- dependent launch
+// Programmatic dependent launch: a kernel launched with it may be scheduled as soon as
+// every block of the previous kernel in the stream has started; it lets its own
+// successor be scheduled likewise and waits (griddepcontrol.wait) for the previous
+// kernel to complete and its writes to be visible before it touches global memory.
+// In a captured graph the edges become programmatic edges.  Every per-iteration kernel
+// calls pdl_entry() first (a no-op when it was launched without the attribute);
+// launch_pdl is followed by IGA_LAUNCH_CHECK() like <<<>>>.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
+// Kernel groups that may use it; which ones do is a measured choice (pdl_mask(),
+// overridable with the IGA_PDL environment variable, a bit mask of these groups).
+enum PdlGroup : int { kPdlFd64 = 1, kPdlOperator = 2, kPdlKrylov = 4, kPdlTensorCore = 8 };
+int pdl_mask();
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(int group, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = (pdl_mask() & group) ? 1 : 0;
+  IGA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
 // ---------------------------------------------------------------- device memory
 template <class T> struct DevBuf {
   T *ptr = nullptr;

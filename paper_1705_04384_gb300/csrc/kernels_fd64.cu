@@ -155,7 +155,9 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
       }
 #pragma unroll
       for (int j = 0; j < kMmaNGB; ++j) {
-        if (j < len) {
+        // DIR 1: a group starting at or past h holds only the middle index (n odd),
+        // whose odd part vanishes
+        if (j < len && (DIR == 0 || u == 0 || c0 + 8 * j < h)) {
           // columns past the block's end (its last group may be partial) multiply zeros
           const int cl = c0 + 8 * j + g;
           const double b =
@@ -201,7 +203,8 @@ __device__ __forceinline__ int fold_group_cost(int DIR, int j, int n, int ne, in
   const int no = n - ne;
   const int blk = j >= g0 ? 1 : 0;
   const int Nb = (DIR == 0 && blk) ? no : ne;
-  return DIR == 0 ? (Nb + 3) / 4 : (ne + 3) / 4 + (no + 3) / 4;
+  if (DIR == 0) return (Nb + 3) / 4;
+  return (ne + 3) / 4 + (8 * j < n / 2 ? (no + 3) / 4 : 0);
 }
 
 // First item of the cost share `target` (0 <= target <= total): the smallest item i with
@@ -277,23 +280,14 @@ void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, Id
   // two warps per SM sub-partition: while one waits on its loads the other keeps the
   // sub-partition's FP64 MMA unit busy
   constexpr int wps = 2;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(num_sms());
-  cfg.blockDim = dim3(32 * kMmaWarps * wps);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  const dim3 grid(num_sms()), block(32 * kMmaWarps * wps);
   FdScale sc = scale ? *scale : FdScale{nullptr, nullptr, nullptr, 1};
   if (dir == 0)
-    IGA_CUDA_TRY(cudaLaunchKernelEx(&cfg, fd_fold_mma_kernel<Tout, 0>, A, Bt, out, M, n, ne, g0,
-                                    g1, nrt, M / nrhs, sc, scale ? 1 : 0));
+    launch_pdl(kPdlFd64, fd_fold_mma_kernel<Tout, 0>, grid, block, 0, s, A, Bt, out, M, n, ne, g0,
+               g1, nrt, M / nrhs, sc, scale ? 1 : 0);
   else
-    IGA_CUDA_TRY(cudaLaunchKernelEx(&cfg, fd_fold_mma_kernel<Tout, 1>, A, Bt, out, M, n, ne, g0,
-                                    g1, nrt, M / nrhs, sc, 0));
+    launch_pdl(kPdlFd64, fd_fold_mma_kernel<Tout, 1>, grid, block, 0, s, A, Bt, out, M, n, ne, g0,
+               g1, nrt, M / nrhs, sc, 0);
   IGA_LAUNCH_CHECK();
 }
 

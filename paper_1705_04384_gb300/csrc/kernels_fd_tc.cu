@@ -173,6 +173,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int K, int n_tile, int tmem_cols, uint32_t idesc, TcEpi epi) {
+  pdl_entry();  // before any global access, TMEM allocation included
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
   __shared__ __align__(8) uint64_t empty_bar[kStages];
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 template <class T>
 __global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, long long N, int n,
                             int ld) {
+  pdl_entry();
   const double *in = inp.get();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -509,11 +511,11 @@ static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEp
   const int M = R * t.M;
   dim3 grid((M + kTileM - 1) / kTileM, t.n_ntiles);
   if (t.prec == IGA_PREC_BF16)
-    tc_gemm_kernel<1><<<grid, kTcThreads, t.smem, s>>>(A, B, M, t.n, t.n, t.n_tile, t.tmem_cols,
-                                                       t.idesc, epi);
+    launch_pdl(kPdlTensorCore, tc_gemm_kernel<1>, grid, dim3(kTcThreads), t.smem, s, A, B, M,
+               t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
   else
-    tc_gemm_kernel<0><<<grid, kTcThreads, t.smem, s>>>(A, B, M, t.n, t.n, t.n_tile, t.tmem_cols,
-                                                       t.idesc, epi);
+    launch_pdl(kPdlTensorCore, tc_gemm_kernel<0>, grid, dim3(kTcThreads), t.smem, s, A, B, M,
+               t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
   IGA_LAUNCH_CHECK();
 }
 
@@ -526,9 +528,11 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, int 
   const long long N = (long long)R * t.M * t.n;
   const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
   if (bf)
-    pack_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(in, (__nv_bfloat16 *)t.P0.ptr, N, t.n, t.kpad);
+    launch_pdl(kPdlTensorCore, pack_kernel<__nv_bfloat16>, dim3(blocks), dim3(256), 0, s, in,
+               (__nv_bfloat16 *)t.P0.ptr, N, t.n, t.kpad);
   else
-    pack_kernel<float><<<blocks, 256, 0, s>>>(in, (float *)t.P0.ptr, N, t.n, t.kpad);
+    launch_pdl(kPdlTensorCore, pack_kernel<float>, dim3(blocks), dim3(256), 0, s, in,
+               (float *)t.P0.ptr, N, t.n, t.kpad);
   IGA_LAUNCH_CHECK();
   TcEpi mid{};
   mid.kind = bf ? kOutBF16 : kOutF32;

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, d
                                                         int ord1, int ord2, int nout, int dir,
                                                         int n1, int n2, int n3, int nrhs,
                                                         BandDev b) {
+  pdl_entry();
   const long long N = (long long)n1 * n2 * n3 * nrhs;
   const Tin *in = inp.get();
   const long long stride = dir == 0 ? 1 : (dir == 1 ? n1 : (long long)n1 * n2);
@@ -228,8 +229,8 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
   const int r0 = orders[0], r1 = nout > 1 ? orders[1] : 0, r2 = nout > 2 ? orders[2] : 0;
 #define IGA_BAND_CASE(WW)                                                                     \
   case WW:                                                                                    \
-    band_pass_kernel<Tin, WW><<<blocks, threads, 0, s>>>(in, o0, o1, o2, r0, r1, r2, nout, dir, \
-                                                         n1, n2, n3, nrhs, b);                \
+    launch_pdl(kPdlOperator, band_pass_kernel<Tin, WW>, dim3(blocks), dim3(threads), 0, s, in, \
+               o0, o1, o2, r0, r1, r2, nout, dir, n1, n2, n3, nrhs, b);                       \
     break;
   switch (b.W) {
     IGA_BAND_CASE(3)
@@ -257,6 +258,7 @@ template <class Tin, int W>
 __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a, double *out,
                                                             int n1, int n2, int n3, int nrhs,
                                                             BandDev b) {
+  pdl_entry();
   const long long N1 = (long long)n1 * n2 * n3;
   const long long N = N1 * nrhs;
   const double *bands[3] = {b.band0, b.band1, b.band2};
@@ -299,7 +301,8 @@ void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *term
   const int threads = 256, blocks = grid_for(N, threads);
 #define IGA_CON_CASE(WW)                                                                   \
   case WW:                                                                                 \
-    contract_pass_kernel<Tin, WW><<<blocks, threads, 0, s>>>(a, out, n1, n2, n3, nrhs, b); \
+    launch_pdl(kPdlOperator, contract_pass_kernel<Tin, WW>, dim3(blocks), dim3(threads), 0, s, \
+               a, out, n1, n2, n3, nrhs, b);                                                   \
     break;
   switch (b.W) {
     IGA_CON_CASE(3)

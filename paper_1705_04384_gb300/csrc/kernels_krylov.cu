@@ -286,6 +286,7 @@ __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
 
 // pass 1: h1 = V_r^T w_r -> H_r[0..k, k]
 __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const double *__restrict__ w) {
+  pdl_entry();
   __shared__ double red[kWarps][kJC];
   const int r = blockIdx.y;
   if (ws.rs[r].done) return;
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const doubl
 
 // pass 2: w_r -= V_r h1; h2 = V_r^T w_r -> H_r[0..k,k] += h2, y_r = h2
 __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w) {
+  pdl_entry();
   __shared__ double red[kWarps][kJC];
   const int r = blockIdx.y;
   if (ws.rs[r].done) return;
@@ -322,6 +324,7 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
 
 // pass 3: w_r -= V_r h2; H_r[k+1,k] = ||w_r||
 __global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, double *__restrict__ w) {
+  pdl_entry();
   __shared__ double red[kWarps][kJC];
   const int r = blockIdx.y;
   if (ws.rs[r].done) return;
@@ -345,6 +348,7 @@ __global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, double *__r
 
 // v_{k+1} = w / H[k+1,k]
 __global__ void normalize_kernel(KrylovWs ws, const double *__restrict__ w) {
+  pdl_entry();
   const int r = blockIdx.y;
   if (ws.rs[r].done) return;
   const int k = ws.st->k;
@@ -359,13 +363,13 @@ __global__ void normalize_kernel(KrylovWs ws, const double *__restrict__ w) {
 
 void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s) {
   const dim3 grid(ws.nblk, ws.R);
-  cgs_pass1_kernel<<<grid, kRT, 0, s>>>(ws, w);
+  launch_pdl(kPdlKrylov, cgs_pass1_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
-  cgs_pass2_kernel<<<grid, kRT, 0, s>>>(ws, w);
+  launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), 0, s, ws, w);
   IGA_LAUNCH_CHECK();
-  cgs_pass3_kernel<<<grid, kRT, 0, s>>>(ws, w);
+  launch_pdl(kPdlKrylov, cgs_pass3_kernel, grid, dim3(kRT), 0, s, ws, w);
   IGA_LAUNCH_CHECK();
-  normalize_kernel<<<grid, kRT, 0, s>>>(ws, w);
+  launch_pdl(kPdlKrylov, normalize_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
 }
 
@@ -395,6 +399,7 @@ constexpr int kGC = 128;  // rotations staged in shared memory per pass
 __global__ void givens_kernel(KrylovWs ws, cudaGraphConditionalHandle cond, int has_cond) {
   __shared__ int active;
   __shared__ double sh_cs[4][kGC], sh_sn[4][kGC], sh_b[4][kGC];
+  pdl_entry();
   SolveState *st = ws.st;
   const int k = st->k;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -468,7 +473,8 @@ __global__ void givens_kernel(KrylovWs ws, cudaGraphConditionalHandle cond, int 
 
 void launch_givens(const KrylovWs &ws, cudaGraphConditionalHandle cond, int has_cond,
                    cudaStream_t s) {
-  givens_kernel<<<1, ws.R == 1 ? 32 : 128, 0, s>>>(ws, cond, has_cond);
+  launch_pdl(kPdlKrylov, givens_kernel, dim3(1), dim3(ws.R == 1 ? 32 : 128), 0, s, ws, cond,
+             has_cond);
   IGA_LAUNCH_CHECK();
 }
 

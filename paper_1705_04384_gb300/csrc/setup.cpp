@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -485,6 +486,18 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
 std::mutex &device_mutex() {
   static std::mutex mu;
   return mu;
+}
+
+int pdl_mask() {
+  // measured on GB300 (3D n = 65 solves): programmatic dependent launch pays off for
+  // the FD mode products (FP64 and tensor-core chains), is neutral for the operator
+  // passes and costs ~0.7 ms per solve for the Krylov reductions, whose early-scheduled
+  // waiting blocks slow the last-block reductions down
+  static const int mask = [] {
+    const char *e = std::getenv("IGA_PDL");
+    return e ? std::atoi(e) : (int)(kPdlFd64 | kPdlTensorCore);
+  }();
+  return mask;
 }
 
 void ensure_kernels_loaded() {
