@@ -21,13 +21,21 @@ constexpr int kRT = 256;  // threads per reduction block
 constexpr int kWarps = kRT / 32;
 constexpr int kJC = 8;    // vectors per register chunk
 
-// GB300 runs FP64 at 2 FMAs per SM and clock, so the FP64 work of a reduction tree
-// matters as much as that of the dot products: blocks are sized so that each thread
-// accumulates about 8 rows before any reduction, one block per SM at most.
+// GB300 runs FP64 at 2 FMAs per SM and clock and the passes are bound by load latency:
+// two blocks per SM (8 warps, two per sub-partition) hide it best; more blocks make the
+// single last-block reduction over their partials slower than they gain (measured on
+// 3D n = 65 solves).  Each block takes at least 512 rows.
 int reduce_blocks(long long N) {
-  long long b = (N + 2047) / 2048;
+  static int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 152;
+    return n;
+  }();
+  long long b = (N + 511) / 512;
   if (b < 1) b = 1;
-  if (b > 152) b = 152;
+  if (b > 2LL * sms) b = 2LL * sms;
   return (int)b;
 }
 
