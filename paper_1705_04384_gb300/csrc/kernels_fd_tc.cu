@@ -181,16 +181,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ uint32_t tmem_base;
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = kTileM * 128, b_bytes = (uint32_t)n_tile * 128;
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + kStages * a_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM, c0 = blockIdx.y * n_tile;
   constexpr int kbox = KIND == 0 ? 32 : 64;  // elements per 128-byte row
   constexpr int kmma = KIND == 0 ? 8 : 16;   // K per instruction (32 bytes)
   const int nchunks = (K + kbox - 1) / kbox;
+  // the ring has min(kStages, nchunks) stages: a short contraction (K = n, two or three
+  // 128-byte chunks at the usual n) takes less shared memory, so more CTAs share an SM
+  const int nstage = min(kStages, nchunks);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + nstage * a_bytes;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < nstage; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == 0 && lane == 0) {
     for (int c = 0; c < nchunks; ++c) {
-      const int s = c % kStages, use = c / kStages;
+      const int s = c % nstage, use = c / nstage;
       if (use > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
         atomicExch(epi.err, 1);
         break;
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp == 1 && lane == 0) {
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
-      const int s = c % kStages, use = c / kStages;
+      const int s = c % nstage, use = c / nstage;
       if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
         atomicExch(epi.err, 2);
         ok = false;
@@ -330,7 +333,8 @@ static void set_tile(TcFd &t, int n_tile) {
   t.n_ntiles = (t.n + n_tile - 1) / n_tile;
   t.tmem_cols = 32;
   while (t.tmem_cols < n_tile) t.tmem_cols *= 2;
-  t.smem = 1024 + (size_t)kStages * (kTileM * 128 + (size_t)n_tile * 128);
+  const int kbox = bf ? 64 : 32, nstage = std::min(kStages, (t.n + kbox - 1) / kbox);
+  t.smem = 1024 + (size_t)nstage * (kTileM * 128 + (size_t)n_tile * 128);
   // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
   const uint32_t fmt = bf ? 1u : 2u;
   t.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n_tile >> 3) << 17) |
