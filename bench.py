@@ -416,7 +416,8 @@ def run_batched(args):
     probs, rhs, outs = [], [], []
     for sp in specs:
         P = Problem(2, sp["n_elem"], sp["p"], "annulus", sp["r0"], sp["r1"],
-                    precision=args.precision, device=dev, stream=torch.cuda.Stream(dev))
+                    precision=args.precision, device=dev, stream=torch.cuda.Stream(dev),
+                    grid="throughput")
         P.prepare(sp["nrhs"], max_iter)
         B = torch.from_numpy(W.gaussian_rhs(P.N, sp["nrhs"], sp["rhs_seed"])).to(dev)
         probs.append(P)

@@ -223,6 +223,19 @@ iga_status iga_precond_apply_noalloc(int d, int n, const double *Vt_dev, const d
                                      const double *lam_dev, const double *b_dev, double *s_dev,
                                      void *stream);
 
+/* Launch shape of the Krylov reduction passes (the Arnoldi dot products and norms).
+ *   IGA_GRID_LATENCY (default): about two blocks per SM, for one solve at a time;
+ *   IGA_GRID_THROUGHPUT: a block per 4096 rows, at most one per SM, for many solves
+ *     running at once (the batched and served forms).
+ * The mode fixes the row partition of every reduction, so results are bitwise
+ * reproducible among solves on handles with the same mode (alone or among others);
+ * the two modes differ by rounding only.  Call it before the first solve or
+ * iga_prepare; a later call drops the workspace and the captured solve graphs.
+ * Must not be called while a solve is in flight on the handle.
+ * Errors: INVALID_ARG (null handle, unknown mode, solve in flight). */
+typedef enum { IGA_GRID_LATENCY = 0, IGA_GRID_THROUGHPUT = 1 } iga_grid_mode;
+iga_status iga_set_grid_mode(iga_handle h, iga_grid_mode mode);
+
 /* Allocate the Krylov workspace for nrhs right-hand sides and max_iter steps and
  * capture the solve graph now, so that the first solve of that size does no setup.
  * Synchronous; must not be called while a solve is in flight on the handle.  */

@@ -49,6 +49,7 @@ PROTOTYPES = {
                                          ctypes.c_void_p]),
     "iga_launch_counts": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p]),
     "iga_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "iga_set_grid_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "iga_precond_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),

@@ -15,6 +15,7 @@ from ._lib import Geometry, check
 GEOM = {"identity": 0, "annulus": 1, "revolved": 2}
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3}
 FACTOR = {"tau": 0, "M": 1, "B1": 2, "K": 3, "lambda": 4, "U": 5, "Vt": 6}
+GRID = {"latency": 0, "throughput": 1}
 STATUS_OK, STATUS_NO_CONVERGENCE, STATUS_NAN = 0, 5, 7
 
 
@@ -26,7 +27,7 @@ class Problem:
     """One collocation problem: ``iga_setup`` ... ``iga_destroy``."""
 
     def __init__(self, d, n_elem, p, geometry="annulus", r_inner=1.0, r_outer=2.0,
-                 precision="fp64", device="cuda", stream=None):
+                 precision="fp64", device="cuda", stream=None, grid="latency"):
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.d, self.n_elem, self.p = d, n_elem, p
@@ -47,6 +48,8 @@ class Problem:
         N = ctypes.c_longlong()
         check(self.lib.iga_dims(self.h, ctypes.byref(n), ctypes.byref(N)), "iga_dims")
         self.n, self.N = n.value, N.value
+        if grid != "latency":
+            self.set_grid_mode(grid)
 
     def close(self):
         if getattr(self, "h", None):
@@ -78,6 +81,11 @@ class Problem:
         check(self.lib.iga_get_factor(self.h, direction, FACTOR[which],
                                       out.ctypes.data_as(ctypes.c_void_p)), "iga_get_factor")
         return out
+
+    def set_grid_mode(self, grid):
+        """'latency' (one solve at a time) or 'throughput' (many solves at once)."""
+        check(self.lib.iga_set_grid_mode(self.h, GRID[grid]), "iga_set_grid_mode")
+        self.grid = grid
 
     def prepare(self, nrhs=1, max_iter=200):
         """Allocate the solve workspace and capture the solve graph ahead of time."""

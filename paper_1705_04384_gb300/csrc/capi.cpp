@@ -257,6 +257,18 @@ iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration) {
   });
 }
 
+iga_status iga_set_grid_mode(iga_handle h, iga_grid_mode mode) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    if (mode != IGA_GRID_LATENCY && mode != IGA_GRID_THROUGHPUT)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "unknown grid mode"};
+    iga::Ctx &c = h->c;
+    if (c.pending) throw iga::Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
+    c.set_grid_mode((int)mode);
+    return IGA_OK;
+  });
+}
+
 iga_status iga_prepare(iga_handle h, int nrhs, int max_iter) {
   return guarded([&]() -> iga_status {
     if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};

@@ -68,6 +68,8 @@ struct Ctx {
 
   // Krylov workspace for (ws_max_iter, ws_R)
   int ws_max_iter = 0, ws_R = 0;
+  // launch shape of the reduction passes (iga_grid_mode); fixes their row partition
+  int grid_mode = IGA_GRID_LATENCY;
   DevBuf<double> V, Zd, H, cs, sn, g, y, hist, partials, scal;
   DevBuf<float> Zf;
   DevBuf<unsigned int> counter;
@@ -100,6 +102,15 @@ struct Ctx {
   void launch_solve_epilogue(int use_x0, cudaStream_t s);
   SolveGraph &graph_for(int R, int use_x0);
   void drop_graphs();
+  // Switch the reduction grid; the workspace (its partials are sized by the grid) and
+  // the captured graphs are rebuilt on the next solve.
+  void set_grid_mode(int mode) {
+    if (mode == grid_mode) return;
+    grid_mode = mode;
+    drop_graphs();
+    ws_max_iter = 0;
+    ws_R = 0;
+  }
   void enqueue(int R, const double *rhs_dev, double *x_dev, int use_x0, double tol,
                int max_iter);
   bool ready();

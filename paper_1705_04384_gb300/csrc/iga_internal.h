@@ -274,7 +274,7 @@ struct KrylovWs {
   long long N;
 };
 
-int reduce_blocks(long long N);
+int reduce_blocks(long long N, int mode);
 void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
                        cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
 void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s);

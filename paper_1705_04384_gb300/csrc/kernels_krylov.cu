@@ -11,6 +11,7 @@
 // Reductions over blocks are done by the last block to finish (atomic ticket, no
 // spinning), always in block order, so results are bitwise reproducible, and the
 // same for a right-hand side alone or among others.
+#include <algorithm>
 #include <cmath>
 
 #include "iga_internal.h"
@@ -21,11 +22,15 @@ constexpr int kRT = 256;  // threads per reduction block
 constexpr int kWarps = kRT / 32;
 constexpr int kJC = 8;    // vectors per register chunk
 
-// GB300 runs FP64 at 2 FMAs per SM and clock and the passes are bound by load latency:
-// two blocks per SM (8 warps, two per sub-partition) hide it best; more blocks make the
-// single last-block reduction over their partials slower than they gain (measured on
-// 3D n = 65 solves).  Each block takes at least 512 rows.
-int reduce_blocks(long long N) {
+// Grid of the reduction passes.  It depends on N and the handle's grid mode only, so
+// that the row partition -- and with it the order of every reduction -- is the same for
+// a right-hand side alone or among others; each block loops over the right-hand sides.
+// Measured on GB300: for one solve at a time two blocks per SM (eight warps each) work
+// best, more blocks make the last-block reduction over their partials slower than they
+// gain (latency mode, >= 512 rows a block); with many solves running at once (batched
+// form, 256 problems x 8 right-hand sides) a block per 4096 rows, at most one per SM,
+// gives 27 % more throughput (throughput mode).
+int reduce_blocks(long long N, int mode) {
   static int sms = [] {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -33,9 +38,11 @@ int reduce_blocks(long long N) {
       n = 152;
     return n;
   }();
-  long long b = (N + 511) / 512;
+  const long long rows = mode == IGA_GRID_THROUGHPUT ? 4096 : 512;
+  const long long cap = mode == IGA_GRID_THROUGHPUT ? sms : 2LL * sms;
+  long long b = (N + rows - 1) / rows;
   if (b < 1) b = 1;
-  if (b > 2LL * sms) b = 2LL * sms;
+  if (b > cap) b = cap;
   return (int)b;
 }
 
@@ -296,81 +303,87 @@ __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
 __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const double *__restrict__ w) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
-  const int r = blockIdx.y;
-  if (ws.rs[r].done) return;
   const int k = ws.st->k, nv = k + 1;
-  const double *wr = w + (long long)r * ws.N;
-  double *part = ws.partials + r * ws.pstride;
   long long lo, hi;
   row_range(ws.N, lo, hi);
-  for (int j0 = 0; j0 < nv; j0 += kJC) chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
-  if (!arrive_last(ws.counter + r)) return;
-  last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 0, nullptr);
-  __syncthreads();
-  if (threadIdx.x == 0) ws.counter[r] = 0;
+  for (int r = 0; r < ws.R; ++r) {
+    if (ws.rs[r].done) continue;
+    const double *wr = w + (long long)r * ws.N;
+    double *part = ws.partials + r * ws.pstride;
+    for (int j0 = 0; j0 < nv; j0 += kJC)
+      chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
+    if (!arrive_last(ws.counter + r)) continue;
+    last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 0, nullptr);
+    __syncthreads();
+    if (threadIdx.x == 0) ws.counter[r] = 0;
+  }
 }
 
 // pass 2: w_r -= V_r h1; h2 = V_r^T w_r -> H_r[0..k,k] += h2, y_r = h2
 __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
-  const int r = blockIdx.y;
-  if (ws.rs[r].done) return;
   const int k = ws.st->k, nv = k + 1;
-  double *wr = w + (long long)r * ws.N;
-  const double *h1 = Hcol(ws, r, k);
-  double *part = ws.partials + r * ws.pstride;
   long long lo, hi;
   row_range(ws.N, lo, hi);
-  subtract_proj(ws, r, nv, h1, wr, lo, hi, nullptr);
-  for (int j0 = 0; j0 < nv; j0 += kJC) chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
-  if (!arrive_last(ws.counter + r)) return;
-  last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, ws.y + r * (ws.max_iter + 2));
-  __syncthreads();
-  if (threadIdx.x == 0) ws.counter[r] = 0;
+  for (int r = 0; r < ws.R; ++r) {
+    if (ws.rs[r].done) continue;
+    double *wr = w + (long long)r * ws.N;
+    const double *h1 = Hcol(ws, r, k);
+    double *part = ws.partials + r * ws.pstride;
+    subtract_proj(ws, r, nv, h1, wr, lo, hi, nullptr);
+    for (int j0 = 0; j0 < nv; j0 += kJC)
+      chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
+    if (!arrive_last(ws.counter + r)) continue;
+    last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, ws.y + r * (ws.max_iter + 2));
+    __syncthreads();
+    if (threadIdx.x == 0) ws.counter[r] = 0;
+  }
 }
 
 // pass 3: w_r -= V_r h2; H_r[k+1,k] = ||w_r||
 __global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, double *__restrict__ w) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
-  const int r = blockIdx.y;
-  if (ws.rs[r].done) return;
   const int k = ws.st->k, nv = k + 1;
-  double *wr = w + (long long)r * ws.N;
-  const double *h2 = ws.y + r * (ws.max_iter + 2);
-  double *part = ws.partials + r * ws.pstride;
   long long lo, hi;
   row_range(ws.N, lo, hi);
-  double acc[kJC] = {};
-  subtract_proj(ws, r, nv, h2, wr, lo, hi, &acc[0]);
-  block_store_partials(acc, 1, 0, part, gridDim.x, red);
-  if (!arrive_last(ws.counter + r)) return;
-  last_block_reduce(part, gridDim.x, 1, ws.scal + 8 * r + 2, 0, nullptr);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Hcol(ws, r, k)[k + 1] = sqrt(ws.scal[8 * r + 2]);
-    ws.counter[r] = 0;
+  for (int r = 0; r < ws.R; ++r) {
+    if (ws.rs[r].done) continue;
+    double *wr = w + (long long)r * ws.N;
+    const double *h2 = ws.y + r * (ws.max_iter + 2);
+    double *part = ws.partials + r * ws.pstride;
+    double acc[kJC] = {};
+    subtract_proj(ws, r, nv, h2, wr, lo, hi, &acc[0]);
+    block_store_partials(acc, 1, 0, part, gridDim.x, red);
+    if (!arrive_last(ws.counter + r)) continue;
+    last_block_reduce(part, gridDim.x, 1, ws.scal + 8 * r + 2, 0, nullptr);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Hcol(ws, r, k)[k + 1] = sqrt(ws.scal[8 * r + 2]);
+      ws.counter[r] = 0;
+    }
   }
 }
 
 // v_{k+1} = w / H[k+1,k]
 __global__ void normalize_kernel(KrylovWs ws, const double *__restrict__ w) {
   pdl_entry();
-  const int r = blockIdx.y;
-  if (ws.rs[r].done) return;
   const int k = ws.st->k;
-  const double h = Hcol(ws, r, k)[k + 1];
-  const double inv = h > 0.0 ? 1.0 / h : 0.0;
-  double *v = ws.V + ((long long)(k + 1) * ws.R + r) * ws.N;
-  const double *wr = w + (long long)r * ws.N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ws.N;
-       i += (long long)gridDim.x * blockDim.x)
-    v[i] = wr[i] * inv;
+  for (int r = 0; r < ws.R; ++r) {
+    if (ws.rs[r].done) continue;
+    const double h = Hcol(ws, r, k)[k + 1];
+    const double inv = h > 0.0 ? 1.0 / h : 0.0;
+    double *v = ws.V + ((long long)(k + 1) * ws.R + r) * ws.N;
+    const double *wr = w + (long long)r * ws.N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ws.N;
+         i += (long long)gridDim.x * blockDim.x)
+      v[i] = wr[i] * inv;
+  }
 }
 
 void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s) {
-  const dim3 grid(ws.nblk, ws.R);
+  const dim3 grid(ws.nblk);
   launch_pdl(kPdlKrylov, cgs_pass1_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
   launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), 0, s, ws, w);

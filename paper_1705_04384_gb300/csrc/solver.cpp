@@ -246,7 +246,7 @@ void Ctx::ensure_ws(int max_iter, int R) {
   drop_graphs();
   const int mi = std::max(max_iter, ws_max_iter);
   const int Rc = std::max(R_max, std::max(R, ws_R));
-  const int nblk = reduce_blocks(N);
+  const int nblk = reduce_blocks(N, grid_mode);
   const size_t vecs = (size_t)Rc * N;
   V.alloc((size_t)(mi + 1) * vecs);
   IGA_CUDA_TRY(cudaMemsetAsync(V.ptr, 0, (size_t)(mi + 1) * vecs * 8, stream));

@@ -69,8 +69,9 @@ class Server:
 
     def __init__(self, precision="tf32", tol=1e-8, max_iter=100, max_inflight=32,
                  mem_budget=None, keep_solutions=False, device="cuda", setup_threads=4,
-                 lookahead=64, max_per_key=4):
+                 lookahead=64, max_per_key=4, grid="throughput"):
         self.max_per_key = max_per_key
+        self.grid = grid  # many solves run at once: few reduction blocks per solve
         self.precision, self.tol, self.max_iter = precision, tol, max_iter
         self.max_inflight = max_inflight
         self.device = torch.device(device)
@@ -93,7 +94,8 @@ class Server:
         t = time.perf_counter()
         with torch.cuda.device(self.device):
             P = Problem(d, n_elem, p, "annulus", r0, r1, precision=self.precision,
-                        device=self.device, stream=torch.cuda.Stream(self.device))
+                        device=self.device, stream=torch.cuda.Stream(self.device),
+                        grid=self.grid)
             P.prepare(1, self.max_iter)
             slot = _Slot(P, nbytes, key)
         return slot, time.perf_counter() - t

@@ -69,3 +69,5 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.iga_dims(None, None, None) == 1
     assert lib.iga_solve(None, None, None, 0, 1e-8, 10, None, None, None) == 1
     assert lib.iga_destroy(None) == 0
+    assert lib.iga_set_grid_mode(None, 0) == 1
+    assert b"null handle" in lib.iga_last_error()

@@ -16,23 +16,25 @@ from tests.oracle_ref import ref
 pytestmark = pytest.mark.gpu
 
 
-def _problem(d, ne, p, precision="fp64", r0=1.0, r1=2.0, stream=None):
+def _problem(d, ne, p, precision="fp64", r0=1.0, r1=2.0, stream=None, grid="latency"):
     from paper_1705_04384_gb300.api import Problem
-    return Problem(d, ne, p, r_inner=r0, r_outer=r1, precision=precision, stream=stream)
+    return Problem(d, ne, p, r_inner=r0, r_outer=r1, precision=precision, stream=stream,
+                   grid=grid)
 
 
 def _rhs(N, nrhs, seed):
     return np.random.Generator(np.random.PCG64(seed)).standard_normal((nrhs, N))
 
 
+@pytest.mark.parametrize("grid", ["latency", "throughput"])
 @pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16", "none"])
 @pytest.mark.parametrize("d,ne,p", [(2, 30, 3), (3, 9, 4)])
-def test_multi_rhs_bitwise_equals_single(prec, d, ne, p):
+def test_multi_rhs_bitwise_equals_single(prec, d, ne, p, grid):
     R = ref(d, ne, p)
     B = _rhs(R.N, 4, 17)
     B[2] *= 1e-3  # different scales converge at different steps
     maxit = 600 if prec == "none" else 200
-    with _problem(d, ne, p, prec) as P:
+    with _problem(d, ne, p, prec, grid=grid) as P:
         X, info = P.solve_multi(torch.from_numpy(B).cuda(), tol=1e-8, max_iter=maxit)
         X = X.cpu().numpy()
         for r in range(4):
@@ -126,3 +128,17 @@ def test_async_ready_collect_overlap():
     assert np.array_equal(i1["iters"], j1["iters"]) and np.array_equal(i2["iters"], j2["iters"])
     P1.close()
     P2.close()
+
+
+@pytest.mark.parametrize("d,ne,p", [(2, 200, 3), (3, 40, 4)])
+def test_grid_modes_agree(d, ne, p):
+    """The two reduction grids partition the rows differently: at a fixed number of
+    Arnoldi steps the iterates differ by rounding only."""
+    b = torch.from_numpy(_rhs(ref(d, ne, p, assemble=False).N, 1, 5)[0]).cuda()
+    xs = []
+    for grid in ("latency", "throughput"):
+        with _problem(d, ne, p, "fp64", grid=grid) as P:
+            x, info = P.solve(b, tol=0.0, max_iter=12)
+            assert info["iters"] == 12
+            xs.append(x.cpu().numpy())
+    assert np.linalg.norm(xs[1] - xs[0]) <= 1e-10 * np.linalg.norm(xs[0])

@@ -27,9 +27,10 @@ def _requests(seed=7, count=18, spread=0.02):
     return reqs
 
 
-def _alone(req, precision):
+def _alone(req, precision, grid):
     from paper_1705_04384_gb300.api import Problem
-    with Problem(req.d, req.n_elem, req.p, "annulus", req.r0, req.r1, precision=precision) as P:
+    with Problem(req.d, req.n_elem, req.p, "annulus", req.r0, req.r1, precision=precision,
+                 grid=grid) as P:
         b = torch.from_numpy(req.rhs(P.N)).cuda()
         x, info = P.solve(b, tol=1e-8, max_iter=100)
         return x.cpu().numpy(), info
@@ -49,7 +50,7 @@ def test_served_results_equal_alone(precision, budget):
         assert srv.setups > 6  # the small budget forced evictions and re-setup
     for r in done:
         assert r.status == 0 and r.relres <= 1.05e-8
-        x, info = _alone(r, precision)
+        x, info = _alone(r, precision, srv.grid)
         assert info["iters"] == r.iters
         assert np.array_equal(x, r.x), r.rid
     # oracle residual on a few of them
