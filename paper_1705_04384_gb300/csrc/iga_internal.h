@@ -77,6 +77,31 @@ inline void launch_pdl(int group, void (*kernel)(KArgs...), dim3 grid, dim3 bloc
   IGA_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
 }
 
+// ---------------------------------------------------------------- index division
+// Division by an invariant 32-bit divisor d >= 1 for dividends x < 2^31, by one high
+// multiply, an add and a shift (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// x / d = (umulhi(x, m) + x) >> l.  The per-element index arithmetic of the operator
+// passes uses it: a 64-bit integer division is a long instruction sequence that on
+// GB300 also occupies the (slow) FP64 unit.
+struct FastDiv {
+  unsigned d, m;
+  int l;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f{d, 1u, 0};
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+  return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv &f) {
+  return (__umulhi(x, f.m) + x) >> f.l;
+}
+#endif
+// Element counts that the operator and pack kernels index with 32-bit arithmetic.
+constexpr long long kMaxIndex32 = (1LL << 31) - 1;
+
 // ---------------------------------------------------------------- device memory
 template <class T> struct DevBuf {
   T *ptr = nullptr;

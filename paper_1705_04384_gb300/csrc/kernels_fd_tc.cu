@@ -291,13 +291,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // FP64 vector (unpadded) -> TF32-rounded FP32 / BF16 tensor with padded fastest index.
 template <class T>
-__global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, long long N, int n,
-                            int ld) {
+__global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, unsigned N,
+                            FastDiv divn, int ld) {
   pdl_entry();
   const double *in = inp.get();
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long o = (i % n) + (long long)ld * (i / n);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const unsigned q = fdiv(i, divn);
+    const long long o = (long long)(i - q * divn.d) + (long long)ld * q;
     if constexpr (sizeof(T) == 4) {
       out[o] = round_tf32((float)in[i]);
     } else {
@@ -530,13 +530,15 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, int 
   if (R < 1 || R > t.R_max) throw Error{IGA_ERR_INVALID_ARG, "too many right-hand sides"};
   const bool bf = t.prec == IGA_PREC_BF16;
   const long long N = (long long)R * t.M * t.n;
+  if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per FD apply"};
   const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
+  const FastDiv divn = make_fastdiv((unsigned)t.n);
   if (bf)
     launch_pdl(kPdlTensorCore, pack_kernel<__nv_bfloat16>, dim3(blocks), dim3(256), 0, s, in,
-               (__nv_bfloat16 *)t.P0.ptr, N, t.n, t.kpad);
+               (__nv_bfloat16 *)t.P0.ptr, (unsigned)N, divn, t.kpad);
   else
     launch_pdl(kPdlTensorCore, pack_kernel<float>, dim3(blocks), dim3(256), 0, s, in,
-               (float *)t.P0.ptr, N, t.n, t.kpad);
+               (float *)t.P0.ptr, (unsigned)N, divn, t.kpad);
   IGA_LAUNCH_CHECK();
   TcEpi mid{};
   mid.kind = bf ? kOutBF16 : kOutF32;

@@ -175,26 +175,23 @@ void launch_geometry_fields(int d, const iga_geometry &g, const double *tau1, co
 template <class T> __device__ __forceinline__ double ld_val(const T *p) { return (double)__ldg(p); }
 
 // out[o][i] = sum_t band_{order[o]}[c * W + t] * in[i + (start[c] + t - c) * stride],
-// c = coordinate of i along dir.  One thread per output point.
+// c = coordinate of i along dir.  One thread per output point; 32-bit indices
+// (N < 2^31): c = (i / divA) mod divB by multiply-shift division, divA = 1, n1 or n1 n2.
 template <class Tin, int W>
 __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, double *out0,
                                                         double *out1, double *out2, int ord0,
                                                         int ord1, int ord2, int nout, int dir,
-                                                        int n1, int n2, int n3, int nrhs,
-                                                        BandDev b) {
+                                                        unsigned N, int stride, FastDiv divA,
+                                                        FastDiv divB, BandDev b) {
   pdl_entry();
-  const long long N = (long long)n1 * n2 * n3 * nrhs;
   const Tin *in = inp.get();
-  const long long stride = dir == 0 ? 1 : (dir == 1 ? n1 : (long long)n1 * n2);
   const double *bands[3] = {b.band0, b.band1, b.band2};
   const double *B0 = bands[ord0], *B1 = bands[ord1], *B2 = bands[ord2];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = dir == 0 ? (int)(i % n1)
-                           : (dir == 1 ? (int)((i / n1) % n2)
-                                       : (int)((i / ((long long)n1 * n2)) % n3));
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const unsigned qa = dir == 0 ? i : fdiv(i, divA);
+    const int c = (int)(qa - fdiv(qa, divB) * divB.d);
     const int st = __ldg(b.start + c);
-    const Tin *src = in + i + (long long)(st - c) * stride;
+    const Tin *src = in + (int)i + (st - c) * stride;
     double v[W];
 #pragma unroll
     for (int t = 0; t < W; ++t) v[t] = ld_val(src + t * stride);
@@ -224,13 +221,18 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
                       int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
                       int nrhs) {
   const long long N = (long long)n1 * n2 * n3 * nrhs;
+  if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per operator pass"};
   const int threads = 256, blocks = grid_for(N, threads);
   double *o0 = outs[0], *o1 = nout > 1 ? outs[1] : nullptr, *o2 = nout > 2 ? outs[2] : nullptr;
   const int r0 = orders[0], r1 = nout > 1 ? orders[1] : 0, r2 = nout > 2 ? orders[2] : 0;
+  const int stride = dir == 0 ? 1 : (dir == 1 ? n1 : n1 * n2);
+  // c = (i / divA) mod divB: dir 0: i mod n1; dir 1: (i / n1) mod n2; dir 2: (i / n1 n2) mod n3
+  const FastDiv divA = make_fastdiv(dir == 2 ? (unsigned)(n1 * n2) : (unsigned)n1);
+  const FastDiv divB = make_fastdiv(dir == 0 ? (unsigned)n1 : (dir == 1 ? (unsigned)n2 : (unsigned)n3));
 #define IGA_BAND_CASE(WW)                                                                     \
   case WW:                                                                                    \
     launch_pdl(kPdlOperator, band_pass_kernel<Tin, WW>, dim3(blocks), dim3(threads), 0, s, in, \
-               o0, o1, o2, r0, r1, r2, nout, dir, n1, n2, n3, nrhs, b);                       \
+               o0, o1, o2, r0, r1, r2, nout, dir, (unsigned)N, stride, divA, divB, b);        \
     break;
   switch (b.W) {
     IGA_BAND_CASE(3)
@@ -256,20 +258,18 @@ template <class Tin> struct ContractArgsT {
 
 template <class Tin, int W>
 __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a, double *out,
-                                                            int n1, int n2, int n3, int nrhs,
-                                                            BandDev b) {
+                                                            unsigned N, FastDiv div1,
+                                                            FastDiv divN1, BandDev b) {
   pdl_entry();
-  const long long N1 = (long long)n1 * n2 * n3;
-  const long long N = N1 * nrhs;
   const double *bands[3] = {b.band0, b.band1, b.band2};
   const Tin *ins[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) ins[q] = a.in[q].base ? a.in[q].get() : nullptr;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % n1);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int c = (int)(i - fdiv(i, div1) * div1.d);         // coordinate along direction 0
+    const unsigned ic = i - fdiv(i, divN1) * divN1.d;         // point index of one rhs
     const int st = __ldg(b.start + c);
-    const long long base = i + (st - c);
+    const int base = (int)i + (st - c);
     double acc = 0.0;
     for (int t = 0; t < a.nterm; ++t) {
       const Tin *src = ins[a.term_input[t]] + base;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a
       double s = 0.0;
 #pragma unroll
       for (int q = 0; q < W; ++q) s = fma(__ldg(B + q), ld_val(src + q), s);
-      acc = fma(__ldg(a.term_coef[t] + i % N1), s, acc);
+      acc = fma(__ldg(a.term_coef[t] + ic), s, acc);
     }
     out[i] = acc;
   }
@@ -298,11 +298,13 @@ void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *term
   for (int q = 0; q < 6; ++q) a.in[q] = q < maxin ? ins[q] : IdxPtr<const Tin>{nullptr, nullptr, 0, 0};
   a.nterm = nterm;
   const long long N = (long long)n1 * n2 * n3 * nrhs;
+  if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per operator pass"};
   const int threads = 256, blocks = grid_for(N, threads);
+  const FastDiv div1 = make_fastdiv((unsigned)n1), divN1 = make_fastdiv((unsigned)(n1 * n2 * n3));
 #define IGA_CON_CASE(WW)                                                                   \
   case WW:                                                                                 \
     launch_pdl(kPdlOperator, contract_pass_kernel<Tin, WW>, dim3(blocks), dim3(threads), 0, s, \
-               a, out, n1, n2, n3, nrhs, b);                                                   \
+               a, out, (unsigned)N, div1, divN1, b);                                           \
     break;
   switch (b.W) {
     IGA_CON_CASE(3)
