@@ -40,6 +40,13 @@ CONFIG = {"workload": f"{WORKLOAD}: 3D extruded quarter annulus r in [1,2], z in
                       f"1e-3 perturbation, FP64 FD-GMRES to 1e-8",
           "step": "one solve per p (setup cached)",
           "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"}
+REVOLVED_TEXT = ("3d_revolved_ne64: 3D quarter ring r in [1,2] revolved by pi/2 about the axis "
+                 "(0,1,0) through (-1,-1,-1), 64 elements/dir, p=3,4,5, f = 1 + seeded 1e-3 "
+                 "perturbation, FP64 FD-GMRES to 1e-8")
+
+
+def geometry_of(c):
+    return c.get("geometry", "annulus")
 
 
 def parse():
@@ -50,9 +57,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", default="3d_ne64", choices=["3d_ne64", "batched", "served"],
-                    help="3d_ne64 (default bench line), batched (256 2D problems x 8 rhs), "
-                         "served (Poisson request stream)")
+    ap.add_argument("--workload", default="3d_ne64",
+                    choices=["3d_ne64", "3d_revolved_ne64", "batched", "served"],
+                    help="3d_ne64 (default bench line), 3d_revolved_ne64 (Sec. 5's revolved "
+                         "ring, same measurement), batched (256 2D problems x 8 rhs), served "
+                         "(Poisson request stream)")
     ap.add_argument("--precision", default="tf32", help="preconditioner precision for the "
                                                         "batched / served forms")
     ap.add_argument("--count", type=int, default=256, help="problems in the batched form")
@@ -161,7 +170,7 @@ def run_reference(args):
     c = W.CONFIGS[WORKLOAD]
     p = c["ps"][0]
     spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
-    fmap = Geo.make_map("annulus", 3, c["r0"], c["r1"])
+    fmap = Geo.make_map(geometry_of(c), 3, c["r0"], c["r1"])
     A = C.assemble_collocation(spaces, fmap)
     pts = C.physical_points(fmap, [s.tau for s in spaces])
     b = W.config_rhs(WORKLOAD, pts, 0)
@@ -202,7 +211,7 @@ def cpu_baseline_sample(budget_s=15.0):
     c = W.CONFIGS[WORKLOAD]
     p = c["ps"][0]
     spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
-    fmap = Geo.make_map("annulus", 3, c["r0"], c["r1"])
+    fmap = Geo.make_map(geometry_of(c), 3, c["r0"], c["r1"])
     A = C.assemble_collocation(spaces, fmap)
     pts = C.physical_points(fmap, [s.tau for s in spaces])
     b = W.config_rhs(WORKLOAD, pts, 0)
@@ -239,7 +248,7 @@ def run_ours(args):
     def make(prec):
         probs = []
         for i, p in enumerate(c["ps"]):
-            P = Problem(3, c["n_elem"], p, "annulus", c["r0"], c["r1"], precision=prec,
+            P = Problem(3, c["n_elem"], p, geometry_of(c), c["r0"], c["r1"], precision=prec,
                         device=dev, stream=stream)
             pts = P.collocation_points()
             rhs = torch.from_numpy(W.config_rhs(WORKLOAD, pts, i)).to(dev)
@@ -521,6 +530,11 @@ def run_served(args):
 
 def main():
     args = parse()
+    if args.workload == "3d_revolved_ne64":
+        global WORKLOAD
+        WORKLOAD = "3d_revolved_ne64"
+        CONFIG["workload"] = REVOLVED_TEXT
+        args.workload = "3d_ne64"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "3d_ne64":

@@ -239,3 +239,29 @@ def test_full_size_3d_ne64(p):
     assert info["iters"] <= 60
     r = b[idx] - rows @ x
     assert np.max(np.abs(r)) <= 1.05e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("ne,p", [(64, 3), (32, 5)])
+def test_full_size_3d_revolved(ne, p):
+    """Sec. 5's 3D domain (the revolved quarter ring, all nine coefficient fields live) at
+    the bench size: sampled oracle rows of A_C, the full FD against the oracle's FD, and
+    the residual of the converged solution on sampled rows."""
+    import workload as W
+    R = ref(3, ne, p, geometry="revolved", assemble=False)
+    b = W.config_rhs("3d_revolved_ne64", R.points, p_index=0)
+    rng = np.random.default_rng(ne + p)
+    idx = np.unique(np.concatenate([[0, R.N - 1, R.N // 2], rng.integers(0, R.N, 24)]))
+    rows = R.rows(idx)
+    with _problem(3, ne, p, "revolved") as P:
+        u = _rand(R.N, 9)
+        Au = P.apply_operator(torch.from_numpy(u).cuda()).cpu().numpy()
+        want = rows @ u
+        assert np.max(np.abs(Au[idx] - want)) <= 1e-13 * np.max(np.abs(want))
+        s = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+        s_ref = R.fd(b)
+        assert np.linalg.norm(s - s_ref) <= 1e-11 * np.linalg.norm(s_ref)
+        x, info = P.solve(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
+        x = x.cpu().numpy()
+    assert info["status"] == 0 and info["relres_true"] <= 1e-8 * 1.05
+    r = b[idx] - rows @ x
+    assert np.max(np.abs(r)) <= 1.05e-8 * np.linalg.norm(b)

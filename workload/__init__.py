@@ -28,6 +28,10 @@ CONFIGS = {
                             rhs="manufactured", sigma=1e-3, seed=0),
     "3d_annulus_ne128": dict(d=3, n_elem=128, ps=[4, 5, 6], r0=1.0, r1=2.0,
                              rhs="manufactured", sigma=1e-3, seed=0),
+    # Sec. 5's 3D domain: the quarter ring revolved about the axis (0,1,0) through
+    # (-1,-1,-1); f = 1 (no closed-form solution is given for it) with the same perturbation
+    "3d_revolved_ne64": dict(d=3, n_elem=64, ps=[3, 4, 5], r0=1.0, r1=2.0,
+                             geometry="revolved", rhs="constant", sigma=1e-3, seed=0),
 }
 
 
@@ -85,7 +89,10 @@ def gaussian_rhs(N, nrhs=1, seed=0):
 def config_rhs(name, points, p_index=0):
     """Right-hand side of a named configuration at the given physical points."""
     c = CONFIGS[name]
-    f = manufactured_f(points, c["r0"], c["r1"])
+    if c["rhs"] == "constant":
+        f = np.ones(np.asarray(points).shape[0])
+    else:
+        f = manufactured_f(points, c["r0"], c["r1"])
     return perturb(f, c["sigma"], c["seed"] + p_index)
 
 
