@@ -22,10 +22,12 @@ analysis" (arXiv:1705.04384), in numpy/scipy FP64:
 * ``gmres``       -- unrestarted right-preconditioned GMRES (Saad--Schultz, cited in
                      Sec. 3) with modified Gram--Schmidt and Givens rotations, plus the
                      flexible variant used for a variable preconditioner.
+* ``bicgstab``    -- right-preconditioned BiCGStab (van der Vorst 1992), the solver of
+                     Sec. 5, with the paper's half-iteration counting.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 against closed forms, library routines, invariants or brute force; none is
 "parity unpinned".
 """
 
-from . import bspline, geometry, collocation, fd, gmres  # noqa: F401
+from . import bspline, geometry, collocation, fd, gmres, bicgstab  # noqa: F401

@@ -55,3 +55,27 @@ def test_transposed_V_in_fd_is_caught():
     fd.V = [V.T for V in fd.V]
     b = np.random.default_rng(1).standard_normal(P.shape[0])
     assert np.linalg.norm(fd(P @ b) - b) > 1e-6 * np.linalg.norm(b)
+
+
+def _bicgstab_with(monkeypatch, old, new):
+    """Re-build the oracle's BiCGStab with one source line changed."""
+    import inspect
+    from oracle import bicgstab as B
+    src = inspect.getsource(B.bicgstab)
+    assert old in src
+    ns = {"np": np}
+    exec(src.replace(old, new), ns)
+    monkeypatch.setattr(B, "bicgstab", ns["bicgstab"])
+
+
+@pytest.mark.parametrize("old,new", [
+    ("p = r + beta * (p - omega * v)", "p = r + beta * p"),           # dropped omega v
+    ("omega = np.dot(t, s) / np.dot(t, t)", "omega = np.dot(t, s) / np.dot(s, s)"),
+    ("r = s - omega * t", "r = s + omega * t"),                        # wrong sign
+    ("x = x + alpha * phat + omega * shat", "x = x + alpha * phat + omega * s"),  # M skipped
+])
+def test_bicgstab_mistakes_are_caught(monkeypatch, old, new):
+    import tests.test_oracle_bicgstab as TB
+    _bicgstab_with(monkeypatch, old, new)
+    with pytest.raises(AssertionError):
+        TB.test_matches_scipy_at_fixed_step_counts(2, 8, 3)
