@@ -223,6 +223,25 @@ iga_status iga_precond_apply_noalloc(int d, int n, const double *Vt_dev, const d
                                      const double *lam_dev, const double *b_dev, double *s_dev,
                                      void *stream);
 
+/* Solve A_C x = b with BiCGStab (van der Vorst 1992), the solver of Sec. 5,
+ * right-preconditioned with the handle's FD solve (none for IGA_PREC_NONE), one
+ * right-hand side.  Device pointers rhs_dev, x_dev: N doubles; x_dev holds x0 on entry
+ * when use_x0 != 0 and the solution on return.  Stops when the recursively updated
+ * residual, checked after each half of an iteration (the BiCG half, then the GMRES(1)
+ * half), satisfies ||r|| <= tol ||b||, or after max_iter iterations.
+ *   half_steps     (out, optional) half steps taken: 2k after iteration k, 2k - 1 when
+ *                  the BiCG half of iteration k met the tolerance (Sec. 5 reports
+ *                  half_steps / 2 = k or k - 0.5 iterations)
+ *   res_hist_host  (out, optional, host) 2 max_iter + 1 doubles: ||r|| / ||b|| before
+ *                  the first step and after each half step; entries past half_steps 0
+ *   true_relres    (out, optional) ||b - A_C x|| / ||b|| recomputed in FP64
+ * Synchronous (waits for the handle's stream).  max_iter in 1..4096.
+ * Errors: INVALID_ARG, NO_CONVERGENCE (max_iter reached with tol > 0, or a breakdown:
+ * rho, (rhat, v) or (t, t) zero -- see iga_last_error), NAN, CUDA, OOM.  */
+iga_status iga_solve_bicgstab(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0,
+                              double tol, int max_iter, int *half_steps, double *res_hist_host,
+                              double *true_relres);
+
 /* Launch shape of the Krylov reduction passes (the Arnoldi dot products and norms).
  *   IGA_GRID_LATENCY (default): about two blocks per SM, for one solve at a time;
  *   IGA_GRID_THROUGHPUT: a block per 4096 rows, at most one per SM, for many solves

@@ -50,6 +50,9 @@ PROTOTYPES = {
     "iga_launch_counts": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p]),
     "iga_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "iga_set_grid_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "iga_solve_bicgstab": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, c_int_p,
+                                          ctypes.c_void_p, c_double_p]),
     "iga_precond_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),

@@ -137,6 +137,29 @@ class Problem:
         k = iters.value
         return out, dict(iters=k, hist=hist[:k + 1].copy(), relres_true=rel.value, status=st)
 
+    def solve_bicgstab(self, rhs, x0=None, tol=1e-8, max_iter=200, out=None,
+                       allow_no_convergence=True):
+        """BiCGStab + FD (Sec. 5's solver).  Returns (x, info) with info = dict(half_steps,
+        iters = half_steps / 2 (the paper's k or k - 0.5), hist, relres_true, status)."""
+        rhs = self._vec(rhs)
+        if out is None:
+            out = torch.empty_like(rhs)
+        use_x0 = 0
+        if x0 is not None:
+            out.copy_(self._vec(x0))
+            use_x0 = 1
+        steps = ctypes.c_int()
+        rel = ctypes.c_double()
+        hist = np.zeros(2 * max_iter + 1, dtype=np.float64)
+        st = self.lib.iga_solve_bicgstab(self.h, _ptr(rhs), _ptr(out), use_x0, float(tol),
+                                         int(max_iter), ctypes.byref(steps),
+                                         hist.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rel))
+        allow = (STATUS_NO_CONVERGENCE,) if allow_no_convergence else ()
+        check(st, "iga_solve_bicgstab", allow)
+        k = steps.value
+        return out, dict(half_steps=k, iters=k / 2.0, hist=hist[:k + 1].copy(),
+                         relres_true=rel.value, status=st)
+
     def solve_host(self, rhs_host, x_host, tol=1e-8, max_iter=200):
         """Host-buffer solve (copies inside the call).  rhs_host/x_host: float64 arrays or
         CPU tensors (pinned for asynchronous copies)."""

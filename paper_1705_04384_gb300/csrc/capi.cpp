@@ -257,6 +257,17 @@ iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration) {
   });
 }
 
+iga_status iga_solve_bicgstab(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0,
+                              double tol, int max_iter, int *half_steps, double *res_hist_host,
+                              double *true_relres) {
+  return guarded([&]() -> iga_status {
+    if (!h || !rhs_dev || !x_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    check_solve_args(1, max_iter, tol);
+    return h->c.solve_bicgstab(rhs_dev, x_dev, use_x0 ? 1 : 0, tol, max_iter, half_steps,
+                               res_hist_host, true_relres);
+  });
+}
+
 iga_status iga_set_grid_mode(iga_handle h, iga_grid_mode mode) {
   return guarded([&]() -> iga_status {
     if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};

@@ -83,6 +83,17 @@ struct Ctx {
   // captured solve graphs keyed by (R, use_x0)
   std::map<std::pair<int, int>, SolveGraph> graphs;
 
+  // BiCGStab (one right-hand side): r, rhat, p, v, s, t, phat, shat, the scalar state,
+  // the residual history and the graphs keyed by use_x0
+  int bicg_max_iter = 0;
+  DevBuf<double> bicg_vec, bicg_hist, bicg_partials;
+  DevBuf<unsigned int> bicg_counter;
+  DevBuf<BicgState> bicg_st;
+  BicgState *h_bicg = nullptr;    // pinned
+  double *h_bicg_hist = nullptr;  // pinned, 2 bicg_max_iter + 1
+  BicgWs bws{};
+  std::map<int, SolveGraph> bicg_graphs;
+
   // the solve in flight (enqueue ... collect)
   bool pending = false;
   int pend_R = 0, pend_max_iter = 0;
@@ -110,7 +121,16 @@ struct Ctx {
     drop_graphs();
     ws_max_iter = 0;
     ws_R = 0;
+    bicg_max_iter = 0;
   }
+  void ensure_bicg(int max_iter);
+  void bicg_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
+  void bicg_prologue(int use_x0, cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
+  void bicg_epilogue(cudaStream_t s);
+  SolveGraph &bicg_graph_for(int use_x0);
+  // Synchronous BiCGStab solve; half_steps = 2k or 2k - 1 (the paper's k or k - 0.5).
+  iga_status solve_bicgstab(const double *rhs_dev, double *x_dev, int use_x0, double tol,
+                            int max_iter, int *half_steps, double *hist_out, double *relres);
   void enqueue(int R, const double *rhs_dev, double *x_dev, int use_x0, double tol,
                int max_iter);
   bool ready();

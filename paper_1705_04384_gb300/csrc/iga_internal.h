@@ -195,6 +195,7 @@ void preload_kernels_fd64();
 void preload_kernels_fd_tc();
 void preload_kernels_geom_op();
 void preload_kernels_krylov();
+void preload_kernels_bicgstab();
 
 // ---------------------------------------------------------------- geometry
 // Coefficient fields of L u_hat = sum_f q_f(x) * (derivative f of u_hat):
@@ -300,6 +301,39 @@ struct KrylovWs {
 };
 
 int reduce_blocks(long long N, int mode);
+
+// ---------------------------------------------------------------- BiCGStab
+struct BicgState {
+  double rho, rho_prev, alpha, omega;  // scalar recurrences
+  double bnorm, tol, relres_true, pad;
+  int k;         // current iteration (1-based)
+  int steps;     // half steps taken: 2k - 1 after the BiCG half, 2k after the GMRES half
+  int done;      // the loop has ended
+  int flag;      // 0 converged, 2 max_iter, 3 breakdown (rho, (rhat, v) or (t, t) zero), 4 NaN
+  int half;      // converged after the BiCG half of iteration k
+  int max_iter;
+  int pad2[2];
+};
+
+struct BicgWs {
+  double *r, *rhat, *p, *v, *s, *t, *phat, *shat, *x;  // N each
+  double *hist;      // ||residual|| / ||b|| at half steps 0 .. 2 max_iter
+  double *partials;  // 3 x nblk
+  unsigned int *counter;
+  BicgState *st;
+  long long N;
+  int nblk;
+};
+
+void launch_bicg_init(const BicgWs &ws, const double *b, const double *r0, const double *x0,
+                      cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
+void launch_bicg_p(const BicgWs &ws, cudaStream_t s);
+void launch_bicg_alpha(const BicgWs &ws, cudaStream_t s);
+void launch_bicg_s(const BicgWs &ws, cudaStream_t s);
+void launch_bicg_omega(const BicgWs &ws, cudaStream_t s);
+void launch_bicg_xr(const BicgWs &ws, cudaGraphConditionalHandle cond, int has_cond,
+                    cudaStream_t s);
+void launch_bicg_residual(const BicgWs &ws, const double *b, const double *Ax, cudaStream_t s);
 void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
                        cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
 void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s);

@@ -510,6 +510,7 @@ void ensure_kernels_loaded() {
   preload_kernels_fd_tc();
   preload_kernels_geom_op();
   preload_kernels_krylov();
+  preload_kernels_bicgstab();
   loaded[dev] = true;
 }
 

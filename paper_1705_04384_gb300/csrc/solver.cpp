@@ -23,6 +23,8 @@ Ctx::~Ctx() {
   if (h_st) cudaFreeHost(h_st);
   if (h_rs) cudaFreeHost(h_rs);
   if (h_hist) cudaFreeHost(h_hist);
+  if (h_bicg) cudaFreeHost(h_bicg);
+  if (h_bicg_hist) cudaFreeHost(h_bicg_hist);
 }
 
 void Ctx::drop_graphs() {
@@ -31,6 +33,11 @@ void Ctx::drop_graphs() {
     if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
   }
   graphs.clear();
+  for (auto &kv : bicg_graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  bicg_graphs.clear();
 }
 
 // ------------------------------------------------------------------ setup
@@ -125,8 +132,9 @@ void Ctx::ensure_capacity(int R) {
   if (R <= R_max) return;
   if (pending) throw Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
   drop_graphs();
-  ws_max_iter = 0;  // the Krylov workspace is rebuilt for the new capacity
+  ws_max_iter = 0;  // the Krylov workspaces are rebuilt for the new capacity
   ws_R = 0;
+  bicg_max_iter = 0;
   op_scratch.alloc((size_t)(plan.nA + plan.nB) * R * N);
   fd_scratch.alloc(2 * (size_t)R * N);
   b.alloc((size_t)R * N);

@@ -1,0 +1,110 @@
+"""GPU parity of BiCGStab + FD (Sec. 5's solver) against the BiCGStab oracle.
+
+Tolerances: at a fixed number of iterations (tol = 0) the iterate is the same rational
+function of the data on both sides, evaluated in a different order: 1e-10 relative
+(the FD and operator parities are 1e-11 / 1e-13; a few BiCGStab steps amplify them
+mildly).  To tolerance 1e-8: half-step counts within +-1 of the oracle's, FP64 true
+residual (recomputed with the oracle's A_C) <= 1.05e-8.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import bicgstab as OB
+from tests.oracle_ref import ref
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(d, ne, p, geometry="annulus", precision="fp64"):
+    from paper_1705_04384_gb300.api import Problem
+    return Problem(d, ne, p, geometry=geometry, precision=precision)
+
+
+def _rand(N, seed):
+    return np.random.default_rng(seed).standard_normal(N)
+
+
+CASES = [(2, 12, 3, "annulus"), (2, 9, 5, "annulus"), (3, 6, 3, "annulus"),
+         (3, 5, 4, "revolved")]
+
+
+@pytest.mark.parametrize("d,ne,p,geo", CASES)
+def test_fixed_iterations_match_oracle(d, ne, p, geo):
+    R = ref(d, ne, p, geo)
+    b = _rand(R.N, 11)
+    with _problem(d, ne, p, geo) as P:
+        for k in (1, 3, 6):
+            x, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=0.0, max_iter=k)
+            want = OB.bicgstab(R.A, b, M=R.fd, tol=0.0, max_iter=k)
+            assert info["half_steps"] == want["steps"] == 2 * k
+            x = x.cpu().numpy()
+            assert np.linalg.norm(x - want["x"]) <= 1e-10 * np.linalg.norm(want["x"]), k
+            assert np.allclose(info["hist"], want["hist"], rtol=1e-8, atol=0)
+
+
+@pytest.mark.parametrize("d,ne,p,geo", CASES + [(3, 12, 4, "revolved")])
+def test_to_tolerance(d, ne, p, geo):
+    R = ref(d, ne, p, geo)
+    b = _rand(R.N, 12)
+    want = OB.bicgstab(R.A, b, M=R.fd, tol=1e-8, max_iter=300)
+    with _problem(d, ne, p, geo) as P:
+        x, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
+    x = x.cpu().numpy()
+    assert info["status"] == 0
+    assert abs(info["half_steps"] - want["steps"]) <= 1
+    assert info["hist"][-1] <= 1e-8
+    true = np.linalg.norm(b - R.A @ x) / np.linalg.norm(b)
+    assert true <= 1.05e-8 and abs(info["relres_true"] - true) <= 1e-3 * true
+
+
+def test_exact_preconditioner_stops_after_one_half_step():
+    # identity map: A_C = P_C, the FD solve is exact
+    R = ref(2, 14, 3, "identity")
+    b = _rand(R.N, 13)
+    with _problem(2, 14, 3, "identity") as P:
+        x, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=50)
+    assert info["status"] == 0 and info["half_steps"] == 1 and info["iters"] == 0.5
+    assert np.linalg.norm(b - R.A @ x.cpu().numpy()) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_zero_and_nan_rhs():
+    from paper_1705_04384_gb300._lib import IgaError
+    with _problem(2, 8, 3) as P:
+        x, info = P.solve_bicgstab(torch.zeros(P.N, dtype=torch.float64).cuda())
+        assert info["half_steps"] == 0 and info["status"] == 0
+        assert not torch.any(x)
+        b = torch.ones(P.N, dtype=torch.float64).cuda()
+        b[3] = float("nan")
+        with pytest.raises(IgaError):
+            P.solve_bicgstab(b)
+
+
+def test_initial_guess_and_reproducibility(monkeypatch):
+    R = ref(2, 16, 4)
+    b = torch.from_numpy(_rand(R.N, 14)).cuda()
+    with _problem(2, 16, 4) as P:
+        x1, i1 = P.solve_bicgstab(b, tol=1e-8, max_iter=200)
+        x2, i2 = P.solve_bicgstab(b, tol=1e-8, max_iter=200)
+        assert torch.equal(x1, x2) and i1["half_steps"] == i2["half_steps"]
+        monkeypatch.setenv("IGA_EAGER", "1")
+        x3, i3 = P.solve_bicgstab(b, tol=1e-8, max_iter=200)
+        monkeypatch.delenv("IGA_EAGER")
+        assert torch.equal(x1, x3) and i1["half_steps"] == i3["half_steps"]
+        # restarting from the converged solution (true residual <= 1.05e-8): nothing left
+        x4, i4 = P.solve_bicgstab(b, x0=x1, tol=2e-8, max_iter=200)
+        assert i4["half_steps"] == 0 and torch.equal(x4, x1)
+        # a nearby guess converges in fewer steps than from zero
+        x5, i5 = P.solve_bicgstab(b, x0=x1 * (1 + 1e-4), tol=1e-8, max_iter=200)
+        assert i5["status"] == 0 and i5["half_steps"] < i1["half_steps"]
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_tensor_core_preconditioner(precision):
+    R = ref(3, 10, 3)
+    b = _rand(R.N, 15)
+    with _problem(3, 10, 3, precision=precision) as P:
+        x, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
+    assert info["status"] == 0
+    assert np.linalg.norm(b - R.A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
