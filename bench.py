@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-bicgstab", action="store_true")
     ap.add_argument("--workload", default="3d_ne64",
                     choices=["3d_ne64", "3d_revolved_ne64", "batched", "served"],
                     help="3d_ne64 (default bench line), 3d_revolved_ne64 (Sec. 5's revolved "
@@ -267,13 +268,16 @@ def run_ours(args):
             mixed_err = str(e)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def run_step(probs, record):
+    def run_step(probs, record, solver="gmres"):
         per = []
         for p, P, rhs, x in probs:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, info = P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+            if solver == "gmres":
+                _, info = P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+            else:
+                _, info = P.solve_bicgstab(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
             e1.record(stream)
             per.append((p, P, info, e0, e1))
         torch.cuda.synchronize(dev)
@@ -282,14 +286,14 @@ def run_ours(args):
             out.append((p, P.N, info["iters"], e0.elapsed_time(e1) * 1e-3, info["relres_true"]))
         return out
 
-    def timed(probs, steps, warmup):
+    def timed(probs, steps, warmup, solver="gmres"):
         for _ in range(warmup):
-            run_step(probs, False)
+            run_step(probs, False, solver)
         results = []
         for _ in range(steps):
             flush.fill_(1.0)  # L2 flush between steps, outside the timed solves
             torch.cuda.synchronize(dev)
-            results.append(run_step(probs, True))
+            results.append(run_step(probs, True, solver))
         return results
 
     if world > 1:
@@ -388,6 +392,20 @@ def run_ours(args):
                      "p99_ms": percentile([s[3] * 1e3 for st in resm for s in st], 99),
                      "time_to_solution_ms_per_step": 1e3 * mt / len(resm)}
 
+    # Sec. 5's solver on the same problems: BiCGStab + FP64 FD; an iteration is a BiCG
+    # step and a GMRES(1) step (two FD solves, two operator applications), counted in
+    # halves as the paper does
+    bicg_out = None
+    if not args.no_bicgstab:
+        resb = timed(fp64, max(1, args.steps // 2), args.warmup, "bicgstab")
+        bt = sum(sum(s[3] for s in step) for step in resb)
+        bd = sum(sum(s[1] * s[2] for s in step) for step in resb)
+        bicg_out = {"value": world * bd / bt, "unit": "DOF-iter/s (BiCGStab iterations)",
+                    "iters": {str(s[0]): s[2] for s in resb[-1]},
+                    "relres_true": {str(s[0]): s[4] for s in resb[-1]},
+                    "p50_ms": percentile([s[3] * 1e3 for st in resb for s in st], 50),
+                    "time_to_solution_ms_per_step": 1e3 * bt / len(resb)}
+
     if rank != 0:
         return 0
     cpu = None
@@ -400,7 +418,7 @@ def run_ours(args):
             "p50_ms": percentile(solve_ms, 50), "p99_ms": percentile(solve_ms, 99),
             "iters": iters, "relres_true": relres, "setup_s_cold": t_setup,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "mixed": mixed_out}
+            "clocks": clk, "mixed": mixed_out, "bicgstab": bicg_out}
     if mixed_out is None and not args.no_mixed:
         line["mixed_unavailable"] = mixed_err if "mixed_err" in locals() else "not built"
     print(json.dumps(line), flush=True)

@@ -108,3 +108,18 @@ def test_tensor_core_preconditioner(precision):
         x, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=300)
     assert info["status"] == 0
     assert np.linalg.norm(b - R.A @ x.cpu().numpy()) <= 1.05e-8 * np.linalg.norm(b)
+
+
+def test_full_size_3d_ne64():
+    """The bench workload (3D extruded annulus, 64 elements, p = 3, manufactured f with
+    the seeded perturbation): half steps against the oracle's BiCGStab, the true
+    residual with the oracle's A_C."""
+    import workload as W
+    R = ref(3, 64, 3)
+    b = W.config_rhs("3d_annulus_ne64", R.points, p_index=0)
+    want = OB.bicgstab(R.A, b, M=R.fd, tol=1e-8, max_iter=200)
+    with _problem(3, 64, 3) as P:
+        x, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=1e-8, max_iter=200)
+    assert info["status"] == 0 and abs(info["half_steps"] - want["steps"]) <= 1
+    true = np.linalg.norm(b - R.A @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert true <= 1.05e-8
