@@ -24,6 +24,8 @@ analysis" (arXiv:1705.04384), in numpy/scipy FP64:
                      flexible variant used for a variable preconditioner.
 * ``bicgstab``    -- right-preconditioned BiCGStab (van der Vorst 1992), the solver of
                      Sec. 5, with the paper's half-iteration counting.
+* convection--diffusion (Sec. 3.2) with a constant wind: ``geometry.wind_coefficients``,
+  the ``wind`` arguments of ``collocation`` and ``fd.FD``.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 against closed forms, library routines, invariants or brute force; none is

@@ -8,6 +8,10 @@ Paper references:
   so a tensor product "D_d (x) ... (x) D_1" is numpy ``kron(D_d, ..., D_1)``;
 * eq. (colloc2D) / (colloc3D) and Sec. 3: P_C = K2 (x) M1 + M2 (x) K1 (2D) and the
   three-term sum in 3D.
+* Sec. 3.2 (convection--diffusion, eq. convection / convec_prec_2), restated for
+  collocation with a constant wind w: the operator gains + sum_c (J^{-1} w)_c d_c, and
+  the preconditioner's factors K_l become K_l + H_l with H_l = w_l B'_l (the collocation
+  counterpart of the paper's H_l with the univariate wind approximation w~_l = w_l).
 """
 
 import itertools
@@ -16,7 +20,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import bspline
-from .geometry import pullback_coefficients
+from .geometry import pullback_coefficients, wind_coefficients
 
 
 class Space1D:
@@ -77,14 +81,19 @@ def coefficient_fields(fmap, taus):
     return G, L
 
 
-def assemble_collocation(spaces, fmap):
+def assemble_collocation(spaces, fmap, wind=None):
     """A_C in CSR, from the definition: row I = -sum_{a,b} G^{ab}(tau_I) d_a d_b B_J(tau_I)
-    - sum_c L_c(tau_I) d_c B_J(tau_I), with tensor-product B_J (eq. multivariatesplines).
+    - sum_c L_c(tau_I) d_c B_J(tau_I), with tensor-product B_J (eq. multivariatesplines);
+    with a constant wind w (Sec. 3.2) also + sum_c (J^{-1} w)_c(tau_I) d_c B_J(tau_I).
 
     The derivative multi-index (e_1, .., e_d) picks the 1D matrix B[e_l] in direction l.
     """
     d = len(spaces)
     G, L = coefficient_fields(fmap, [s.tau for s in spaces])
+    if wind is not None:
+        pts = tensor_points([s.tau for s in spaces])
+        Wc = np.array([wind_coefficients(fmap, x, wind) for x in pts])
+        L = L - Wc  # the first-order term enters with -L_c
     N = G.shape[0]
     A = sp.csr_matrix((N, N))
     for a, b in itertools.product(range(d), range(d)):
@@ -103,19 +112,26 @@ def assemble_collocation(spaces, fmap):
     return A
 
 
-def assemble_preconditioner(spaces):
+def wind_factor(space, w_l):
+    """K_l + H_l of Sec. 3.2 in collocation form: -B'' + w_l B' (w_l = 0: K_l)."""
+    return space.K + w_l * space.B[1]
+
+
+def assemble_preconditioner(spaces, wind=None):
     """P_C from eq. (colloc2D) (d = 2) or eq. (colloc3D) (d = 3): sum over l of the
-    Kronecker product with K_l in slot l and M in every other slot."""
+    Kronecker product with K_l in slot l and M in every other slot; with a wind, K_l is
+    K_l + H_l (eq. convec_prec_2)."""
     d = len(spaces)
+    w = np.zeros(d) if wind is None else np.asarray(wind, dtype=np.float64)
     P = None
     for l in range(d):
-        mats = [spaces[j].K if j == l else spaces[j].M for j in range(d)]
+        mats = [wind_factor(spaces[j], w[j]) if j == l else spaces[j].M for j in range(d)]
         term = kron_list(mats)
         P = term if P is None else P + term
     return P.tocsr()
 
 
-def collocation_rows(spaces, fmap, rows):
+def collocation_rows(spaces, fmap, rows, wind=None):
     """Selected rows of A_C (same definition as ``assemble_collocation``), for
     checking large problems on sampled collocation points.  Returns a dense array
     of shape (len(rows), N)."""
@@ -131,6 +147,8 @@ def collocation_rows(spaces, fmap, rows):
             rem //= ns[l]
         xi = np.array([spaces[l].tau[idx[l]] for l in range(d)])
         G, Lv = pullback_coefficients(fmap, xi)
+        if wind is not None:
+            Lv = Lv - wind_coefficients(fmap, xi, wind)
         row = np.zeros(N)
 
         def add(coef, orders):

@@ -102,15 +102,18 @@ def kron_apply(mats, b, shape):
 
 
 class FD:
-    """The FD preconditioner for P = sum_l M (x) .. K_l .. (x) M."""
+    """The FD preconditioner for P = sum_l M (x) .. K_l .. (x) M (with a constant wind w:
+    K_l + H_l = -B''_l + w_l B'_l, Sec. 3.2, eq. convec_prec_2)."""
 
-    def __init__(self, spaces):
+    def __init__(self, spaces, wind=None):
         self.d = len(spaces)
         self.n = [s.n for s in spaces]
         self.shape = tuple(self.n[::-1])
         self.lam, self.U, self.V = [], [], []
-        for s in spaces:
-            lam, U, V = eig_factors(s.K, s.M)
+        w = np.zeros(self.d) if wind is None else np.asarray(wind, dtype=np.float64)
+        for l, s in enumerate(spaces):
+            K = s.K if w[l] == 0.0 else s.K + w[l] * s.B[1]
+            lam, U, V = eig_factors(K, s.M)
             self.lam.append(lam)
             self.U.append(U)
             self.V.append(V)

@@ -205,6 +205,13 @@ def pullback_coefficients(fmap, xi):
     return G, Lvec
 
 
+def wind_coefficients(fmap, xi, wind):
+    """Coefficients of the convective term w . grad_x (u_hat o F^{-1}) of eq. (convection)
+    (Sec. 3.2) at the parametric point xi, for a constant wind w: grad_x u = J^{-T}
+    grad_xi u_hat, so w . grad_x u = sum_c (J^{-1} w)_c d_c u_hat.  Returns J^{-1} w."""
+    return np.linalg.solve(fmap.J(xi), np.asarray(wind, dtype=np.float64))
+
+
 def annulus_closed_form(r0, r1, xi):
     """Polar form of -Lap for the quarter annulus (pin for ``pullback_coefficients``):
     -Lap u = -(1/R^2) u_xixi - 1/(R r) u_xi - 4/(pi^2 r^2) u_etaeta, R = r1 - r0."""

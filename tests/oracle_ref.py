@@ -12,15 +12,18 @@ class Ref:
     """Oracle view of one problem: spaces, map, collocation points, FD, and (for
     sizes where it is affordable) the assembled A_C."""
 
-    def __init__(self, d, n_elem, p, geometry="annulus", r0=1.0, r1=2.0, assemble=True):
+    def __init__(self, d, n_elem, p, geometry="annulus", r0=1.0, r1=2.0, assemble=True,
+                 wind=None):
         self.d, self.n_elem, self.p = d, n_elem, p
+        self.wind = None if wind is None else np.asarray(wind, dtype=np.float64)
         self.fmap = Geo.make_map(geometry, d, r0, r1)
         self.spaces = [C.Space1D(n_elem, p) for _ in range(d)]
         self.n = self.spaces[0].n
         self.N = self.n ** d
         self.points = C.physical_points(self.fmap, [s.tau for s in self.spaces])
-        self.fd = F.FD(self.spaces)
-        self.A = C.assemble_collocation(self.spaces, self.fmap) if assemble else None
+        self.fd = F.FD(self.spaces, self.wind)
+        self.A = (C.assemble_collocation(self.spaces, self.fmap, self.wind) if assemble
+                  else None)
         self.r0, self.r1 = r0, r1
 
     def P_apply(self, s):
@@ -28,12 +31,14 @@ class Ref:
         out = np.zeros(self.N)
         shape = tuple([self.n] * self.d)
         for l in range(self.d):
-            mats = [self.spaces[j].K if j == l else self.spaces[j].M for j in range(self.d)]
+            w = 0.0 if self.wind is None else self.wind[l]
+            mats = [C.wind_factor(self.spaces[j], w) if j == l else self.spaces[j].M
+                    for j in range(self.d)]
             out += F.kron_apply(mats, s, shape)
         return out
 
     def rows(self, idx):
-        return C.collocation_rows(self.spaces, self.fmap, idx)
+        return C.collocation_rows(self.spaces, self.fmap, idx, self.wind)
 
     def gmres(self, b, M="fd", tol=1e-8, max_iter=200, flexible=False):
         Mop = self.fd if M == "fd" else None
@@ -44,5 +49,6 @@ class Ref:
 
 
 @functools.lru_cache(maxsize=32)
-def ref(d, n_elem, p, geometry="annulus", r0=1.0, r1=2.0, assemble=True):
-    return Ref(d, n_elem, p, geometry, r0, r1, assemble)
+def ref(d, n_elem, p, geometry="annulus", r0=1.0, r1=2.0, assemble=True, wind=None):
+    """``wind``: None or a tuple of d floats (hashable, for the cache)."""
+    return Ref(d, n_elem, p, geometry, r0, r1, assemble, wind)

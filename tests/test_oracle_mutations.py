@@ -79,3 +79,16 @@ def test_bicgstab_mistakes_are_caught(monkeypatch, old, new):
     _bicgstab_with(monkeypatch, old, new)
     with pytest.raises(AssertionError):
         TB.test_matches_scipy_at_fixed_step_counts(2, 8, 3)
+
+
+def test_wrong_sign_or_transpose_of_wind_term_is_caught(monkeypatch):
+    import tests.test_oracle_wind as TW
+    orig = Geo.wind_coefficients
+    monkeypatch.setattr(C, "wind_coefficients", lambda fmap, xi, w: -orig(fmap, xi, w))
+    with pytest.raises(AssertionError):
+        TW.test_convective_term_against_finite_differences()
+    # J^{-T} w instead of J^{-1} w
+    monkeypatch.setattr(C, "wind_coefficients",
+                        lambda fmap, xi, w: np.linalg.solve(fmap.J(xi).T, np.asarray(w)))
+    with pytest.raises(AssertionError):
+        TW.test_convective_term_against_finite_differences()
