@@ -45,6 +45,11 @@ REVOLVED_TEXT = ("3d_revolved_ne64: 3D quarter ring r in [1,2] revolved by pi/2 
                  "perturbation, FP64 FD-GMRES to 1e-8")
 
 
+WIND_TEXT = ("3d_wind_ne64: convection-diffusion -Lap + w.grad (Sec. 3.2) with w = (5,5,5) on "
+             "the 3D extruded quarter annulus, 64 elements/dir, p=3,4,5, f = 1 + seeded 1e-3 "
+             "perturbation, FD of the wind-shifted pencils, FP64 FD-GMRES to 1e-8")
+
+
 def geometry_of(c):
     return c.get("geometry", "annulus")
 
@@ -59,10 +64,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-bicgstab", action="store_true")
     ap.add_argument("--workload", default="3d_ne64",
-                    choices=["3d_ne64", "3d_revolved_ne64", "batched", "served"],
+                    choices=["3d_ne64", "3d_revolved_ne64", "3d_wind_ne64", "batched", "served"],
                     help="3d_ne64 (default bench line), 3d_revolved_ne64 (Sec. 5's revolved "
-                         "ring, same measurement), batched (256 2D problems x 8 rhs), served "
-                         "(Poisson request stream)")
+                         "ring, same measurement), 3d_wind_ne64 (Sec. 3.2 convection-diffusion), "
+                         "batched (256 2D problems x 8 rhs), served (Poisson request stream)")
     ap.add_argument("--precision", default="tf32", help="preconditioner precision for the "
                                                         "batched / served forms")
     ap.add_argument("--count", type=int, default=256, help="problems in the batched form")
@@ -172,10 +177,10 @@ def run_reference(args):
     p = c["ps"][0]
     spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
     fmap = Geo.make_map(geometry_of(c), 3, c["r0"], c["r1"])
-    A = C.assemble_collocation(spaces, fmap)
+    A = C.assemble_collocation(spaces, fmap, c.get("wind"))
     pts = C.physical_points(fmap, [s.tau for s in spaces])
     b = W.config_rhs(WORKLOAD, pts, 0)
-    fd = F.FD(spaces)
+    fd = F.FD(spaces, c.get("wind"))
     N = A.shape[0]
     times, dofit = [], 0
     for it in range(args.warmup + args.steps):
@@ -213,10 +218,10 @@ def cpu_baseline_sample(budget_s=15.0):
     p = c["ps"][0]
     spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
     fmap = Geo.make_map(geometry_of(c), 3, c["r0"], c["r1"])
-    A = C.assemble_collocation(spaces, fmap)
+    A = C.assemble_collocation(spaces, fmap, c.get("wind"))
     pts = C.physical_points(fmap, [s.tau for s in spaces])
     b = W.config_rhs(WORKLOAD, pts, 0)
-    fd = F.FD(spaces)
+    fd = F.FD(spaces, c.get("wind"))
     N = A.shape[0]
     dofit, spent, solves, its = 0, 0.0, 0, 0
     while spent < budget_s and solves < 50:
@@ -250,6 +255,7 @@ def run_ours(args):
         probs = []
         for i, p in enumerate(c["ps"]):
             P = Problem(3, c["n_elem"], p, geometry_of(c), c["r0"], c["r1"], precision=prec,
+                        wind=c.get("wind"),
                         device=dev, stream=stream)
             pts = P.collocation_points()
             rhs = torch.from_numpy(W.config_rhs(WORKLOAD, pts, i)).to(dev)
@@ -548,10 +554,12 @@ def run_served(args):
 
 def main():
     args = parse()
-    if args.workload == "3d_revolved_ne64":
+    if args.workload in ("3d_revolved_ne64", "3d_wind_ne64"):
         global WORKLOAD
-        WORKLOAD = "3d_revolved_ne64"
-        CONFIG["workload"] = REVOLVED_TEXT
+        WORKLOAD = args.workload
+        CONFIG["workload"] = REVOLVED_TEXT if args.workload == "3d_revolved_ne64" else WIND_TEXT
+        if args.workload == "3d_wind_ne64":
+            args.no_mixed = True  # the wind path runs the FP64 FD only
         args.workload = "3d_ne64"
     if args.impl == "reference":
         return run_reference(args)

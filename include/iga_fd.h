@@ -68,6 +68,14 @@ typedef struct {
   int kind;       /* iga_geom_kind */
   double r_inner; /* ring radii (ignored for IDENTITY); 0 < r_inner < r_outer */
   double r_outer;
+  /* Constant wind w (physical components; entries past d ignored).  Zero: the Poisson
+   * problem of eq. (poisson).  Nonzero: the convection-diffusion operator
+   * -Lap + w . grad of Sec. 3.2 (eq. convection), collocated like -Lap, and the FD
+   * preconditioner of eq. (convec_prec_2) in collocation form, direction l factor
+   * K_l + H_l = -B''_l + w_l B'_l.  Requires precision FP64 or NONE.  The FD needs the
+   * shifted pencils to be diagonalizable with a well-conditioned eigenvector basis:
+   * on these meshes that holds for |w_l| up to about 10 (NOT_DIAGONALIZABLE beyond). */
+  double wind[3];
 } iga_geometry;
 
 /* Precision of the preconditioner apply (Sec. 4 FD).  FP64: plain GMRES with an

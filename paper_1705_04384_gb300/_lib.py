@@ -16,7 +16,8 @@ c_ll_p = ctypes.POINTER(ctypes.c_longlong)
 
 
 class Geometry(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double)]
+    _fields_ = [("kind", ctypes.c_int), ("r_inner", ctypes.c_double), ("r_outer", ctypes.c_double),
+                ("wind", ctypes.c_double * 3)]
 
 
 # name -> (restype, argtypes); mirrors include/iga_fd.h

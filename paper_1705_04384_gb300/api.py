@@ -27,7 +27,7 @@ class Problem:
     """One collocation problem: ``iga_setup`` ... ``iga_destroy``."""
 
     def __init__(self, d, n_elem, p, geometry="annulus", r_inner=1.0, r_outer=2.0,
-                 precision="fp64", device="cuda", stream=None, grid="latency"):
+                 precision="fp64", device="cuda", stream=None, grid="latency", wind=None):
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.d, self.n_elem, self.p = d, n_elem, p
@@ -38,6 +38,10 @@ class Problem:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         g = Geometry(GEOM[geometry], float(r_inner), float(r_outer))
+        self.wind = tuple(float(w) for w in wind) if wind is not None else None
+        if self.wind is not None:
+            for l, w in enumerate(self.wind[:3]):
+                g.wind[l] = w
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(self.lib.iga_setup(d, n_elem, p, ctypes.byref(g), PREC[precision],

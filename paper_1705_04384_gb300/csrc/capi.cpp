@@ -56,6 +56,8 @@ iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom, int pre
       throw iga::Error{IGA_ERR_INVALID_ARG, "need 0 < r_inner < r_outer"};
     if (geom->kind == IGA_GEOM_REVOLVED_ANNULUS && d != 3)
       throw iga::Error{IGA_ERR_INVALID_ARG, "the revolved ring is 3D"};
+    for (int l = 0; l < d; ++l)
+      if (!std::isfinite(geom->wind[l])) throw iga::Error{IGA_ERR_INVALID_ARG, "wind must be finite"};
     const double n = n_elem + p - 2;
     if (std::pow(n, d) > 2.0e9) throw iga::Error{IGA_ERR_INVALID_ARG, "problem too large"};
     iga_ctx *h = new iga_ctx();
@@ -91,7 +93,8 @@ iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host) {
   return guarded([&]() -> iga_status {
     if (!h || !out_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
     if (dir < 0 || dir >= h->c.d) throw iga::Error{IGA_ERR_INVALID_ARG, "bad direction"};
-    const iga::Factor1D &f = *h->c.fac;
+    const iga::Factor1D &f = *h->c.fac;            // collocation factors
+    const iga::Factor1D &fd = *h->c.facd[dir];     // FD factors of this direction
     const int n = f.n, W = f.W;
     auto dense = [&](int o, double sign) {
       std::memset(out_host, 0, sizeof(double) * n * n);
@@ -104,9 +107,9 @@ iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host) {
       case IGA_FACTOR_M: dense(0, 1.0); break;
       case IGA_FACTOR_B1: dense(1, 1.0); break;
       case IGA_FACTOR_K: dense(2, -1.0); break;
-      case IGA_FACTOR_LAMBDA: std::memcpy(out_host, f.lam.data(), sizeof(double) * n); break;
-      case IGA_FACTOR_U: std::memcpy(out_host, f.U.data(), sizeof(double) * n * n); break;
-      case IGA_FACTOR_VT: std::memcpy(out_host, f.Vt.data(), sizeof(double) * n * n); break;
+      case IGA_FACTOR_LAMBDA: std::memcpy(out_host, fd.lam.data(), sizeof(double) * n); break;
+      case IGA_FACTOR_U: std::memcpy(out_host, fd.U.data(), sizeof(double) * n * n); break;
+      case IGA_FACTOR_VT: std::memcpy(out_host, fd.Vt.data(), sizeof(double) * n * n); break;
       default: throw iga::Error{IGA_ERR_INVALID_ARG, "bad factor selector"};
     }
     return IGA_OK;

@@ -47,7 +47,9 @@ struct Ctx {
   int prec = IGA_PREC_FP64;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  std::shared_ptr<Factor1D> fac;
+  std::shared_ptr<Factor1D> fac;       // bands (operator) and the Poisson FD factors
+  std::shared_ptr<Factor1D> facd[3];   // FD factors of each direction (pencil K + w_l B', M)
+  bool fold_ok = false;                // one folded factor set serves every direction
   BandDev band{};
 
   DevBuf<double> fields;

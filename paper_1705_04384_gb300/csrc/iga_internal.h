@@ -173,14 +173,20 @@ struct Factor1D {
   bool folded = false;
   int ne = 0;
   DevBuf<double> d_Bf, d_Bi, d_lam_fold;
+  // FD pencil (K + shift B', M): shift = w_l, the wind of the direction (Sec. 3.2)
+  double shift = 0.0;
 };
 
 struct FdScale;
 template <class Tout>
 void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
                            int M, int n, int ne, const FdScale *scale, cudaStream_t s, int nrhs);
+template <class Tout>
+void launch_gemm_fp64_dense_mma(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
+                                int M, int n, const FdScale *scale, cudaStream_t s, int nrhs);
 
-std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream);
+// 1D factors of (n_elem, p) with the FD pencil (K + shift B', M), cached per device.
+std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, double shift = 0.0);
 void build_basis_1d(Factor1D &f);  // host part (knots, tau, bands)
 
 // Operations that touch device-wide state -- stream capture of a solve graph, the
@@ -256,6 +262,9 @@ struct FdScale {
 // and (if dinv32 != nullptr) FP32.
 void launch_fd_diag_inverse(const double *lam, int n, int d, double *dinv, float *dinv32,
                             cudaStream_t s);
+// the same with the eigenvalues of each direction (lam3 unused for d = 2)
+void launch_fd_diag_inverse3(const double *lam1, const double *lam2, const double *lam3, int n,
+                             int d, double *dinv, float *dinv32, cudaStream_t s);
 // nrhs right-hand sides stacked as the slowest index (M = nrhs * rows per rhs).
 template <class Tout>
 void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out, int M, int N,

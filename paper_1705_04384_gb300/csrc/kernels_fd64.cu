@@ -119,6 +119,8 @@ __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, do
 }
 
 // One run: column groups cg .. cg+len-1 of block blk for the 8 rows of row tile rt.
+// DIR 0 / 1: folded forward / inverse product; DIR 2: dense product (no fold, one block
+// of n columns, K = n; the caller passes ne = n), for pencils without parity.
 template <class Tout, int DIR>
 __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
                                              const double *__restrict__ Bt, Tout *__restrict__ O,
@@ -138,18 +140,18 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
 #pragma unroll
     for (int j = 0; j < kMmaNGB; ++j) acc[u][j][0] = acc[u][j][1] = 0.0;
 #pragma unroll
-  for (int u = 0; u < (DIR == 0 ? 1 : 2); ++u) {
+  for (int u = 0; u < (DIR == 1 ? 2 : 1); ++u) {
     // DIR 0: one contraction of length Nb over the block's folded entries;
-    // DIR 1: pe over k < ne (u = 0), po over k >= ne (u = 1)
+    // DIR 1: pe over k < ne (u = 0), po over k >= ne (u = 1); DIR 2: k < n
     const int kb = DIR == 0 ? (blk ? ne : 0) : (u ? ne : 0);
-    const int K = DIR == 0 ? Nb : (u ? no : ne);
+    const int K = DIR == 1 ? (u ? no : ne) : Nb;
 #pragma unroll 2
     for (int s = 0; s < K; s += 4) {
       const int k = s + t;
       const bool kv = k < K;
       double a = 0.0;
       if (rv && kv) {
-        if (DIR == 1) a = x[kb + k];
+        if (DIR != 0) a = x[kb + k];
         else if (!blk) a = k < h ? x[k] + x[n - 1 - k] : x[h];
         else a = x[k] - x[n - 1 - k];
       }
@@ -157,7 +159,7 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
       for (int j = 0; j < kMmaNGB; ++j) {
         // DIR 1: a group starting at or past h holds only the middle index (n odd),
         // whose odd part vanishes
-        if (j < len && (DIR == 0 || u == 0 || c0 + 8 * j < h)) {
+        if (j < len && (DIR != 1 || u == 0 || c0 + 8 * j < h)) {
           // columns past the block's end (its last group may be partial) multiply zeros
           const int cl = c0 + 8 * j + g;
           const double b =
@@ -178,7 +180,7 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
     for (int i = 0; i < 2; ++i) {
       const int cl = c0 + 8 * j + 2 * t + i;
       if (cl >= Nb) continue;
-      if (DIR == 0) {
+      if (DIR != 1) {
         const int col = brow0 + cl;
         double v = acc[0][j][i];
         if (has_scale) v *= __ldg(sc.dinv + rl + (long long)rows_per * col);
@@ -196,14 +198,13 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
   }
 }
 
-// Cost of column group j of a row tile, in units of 1/8 of one m8n8k4 MMA: a full group
-// takes one MMA per k-step, a partial group of r columns r FP64 FMAs and one add per
-// k-step, each 1/8 of an MMA on the FP64 pipe.
+// Cost of column group j of a row tile in MMAs: one per k-step of its contraction(s);
+// a partial last group is padded to a full MMA group.
 __device__ __forceinline__ int fold_group_cost(int DIR, int j, int n, int ne, int g0) {
   const int no = n - ne;
   const int blk = j >= g0 ? 1 : 0;
   const int Nb = (DIR == 0 && blk) ? no : ne;
-  if (DIR == 0) return (Nb + 3) / 4;
+  if (DIR != 1) return (Nb + 3) / 4;
   return (ne + 3) / 4 + (8 * j < n / 2 ? (no + 3) / 4 : 0);
 }
 
@@ -291,6 +292,28 @@ void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, Id
   IGA_LAUNCH_CHECK();
 }
 
+// Dense FP64 mode product on the FP64 tensor path (no parity: wind-shifted pencils):
+// out[rl + P (c + n r)] = sum_k A[row][k] Bt[c][k] (times dinv with a scale).
+template <class Tout>
+void launch_gemm_fp64_dense_mma(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
+                                int M, int n, const FdScale *scale, cudaStream_t s, int nrhs) {
+  const int g0 = (n + 7) / 8;
+  const long long nrt = (M + kMmaRows - 1) / kMmaRows;
+  constexpr int wps = 2;
+  const dim3 grid(num_sms()), block(32 * kMmaWarps * wps);
+  FdScale sc = scale ? *scale : FdScale{nullptr, nullptr, nullptr, 1};
+  launch_pdl(kPdlFd64, fd_fold_mma_kernel<Tout, 2>, grid, block, 0, s, A, Bt, out, M, n, n, g0, 0,
+             nrt, M / nrhs, sc, scale ? 1 : 0);
+  IGA_LAUNCH_CHECK();
+}
+
+template void launch_gemm_fp64_dense_mma<double>(IdxPtr<const double>, const double *,
+                                                 IdxPtr<double>, int, int, const FdScale *,
+                                                 cudaStream_t, int);
+template void launch_gemm_fp64_dense_mma<float>(IdxPtr<const double>, const double *,
+                                                IdxPtr<float>, int, int, const FdScale *,
+                                                cudaStream_t, int);
+
 template void launch_gemm_fp64_fold<double>(int, IdxPtr<const double>, const double *,
                                             IdxPtr<double>, int, int, int, const FdScale *,
                                             cudaStream_t, int);
@@ -309,6 +332,29 @@ __global__ void fd_diag_inverse_kernel(const double *__restrict__ lam, int n, in
     if (dinv) dinv[i] = v;
     if (dinv32) dinv32[i] = (float)v;
   }
+}
+
+__global__ void fd_diag_inverse3_kernel(const double *__restrict__ lam1,
+                                        const double *__restrict__ lam2,
+                                        const double *__restrict__ lam3, int n, int d,
+                                        double *__restrict__ dinv, float *__restrict__ dinv32) {
+  const long long N = d == 2 ? (long long)n * n : (long long)n * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    double den = lam1[i % n] + lam2[(i / n) % n];
+    if (d == 3) den += lam3[i / ((long long)n * n)];
+    const double v = 1.0 / den;
+    if (dinv) dinv[i] = v;
+    if (dinv32) dinv32[i] = (float)v;
+  }
+}
+
+void launch_fd_diag_inverse3(const double *lam1, const double *lam2, const double *lam3, int n,
+                             int d, double *dinv, float *dinv32, cudaStream_t s) {
+  const long long N = d == 2 ? (long long)n * n : (long long)n * n * n;
+  const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 8);
+  fd_diag_inverse3_kernel<<<blocks, 256, 0, s>>>(lam1, lam2, lam3, n, d, dinv, dinv32);
+  IGA_LAUNCH_CHECK();
 }
 
 void launch_fd_diag_inverse(const double *lam, int n, int d, double *dinv, float *dinv32,
@@ -339,10 +385,13 @@ void preload_kernels_fd64() {
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_kernel<double>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, gemm_fp64_kernel<float>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_diag_inverse_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_diag_inverse3_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<double, 0>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<double, 1>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<float, 0>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<float, 1>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<double, 2>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, fd_fold_mma_kernel<float, 2>));
 }
 
 }  // namespace iga

@@ -106,7 +106,8 @@ __device__ static void inv_small(int d, const double J[3][3], double Ji[3][3]) {
 
 // fields[f * ldf + i]: q_aa = -G^{aa}, q_ab = -2 G^{ab} (a < b), q_c = -L_c, ordered
 // as in field_desc(): 2D (11, 22, 12, 1, 2), 3D (11, 22, 33, 12, 13, 23, 1, 2, 3).
-__global__ void geometry_fields_kernel(int d, int kind, double r0, double r1, const double *tau1,
+__global__ void geometry_fields_kernel(int d, int kind, double r0, double r1, double w0,
+                                       double w1, double w2, const double *tau1,
                                        const double *tau2, const double *tau3, int n1, int n2,
                                        int n3, double *fields, long long ldf) {
   const long long N = (long long)n1 * n2 * n3;
@@ -134,11 +135,17 @@ __global__ void geometry_fields_kernel(int d, int kind, double r0, double r1, co
         for (int b = 0; b < d; ++b) s += G[a][b] * g.H[k][a][b];
       lapF[k] = s;
     }
+    // first-order coefficients: -L_c of -Lap, plus (J^{-1} w)_c of the convective term
+    // w . grad_x u = sum_c (J^{-1} w)_c d_c u_hat (Sec. 3.2, constant wind)
+    const double wv[3] = {w0, w1, w2};
     double L[3];
     for (int c = 0; c < d; ++c) {
-      double s = 0.0;
-      for (int k = 0; k < d; ++k) s += Ji[c][k] * lapF[k];
-      L[c] = -s;
+      double s = 0.0, sw = 0.0;
+      for (int k = 0; k < d; ++k) {
+        s += Ji[c][k] * lapF[k];
+        sw += Ji[c][k] * wv[k];
+      }
+      L[c] = -s - sw;  // the fields hold -L_c
     }
     if (d == 2) {
       fields[0 * ldf + i] = -G[0][0];
@@ -166,8 +173,9 @@ void launch_geometry_fields(int d, const iga_geometry &g, const double *tau1, co
   const long long N = (long long)n1 * n2 * n3;
   const int threads = 256;
   const int blocks = (int)std::min<long long>((N + threads - 1) / threads, 152LL * 16);
-  geometry_fields_kernel<<<blocks, threads, 0, s>>>(d, g.kind, g.r_inner, g.r_outer, tau1, tau2,
-                                                    tau3, n1, n2, n3, fields, ldf);
+  geometry_fields_kernel<<<blocks, threads, 0, s>>>(d, g.kind, g.r_inner, g.r_outer, g.wind[0],
+                                                    g.wind[1], d == 3 ? g.wind[2] : 0.0, tau1,
+                                                    tau2, tau3, n1, n2, n3, fields, ldf);
   IGA_LAUNCH_CHECK();
 }
 

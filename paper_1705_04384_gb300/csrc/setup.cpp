@@ -312,7 +312,7 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
     for (int t = 0; t < W; ++t) {
       const int j = f.start[i] + t;
       Mc[i + (size_t)n * j] = f.band[0][(size_t)i * W + t];
-      Kc[i + (size_t)n * j] = -f.band[2][(size_t)i * W + t];
+      Kc[i + (size_t)n * j] = -f.band[2][(size_t)i * W + t] + f.shift * f.band[1][(size_t)i * W + t];
     }
   SolverHandle sh;
   CUSOLVER_TRY(cusolverDnCreate(&sh.h));
@@ -515,12 +515,14 @@ void ensure_kernels_loaded() {
 }
 
 // ------------------------------------------------------------------ factor cache
-std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream) {
+std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, double shift) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int>, std::weak_ptr<Factor1D>> cache;
+  static std::map<std::tuple<int, int, int, long long>, std::weak_ptr<Factor1D>> cache;
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(dev, n_elem, p);
+  long long sbits = 0;
+  std::memcpy(&sbits, &shift, sizeof(sbits));
+  const auto key = std::make_tuple(dev, n_elem, p, sbits);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -533,6 +535,7 @@ std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream) {
   auto f = std::make_shared<Factor1D>();
   f->n_elem = n_elem;
   f->p = p;
+  f->shift = shift;
   build_basis_1d(*f);
   {
     std::lock_guard<std::mutex> dlk(device_mutex());

@@ -50,6 +50,14 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   stream = s_;
   ensure_kernels_loaded();
   fac = get_factor(n_elem, p, stream);
+  bool has_wind = false;
+  for (int l = 0; l < d; ++l) has_wind = has_wind || geom.wind[l] != 0.0;
+  if (has_wind && (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16))
+    throw Error{IGA_ERR_INVALID_ARG, "a wind requires precision FP64 or NONE"};
+  // per-direction FD factors: the pencil (K + w_l B', M) of Sec. 3.2 (w_l = 0: Poisson)
+  for (int l = 0; l < 3; ++l)
+    facd[l] = (l >= d || geom.wind[l] == 0.0) ? fac : get_factor(n_elem, p, stream, geom.wind[l]);
+  fold_ok = fac->folded && !has_wind;
   n = fac->n;
   N = 1;
   for (int l = 0; l < d; ++l) N *= n;
@@ -115,10 +123,14 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
     plan.terms[plan.nterm++] = ContractTerm{input, fd.order[0], fields.ptr + active[a] * ldf};
   }
   if (prec == IGA_PREC_FP64) {
-    // the FP64 chain uses the folded eigen-order when the factors have parity
+    // the FP64 chain uses the folded eigen-order when one factor set with parity serves
+    // every direction, else each direction's own eigenvalues
     dinv.alloc(N);
-    launch_fd_diag_inverse(fac->folded ? fac->d_lam_fold.ptr : fac->d_lam.ptr, n, d, dinv.ptr,
-                           nullptr, stream);
+    if (fold_ok)
+      launch_fd_diag_inverse(fac->d_lam_fold.ptr, n, d, dinv.ptr, nullptr, stream);
+    else
+      launch_fd_diag_inverse3(facd[0]->d_lam.ptr, facd[1]->d_lam.ptr, facd[2]->d_lam.ptr, n, d,
+                              dinv.ptr, nullptr, stream);
   } else if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) {
     dinv32.alloc(N);
     launch_fd_diag_inverse(fac->d_lam.ptr, n, d, nullptr, dinv32.ptr, stream);
@@ -195,7 +207,7 @@ static void fd_chain_fp64(const Ctx &c, IdxPtr<const double> in, IdxPtr<Tout> ou
   const int M = (int)(R * (c.N / n));
   auto P = [](double *p) { return plain_ptr<double>(p); };
   auto Pc = [](const double *p) { return plain_ptr<const double>(p); };
-  if (f.folded) {
+  if (c.fold_ok) {
     // d forward products (the last one fused with the diagonal), d inverse products,
     // each on folded vectors with half the FMAs of a dense product
     FdScale sc{nullptr, nullptr, nullptr, n, c.dinv.ptr};
@@ -214,20 +226,24 @@ static void fd_chain_fp64(const Ctx &c, IdxPtr<const double> in, IdxPtr<Tout> ou
     }
     return;
   }
+  // dense products: the g-th forward (inverse) product contracts direction g with that
+  // direction's V^T (U); the diagonal (dinv, each direction's eigenvalues) is fused into
+  // the d-th forward product
+  const Factor1D &f0 = *c.facd[0], &f1 = *c.facd[1], &f2 = *c.facd[2];
   if (c.d == 2) {
-    FdScale sc{f.d_lam.ptr, nullptr, f.d_lam.ptr, n, c.dinv.ptr};
-    launch_gemm_fp64<double>(in, f.d_Vt.ptr, P(t0), M, n, n, nullptr, s, R);
-    launch_gemm_fp64<double>(Pc(t0), f.d_Vt.ptr, P(t1), M, n, n, &sc, s, R);
-    launch_gemm_fp64<double>(Pc(t1), f.d_U.ptr, P(t0), M, n, n, nullptr, s, R);
-    launch_gemm_fp64<Tout>(Pc(t0), f.d_U.ptr, out, M, n, n, nullptr, s, R);
+    FdScale sc{f0.d_lam.ptr, nullptr, f1.d_lam.ptr, n, c.dinv.ptr};
+    launch_gemm_fp64_dense_mma<double>(in, f0.d_Vt.ptr, P(t0), M, n, nullptr, s, R);
+    launch_gemm_fp64_dense_mma<double>(Pc(t0), f1.d_Vt.ptr, P(t1), M, n, &sc, s, R);
+    launch_gemm_fp64_dense_mma<double>(Pc(t1), f0.d_U.ptr, P(t0), M, n, nullptr, s, R);
+    launch_gemm_fp64_dense_mma<Tout>(Pc(t0), f1.d_U.ptr, out, M, n, nullptr, s, R);
   } else {
-    FdScale sc{f.d_lam.ptr, f.d_lam.ptr, f.d_lam.ptr, n, c.dinv.ptr};
-    launch_gemm_fp64<double>(in, f.d_Vt.ptr, P(t0), M, n, n, nullptr, s, R);
-    launch_gemm_fp64<double>(Pc(t0), f.d_Vt.ptr, P(t1), M, n, n, nullptr, s, R);
-    launch_gemm_fp64<double>(Pc(t1), f.d_Vt.ptr, P(t0), M, n, n, &sc, s, R);
-    launch_gemm_fp64<double>(Pc(t0), f.d_U.ptr, P(t1), M, n, n, nullptr, s, R);
-    launch_gemm_fp64<double>(Pc(t1), f.d_U.ptr, P(t0), M, n, n, nullptr, s, R);
-    launch_gemm_fp64<Tout>(Pc(t0), f.d_U.ptr, out, M, n, n, nullptr, s, R);
+    FdScale sc{f0.d_lam.ptr, f1.d_lam.ptr, f2.d_lam.ptr, n, c.dinv.ptr};
+    launch_gemm_fp64_dense_mma<double>(in, f0.d_Vt.ptr, P(t0), M, n, nullptr, s, R);
+    launch_gemm_fp64_dense_mma<double>(Pc(t0), f1.d_Vt.ptr, P(t1), M, n, nullptr, s, R);
+    launch_gemm_fp64_dense_mma<double>(Pc(t1), f2.d_Vt.ptr, P(t0), M, n, &sc, s, R);
+    launch_gemm_fp64_dense_mma<double>(Pc(t0), f0.d_U.ptr, P(t1), M, n, nullptr, s, R);
+    launch_gemm_fp64_dense_mma<double>(Pc(t1), f1.d_U.ptr, P(t0), M, n, nullptr, s, R);
+    launch_gemm_fp64_dense_mma<Tout>(Pc(t0), f2.d_U.ptr, out, M, n, nullptr, s, R);
   }
 }
 

@@ -71,3 +71,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.iga_destroy(None) == 0
     assert lib.iga_set_grid_mode(None, 0) == 1
     assert b"null handle" in lib.iga_last_error()
+    w = Geometry(1, 1.0, 2.0)
+    w.wind[1] = float("inf")
+    assert lib.iga_setup(2, 32, 3, ctypes.byref(w), 0, None, ctypes.byref(h)) == 1
+    assert b"wind" in lib.iga_last_error()

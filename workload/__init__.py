@@ -32,6 +32,10 @@ CONFIGS = {
     # (-1,-1,-1); f = 1 (no closed-form solution is given for it) with the same perturbation
     "3d_revolved_ne64": dict(d=3, n_elem=64, ps=[3, 4, 5], r0=1.0, r1=2.0,
                              geometry="revolved", rhs="constant", sigma=1e-3, seed=0),
+    # Sec. 3.2's convection-diffusion operator -Lap + w . grad on the extruded ring with
+    # a constant wind (5, 5, 5); f = 1 with the same perturbation
+    "3d_wind_ne64": dict(d=3, n_elem=64, ps=[3, 4, 5], r0=1.0, r1=2.0,
+                         wind=(5.0, 5.0, 5.0), rhs="constant", sigma=1e-3, seed=0),
 }
 
 
