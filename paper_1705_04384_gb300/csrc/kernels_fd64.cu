@@ -106,10 +106,13 @@ __global__ void __launch_bounds__(kThreads)
 // grid sized to the SM count takes an equal contiguous range of it: each SM sub-partition
 // receives the same number of FMAs whatever M and n are.  A warp forms the folded
 // A-fragment of a k-step once and feeds up to kMmaNGB column groups of the same row tile
-// and block with it.  A block's last group, when it has fewer than 8 columns, runs on
-// FP64 FMAs with the k-steps split over the four lanes of a fragment row and a
-// two-step shuffle reduction.  Each output is written by one lane, in a fixed order:
-// the results are bitwise reproducible.
+// and block with it.  A block's last group, when it has fewer than 8 columns, is padded
+// to a full MMA group with zero factor entries.  FP64 FMAs and MMAs share the FP64 pipe
+// of an SM sub-partition and their pipe times add (measured on GB300: 619 cycles per
+// m8n8k4, 81 per warp FMA), but computing the partial group on FMAs instead, as an item
+// of its own, measured slower (the FMA items' latency lands in the tail of the split).
+// Each output is written by one lane, in a fixed order: the results are bitwise
+// reproducible.
 constexpr int kMmaWarps = 4, kMmaRows = 8, kMmaNGB = 4;
 
 __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, double b) {

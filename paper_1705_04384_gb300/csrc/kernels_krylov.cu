@@ -224,13 +224,18 @@ void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
 
 // ------------------------------------------------------------------ CGS2
 // Dots of vectors V_r[j0 .. j0+cnt) with u over this block's rows, two rows per step
-// so that the loads of both are in flight together; block-reduced into partials.
+// so that the loads of both are in flight together; block-reduced into partials.  Index
+// jself (if in range) stands for u itself: its dot is ||u||^2 over the rows.
 __device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, int cnt,
                                            const double *__restrict__ u, long long lo,
-                                           long long hi, double *part, double (*red)[kJC]) {
+                                           long long hi, double *part, double (*red)[kJC],
+                                           int jself = -1) {
   const double *vb[kJC];
 #pragma unroll
-  for (int q = 0; q < kJC; ++q) vb[q] = Vvec(ws, j0 + min(q, cnt - 1), r);
+  for (int q = 0; q < kJC; ++q) {
+    const int j = j0 + min(q, cnt - 1);
+    vb[q] = j == jself ? u : Vvec(ws, j, r);
+  }
   double acc[kJC] = {};
   long long i = lo + threadIdx.x;
   for (; i + kRT < hi; i += 2 * kRT) {
@@ -255,13 +260,14 @@ __device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, in
   block_store_partials(acc, cnt, j0, part, gridDim.x, red);
 }
 
-// u_r[i] -= sum_j V_r[j][i] h[j] for this block's rows, two rows per step with two
-// partial sums each (independent FMA chains).
+// dst[i] = (u_r[i] - sum_j V_r[j][i] h[j]) (* scale with kScale) for this block's rows,
+// two rows per step with two partial sums each (independent FMA chains).  dst may be u.
+template <bool kScale = false>
 __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
-                                              const double *__restrict__ h, double *u,
-                                              long long lo, long long hi, double *norm2) {
+                                              const double *__restrict__ h, const double *u,
+                                              long long lo, long long hi, double *dst,
+                                              double scale = 1.0) {
   long long i = lo + threadIdx.x;
-  double nn = 0.0;
   for (; i + kRT < hi; i += 2 * kRT) {
     double s0a = 0.0, s0b = 0.0, s1a = 0.0, s1b = 0.0;
     int j = 0;
@@ -279,10 +285,13 @@ __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
       s0a = fma(v0[i], hj, s0a);
       s1a = fma(v0[i + kRT], hj, s1a);
     }
-    const double x0 = u[i] - (s0a + s0b), x1 = u[i + kRT] - (s1a + s1b);
-    u[i] = x0;
-    u[i + kRT] = x1;
-    nn = fma(x1, x1, fma(x0, x0, nn));
+    double x0 = u[i] - (s0a + s0b), x1 = u[i + kRT] - (s1a + s1b);
+    if (kScale) {
+      x0 *= scale;
+      x1 *= scale;
+    }
+    dst[i] = x0;
+    dst[i + kRT] = x1;
   }
   if (i < hi) {
     double sa = 0.0, sb = 0.0;
@@ -292,11 +301,10 @@ __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
       sb = fma(Vvec(ws, j + 1, r)[i], __ldg(h + j + 1), sb);
     }
     if (j < nv) sa = fma(Vvec(ws, j, r)[i], __ldg(h + j), sa);
-    const double x0 = u[i] - (sa + sb);
-    u[i] = x0;
-    nn = fma(x0, x0, nn);
+    double x0 = u[i] - (sa + sb);
+    if (kScale) x0 *= scale;
+    dst[i] = x0;
   }
-  if (norm2) *norm2 = nn;
 }
 
 // pass 1: h1 = V_r^T w_r -> H_r[0..k, k]
@@ -319,7 +327,11 @@ __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const doubl
   }
 }
 
-// pass 2: w_r -= V_r h1; h2 = V_r^T w_r -> H_r[0..k,k] += h2, y_r = h2
+// pass 2: w_r -= V_r h1; h2 = V_r^T w_r -> H_r[0..k,k] += h2, y_r = h2; nu = ||w_r||^2;
+// H_r[k+1,k] = sqrt(nu - ||h2||^2), the norm of w_r - V_r h2 (V_r orthonormal), so
+// that pass 3 needs no reduction of its own.  After the first projection w_r is
+// orthogonal to V_r to working accuracy, ||h2|| <= ||w_r|| times a small multiple of the
+// unit roundoff, and the difference loses no significant digits.
 __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
@@ -331,54 +343,42 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
     double *wr = w + (long long)r * ws.N;
     const double *h1 = Hcol(ws, r, k);
     double *part = ws.partials + r * ws.pstride;
-    subtract_proj(ws, r, nv, h1, wr, lo, hi, nullptr);
-    for (int j0 = 0; j0 < nv; j0 += kJC)
-      chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
+    subtract_proj(ws, r, nv, h1, wr, lo, hi, wr);
+    for (int j0 = 0; j0 <= nv; j0 += kJC)
+      chunk_dots(ws, r, j0, min(kJC, nv + 1 - j0), wr, lo, hi, part, red, nv);
     if (!arrive_last(ws.counter + r)) continue;
-    last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, ws.y + r * (ws.max_iter + 2));
+    double *y = ws.y + r * (ws.max_iter + 2);
+    last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, y);
+    last_block_reduce(part + (long long)nv * gridDim.x, gridDim.x, 1, ws.scal + 8 * r + 2, 0,
+                      nullptr);
     __syncthreads();
-    if (threadIdx.x == 0) ws.counter[r] = 0;
+    if (threadIdx.x < 32) {
+      double q = 0.0;
+      for (int j = threadIdx.x; j < nv; j += 32) q = fma(y[j], y[j], q);
+      q = warp_sum(q);
+      if (threadIdx.x == 0) {
+        const double b2 = ws.scal[8 * r + 2] - q;
+        Hcol(ws, r, k)[k + 1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+        ws.counter[r] = 0;
+      }
+    }
   }
 }
 
-// pass 3: w_r -= V_r h2; H_r[k+1,k] = ||w_r||
-__global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, double *__restrict__ w) {
+// pass 3: v_{k+1} = (w_r - V_r h2) / H_r[k+1,k] (zero on breakdown)
+__global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, const double *__restrict__ w) {
   pdl_entry();
-  __shared__ double red[kWarps][kJC];
   const int k = ws.st->k, nv = k + 1;
   long long lo, hi;
   row_range(ws.N, lo, hi);
   for (int r = 0; r < ws.R; ++r) {
     if (ws.rs[r].done) continue;
-    double *wr = w + (long long)r * ws.N;
-    const double *h2 = ws.y + r * (ws.max_iter + 2);
-    double *part = ws.partials + r * ws.pstride;
-    double acc[kJC] = {};
-    subtract_proj(ws, r, nv, h2, wr, lo, hi, &acc[0]);
-    block_store_partials(acc, 1, 0, part, gridDim.x, red);
-    if (!arrive_last(ws.counter + r)) continue;
-    last_block_reduce(part, gridDim.x, 1, ws.scal + 8 * r + 2, 0, nullptr);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Hcol(ws, r, k)[k + 1] = sqrt(ws.scal[8 * r + 2]);
-      ws.counter[r] = 0;
-    }
-  }
-}
-
-// v_{k+1} = w / H[k+1,k]
-__global__ void normalize_kernel(KrylovWs ws, const double *__restrict__ w) {
-  pdl_entry();
-  const int k = ws.st->k;
-  for (int r = 0; r < ws.R; ++r) {
-    if (ws.rs[r].done) continue;
-    const double h = Hcol(ws, r, k)[k + 1];
-    const double inv = h > 0.0 ? 1.0 / h : 0.0;
-    double *v = ws.V + ((long long)(k + 1) * ws.R + r) * ws.N;
     const double *wr = w + (long long)r * ws.N;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ws.N;
-         i += (long long)gridDim.x * blockDim.x)
-      v[i] = wr[i] * inv;
+    const double *h2 = ws.y + r * (ws.max_iter + 2);
+    const double hn = Hcol(ws, r, k)[k + 1];
+    const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    double *v = ws.V + ((long long)(k + 1) * ws.R + r) * ws.N;
+    subtract_proj<true>(ws, r, nv, h2, wr, lo, hi, v, inv);
   }
 }
 
@@ -388,9 +388,7 @@ void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s) {
   IGA_LAUNCH_CHECK();
   launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), 0, s, ws, w);
   IGA_LAUNCH_CHECK();
-  launch_pdl(kPdlKrylov, cgs_pass3_kernel, grid, dim3(kRT), 0, s, ws, w);
-  IGA_LAUNCH_CHECK();
-  launch_pdl(kPdlKrylov, normalize_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
+  launch_pdl(kPdlKrylov, cgs_pass3_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
 }
 
@@ -609,7 +607,6 @@ void preload_kernels_krylov() {
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass2_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass3_kernel));
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, normalize_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, givens_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, backsolve_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, update_x_kernel<double>));
