@@ -233,6 +233,13 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
                       int dir, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
                       int nrhs = 1);
 
+// Several banded mode products along one direction in one launch: output q is
+// B^{(orders[q])}_dir applied to ins[in_of[q]] (nin <= 3 FP64 inputs, nout <= 6 outputs);
+// each input's taps are loaded once per point for all of its outputs.
+void launch_band_pass_multi(const double *const *ins, int nin, double *const *outs,
+                            const int *in_of, const int *orders, int nout, int dir, int n1, int n2,
+                            int n3, const BandDev &b, cudaStream_t s, int nrhs = 1);
+
 // Final pass along direction 0 with contraction by the coefficient fields:
 // out = sum_t coef_t(x) * B^{(order_t)}_0 in[input_t].
 struct ContractTerm {

@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, d
                                                         FastDiv divB, BandDev b) {
   pdl_entry();
   const Tin *in = inp.get();
-  const double *bands[3] = {b.band0, b.band1, b.band2};
-  const double *B0 = bands[ord0], *B1 = bands[ord1], *B2 = bands[ord2];
+  auto band = [&](int o) { return o == 0 ? b.band0 : (o == 1 ? b.band1 : b.band2); };
+  const double *B0 = band(ord0), *B1 = band(ord1), *B2 = band(ord2);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const unsigned qa = dir == 0 ? i : fdiv(i, divA);
     const int c = (int)(qa - fdiv(qa, divB) * divB.d);
@@ -255,12 +255,95 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
   IGA_LAUNCH_CHECK();
 }
 
+struct BandMulti {
+  const double *in[3];
+  double *out[6];
+  int in_of[6];
+  int ord[6];
+  int nin, nout;
+};
+
+// The band passes of several inputs along one direction in one launch (see
+// band_pass_kernel): per point, each input's W taps are loaded once and feed all outputs
+// that read it.
+template <int W>
+__global__ void __launch_bounds__(256) band_pass_multi_kernel(BandMulti m, int dir, unsigned N,
+                                                              int stride, FastDiv divA,
+                                                              FastDiv divB, BandDev b) {
+  pdl_entry();
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const unsigned qa = dir == 0 ? i : fdiv(i, divA);
+    const int c = (int)(qa - fdiv(qa, divB) * divB.d);
+    const int off = (int)i + (__ldg(b.start + c) - c) * stride;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= m.nin) break;
+      const double *src = m.in[a] + off;
+      double v[W];
+#pragma unroll
+      for (int t = 0; t < W; ++t) v[t] = __ldg(src + t * stride);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        if (q >= m.nout || m.in_of[q] != a) continue;
+        const int o = m.ord[q];
+        const double *B = (o == 0 ? b.band0 : (o == 1 ? b.band1 : b.band2)) + c * W;
+        double acc = 0.0;
+#pragma unroll
+        for (int t = 0; t < W; ++t) acc = fma(__ldg(B + t), v[t], acc);
+        m.out[q][i] = acc;
+      }
+    }
+  }
+}
+
+void launch_band_pass_multi(const double *const *ins, int nin, double *const *outs,
+                            const int *in_of, const int *orders, int nout, int dir, int n1, int n2,
+                            int n3, const BandDev &b, cudaStream_t s, int nrhs) {
+  if (nin < 1 || nin > 3 || nout < 1 || nout > 6)
+    throw Error{IGA_ERR_INVALID_ARG, "band pass: 1..3 inputs and 1..6 outputs"};
+  const long long N = (long long)n1 * n2 * n3 * nrhs;
+  if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per operator pass"};
+  BandMulti m{};
+  for (int a = 0; a < nin; ++a) m.in[a] = ins[a];
+  for (int q = 0; q < nout; ++q) {
+    if (in_of[q] < 0 || in_of[q] >= nin) throw Error{IGA_ERR_INVALID_ARG, "band pass input index"};
+    m.out[q] = outs[q];
+    m.in_of[q] = in_of[q];
+    m.ord[q] = orders[q];
+  }
+  m.nin = nin;
+  m.nout = nout;
+  const int threads = 256, blocks = grid_for(N, threads);
+  const int stride = dir == 0 ? 1 : (dir == 1 ? n1 : n1 * n2);
+  const FastDiv divA = make_fastdiv(dir == 2 ? (unsigned)(n1 * n2) : (unsigned)n1);
+  const FastDiv divB = make_fastdiv(dir == 0 ? (unsigned)n1 : (dir == 1 ? (unsigned)n2 : (unsigned)n3));
+#define IGA_BANDM_CASE(WW)                                                                       \
+  case WW:                                                                                       \
+    launch_pdl(kPdlOperator, band_pass_multi_kernel<WW>, dim3(blocks), dim3(threads), 0, s, m,   \
+               dir, (unsigned)N, stride, divA, divB, b);                                         \
+    break;
+  switch (b.W) {
+    IGA_BANDM_CASE(3)
+    IGA_BANDM_CASE(4)
+    IGA_BANDM_CASE(5)
+    IGA_BANDM_CASE(6)
+    IGA_BANDM_CASE(7)
+    default:
+      throw Error{IGA_ERR_INVALID_ARG, "band width out of range"};
+  }
+#undef IGA_BANDM_CASE
+  IGA_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------ contraction pass
+// Per-term arguments, resolved on the host: term t reads src[t] (an intermediate of the
+// earlier passes) with the band of order[t] along direction 0 and the field coef[t].  The
+// kernel unrolls over the terms so that it indexes its parameters statically (no local
+// copy of the arrays).
 template <class Tin> struct ContractArgsT {
-  IdxPtr<const Tin> in[6];
-  int term_input[kMaxFields];
-  int term_order[kMaxFields];
-  const double *term_coef[kMaxFields];
+  const Tin *src[kMaxFields];
+  int order[kMaxFields];
+  const double *coef[kMaxFields];
   int nterm;
 };
 
@@ -269,23 +352,22 @@ __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a
                                                             unsigned N, FastDiv div1,
                                                             FastDiv divN1, BandDev b) {
   pdl_entry();
-  const double *bands[3] = {b.band0, b.band1, b.band2};
-  const Tin *ins[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) ins[q] = a.in[q].base ? a.in[q].get() : nullptr;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const int c = (int)(i - fdiv(i, div1) * div1.d);         // coordinate along direction 0
     const unsigned ic = i - fdiv(i, divN1) * divN1.d;         // point index of one rhs
     const int st = __ldg(b.start + c);
     const int base = (int)i + (st - c);
     double acc = 0.0;
-    for (int t = 0; t < a.nterm; ++t) {
-      const Tin *src = ins[a.term_input[t]] + base;
-      const double *B = bands[a.term_order[t]] + c * W;
+#pragma unroll
+    for (int t = 0; t < kMaxFields; ++t) {
+      if (t >= a.nterm) break;
+      const Tin *src = a.src[t] + base;
+      const int o = a.order[t];
+      const double *B = (o == 0 ? b.band0 : (o == 1 ? b.band1 : b.band2)) + c * W;
       double s = 0.0;
 #pragma unroll
       for (int q = 0; q < W; ++q) s = fma(__ldg(B + q), ld_val(src + q), s);
-      acc = fma(__ldg(a.term_coef[t] + ic), s, acc);
+      acc = fma(__ldg(a.coef[t] + ic), s, acc);
     }
     out[i] = acc;
   }
@@ -295,15 +377,15 @@ template <class Tin>
 void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *terms, int nterm,
                           double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
                           int nrhs) {
+  if (nterm < 0 || nterm > kMaxFields) throw Error{IGA_ERR_INVALID_ARG, "contraction terms"};
   ContractArgsT<Tin> a{};
-  int maxin = 0;
   for (int t = 0; t < nterm; ++t) {
-    a.term_input[t] = terms[t].input;
-    a.term_order[t] = terms[t].order;
-    a.term_coef[t] = terms[t].coef;
-    maxin = std::max(maxin, terms[t].input + 1);
+    const IdxPtr<const Tin> &in = ins[terms[t].input];
+    if (in.idx) throw Error{IGA_ERR_INVALID_ARG, "contraction inputs must be plain pointers"};
+    a.src[t] = in.base;
+    a.order[t] = terms[t].order;
+    a.coef[t] = terms[t].coef;
   }
-  for (int q = 0; q < 6; ++q) a.in[q] = q < maxin ? ins[q] : IdxPtr<const Tin>{nullptr, nullptr, 0, 0};
   a.nterm = nterm;
   const long long N = (long long)n1 * n2 * n3 * nrhs;
   if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per operator pass"};
@@ -362,6 +444,7 @@ template <class Tin, int W> static void preload_op_w() {
   cudaFuncAttributes a;
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_kernel<Tin, W>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, contract_pass_kernel<Tin, W>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_multi_kernel<W>));
 }
 
 void preload_kernels_geom_op() {

@@ -176,19 +176,12 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t 
   if (d == 2) {
     for (int q = 0; q < plan.nA; ++q) ins[q] = plain_ptr<const double>(TA[q]);
   } else {
-    for (int a = 0; a < plan.nA; ++a) {
-      double *outs[3];
-      int ords[3], cnt = 0;
-      for (int q = 0; q < plan.nB; ++q)
-        if (plan.B_in[q] == a) {
-          outs[cnt] = TB[q];
-          ords[cnt] = plan.B_ord[q];
-          ++cnt;
-        }
-      if (cnt)
-        launch_band_pass<double>(plain_ptr<const double>(TA[a]), outs, ords, cnt, 1, n, n, n3,
-                                 band, s, R);
-    }
+    // all second-direction passes in one launch
+    const double *ina[3];
+    for (int a = 0; a < plan.nA; ++a) ina[a] = TA[a];
+    if (plan.nB > 0)
+      launch_band_pass_multi(ina, plan.nA, TB, plan.B_in, plan.B_ord, plan.nB, 1, n, n, n3, band,
+                             s, R);
     for (int q = 0; q < plan.nB; ++q) ins[q] = plain_ptr<const double>(TB[q]);
   }
   launch_contract_pass<double>(ins, plan.terms, plan.nterm, out, n, n, n3, band, s, R);
