@@ -101,6 +101,9 @@ struct Ctx {
   int pend_R = 0, pend_max_iter = 0;
   double pend_tol = 0.0;
   cudaEvent_t done_ev = nullptr;
+  // an Arnoldi step forks the Givens kernel onto side_stream beside the last CGS2 pass
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
   ~Ctx();
   void setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_);

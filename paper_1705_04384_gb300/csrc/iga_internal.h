@@ -290,6 +290,8 @@ struct RhsState {
 
 struct SolveState {
   int k;            // Arnoldi step shared by all right-hand sides
+  int kv;           // the step whose basis vector the third CGS2 pass writes (k before
+                    // the Givens kernel, which runs beside that pass, advances it)
   int active;       // right-hand sides still iterating
   int max_iter;
   int R;
@@ -352,7 +354,10 @@ void launch_bicg_xr(const BicgWs &ws, cudaGraphConditionalHandle cond, int has_c
 void launch_bicg_residual(const BicgWs &ws, const double *b, const double *Ax, cudaStream_t s);
 void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
                        cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);
-void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s);
+// CGS2 in two parts: passes 1 and 2 (coefficients, the subdiagonal entry), then pass 3
+// (the next basis vector), which may run beside the Givens kernel of the same step.
+void launch_cgs2_coeffs(const KrylovWs &ws, double *w, cudaStream_t s);
+void launch_cgs2_vector(const KrylovWs &ws, const double *w, cudaStream_t s);
 void launch_givens(const KrylovWs &ws, cudaGraphConditionalHandle cond, int has_cond,
                    cudaStream_t s);
 void launch_finish(const KrylovWs &ws, const double *x0, int use_x0, double *x, cudaStream_t s);

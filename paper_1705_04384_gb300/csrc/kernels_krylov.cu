@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
   pdl_entry();
   __shared__ double red[kWarps][kJC];
   const int k = ws.st->k, nv = k + 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ws.st->kv = k;
   long long lo, hi;
   row_range(ws.N, lo, hi);
   for (int r = 0; r < ws.R; ++r) {
@@ -358,37 +359,45 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
       q = warp_sum(q);
       if (threadIdx.x == 0) {
         const double b2 = ws.scal[8 * r + 2] - q;
-        Hcol(ws, r, k)[k + 1] = b2 > 0.0 ? sqrt(b2) : 0.0;
+        const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+        Hcol(ws, r, k)[k + 1] = beta;  // the Givens kernel rotates this entry away
+        ws.scal[8 * r + 4] = beta;     // pass 3 reads this copy
         ws.counter[r] = 0;
       }
     }
   }
 }
 
-// pass 3: v_{k+1} = (w_r - V_r h2) / H_r[k+1,k] (zero on breakdown)
+// pass 3: v_{k+1} = (w_r - V_r h2) / H_r[k+1,k] (zero on breakdown).  It runs beside the
+// Givens kernel of the same step, which advances k, sets the done flags and rotates H:
+// the step comes from kv and the norm from its copy in scal.  A right-hand side that the
+// Givens kernel has just retired may or may not get its v_{k+1}; it is never read.
 __global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, const double *__restrict__ w) {
   pdl_entry();
-  const int k = ws.st->k, nv = k + 1;
+  const int k = ws.st->kv, nv = k + 1;
   long long lo, hi;
   row_range(ws.N, lo, hi);
   for (int r = 0; r < ws.R; ++r) {
     if (ws.rs[r].done) continue;
     const double *wr = w + (long long)r * ws.N;
     const double *h2 = ws.y + r * (ws.max_iter + 2);
-    const double hn = Hcol(ws, r, k)[k + 1];
+    const double hn = ws.scal[8 * r + 4];
     const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
     double *v = ws.V + ((long long)(k + 1) * ws.R + r) * ws.N;
     subtract_proj<true>(ws, r, nv, h2, wr, lo, hi, v, inv);
   }
 }
 
-void launch_cgs2(const KrylovWs &ws, double *w, cudaStream_t s) {
+void launch_cgs2_coeffs(const KrylovWs &ws, double *w, cudaStream_t s) {
   const dim3 grid(ws.nblk);
   launch_pdl(kPdlKrylov, cgs_pass1_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
   launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), 0, s, ws, w);
   IGA_LAUNCH_CHECK();
-  launch_pdl(kPdlKrylov, cgs_pass3_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
+}
+
+void launch_cgs2_vector(const KrylovWs &ws, const double *w, cudaStream_t s) {
+  launch_pdl(kPdlKrylov, cgs_pass3_kernel, dim3(ws.nblk), dim3(kRT), 0, s, ws, w);
   IGA_LAUNCH_CHECK();
 }
 

@@ -19,6 +19,9 @@ Ctx::~Ctx() {
   if (pending && done_ev) cudaEventSynchronize(done_ev);
   drop_graphs();
   if (done_ev) cudaEventDestroy(done_ev);
+  if (fork_ev) cudaEventDestroy(fork_ev);
+  if (join_ev) cudaEventDestroy(join_ev);
+  if (side_stream) cudaStreamDestroy(side_stream);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (h_st) cudaFreeHost(h_st);
   if (h_rs) cudaFreeHost(h_rs);
@@ -65,6 +68,9 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
                  fac->W};
   IGA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
   IGA_CUDA_TRY(cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
+  IGA_CUDA_TRY(cudaStreamCreateWithFlags(&side_stream, cudaStreamNonBlocking));
+  IGA_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  IGA_CUDA_TRY(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
 
   // geometry coefficient fields at the collocation points
   const int nf = num_fields(d);
@@ -346,8 +352,15 @@ void Ctx::launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaSt
     tc_fd_apply(*tc, vk, zk, R, s);
     apply_operator<float>(IdxPtr<const float>{(const float *)ws.Z, kptr, 0, blk}, w.ptr, R, s);
   }
-  launch_cgs2(ws, w.ptr, s);
-  launch_givens(ws, cond, has_cond, s);
+  launch_cgs2_coeffs(ws, w.ptr, s);
+  // the Givens update of column k needs only passes 1 and 2: it runs on a side stream
+  // beside pass 3, and the step ends when both have finished
+  IGA_CUDA_TRY(cudaEventRecord(fork_ev, s));
+  IGA_CUDA_TRY(cudaStreamWaitEvent(side_stream, fork_ev, 0));
+  launch_givens(ws, cond, has_cond, side_stream);
+  launch_cgs2_vector(ws, w.ptr, s);
+  IGA_CUDA_TRY(cudaEventRecord(join_ev, side_stream));
+  IGA_CUDA_TRY(cudaStreamWaitEvent(s, join_ev, 0));
 }
 
 void Ctx::launch_solve_prologue(int use_x0, cudaGraphConditionalHandle cond, int has_cond,
