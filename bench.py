@@ -167,6 +167,24 @@ def committed_traffic(summary="fd_fold_mma_3d_ne64.md"):
     return float(vals["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in vals else None
 
 
+def aggregate(units, seconds, device=None):
+    """Replicas: the units (DOF-iterations) all ranks processed and the longest time any
+    rank took (sum and max over the process group when one is initialised)."""
+    try:
+        import torch.distributed as dist
+        active = dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+    except ImportError:
+        active = False
+    if not active:
+        return float(units), float(seconds)
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def percentile(vals, q):
     return float(np.percentile(np.asarray(vals, dtype=np.float64), q)) if vals else None
 
@@ -318,14 +336,11 @@ def run_ours(args):
     clk = clocks.stop()
     step_times = [sum(s[3] for s in step) for step in res64]
     dof_iters = [sum(s[1] * s[2] for s in step) for step in res64]
-    total_t = sum(step_times)
+    all_units, total_t = aggregate(sum(dof_iters), sum(step_times), dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_t = float(t.item())
         dist.barrier()
-    value = world * sum(dof_iters) / total_t
+    value = all_units / total_t
     solve_ms = [s[3] * 1e3 for step in res64 for s in step]
     iters = {str(s[0]): s[2] for s in res64[-1]}
     relres = {str(s[0]): s[4] for s in res64[-1]}
@@ -388,15 +403,16 @@ def run_ours(args):
     for P, hr, hx in host:
         h2d += P.N * 8
         d2h += P.N * 8 + (MAX_ITER + 1) * 8 + 64
-    e2e = {"value": world * e2e_dofit / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
+    eu, et = aggregate(e2e_dofit, sum(e2e_times), dev)
+    e2e = {"value": eu / et, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     mixed_out = None
     if mixed is not None:
         resm = timed(mixed, args.steps, args.warmup)
         mt = sum(sum(s[3] for s in step) for step in resm)
         md = sum(sum(s[1] * s[2] for s in step) for step in resm)
-        mixed_out = {"value": world * md / mt, "unit": UNIT,
+        mu, mtx = aggregate(md, mt, dev)
+        mixed_out = {"value": mu / mtx, "unit": UNIT,
                      "iters": {str(s[0]): s[2] for s in resm[-1]},
                      "relres_true": {str(s[0]): s[4] for s in resm[-1]},
                      "p50_ms": percentile([s[3] * 1e3 for st in resm for s in st], 50),
@@ -411,7 +427,8 @@ def run_ours(args):
         resb = timed(fp64, max(1, args.steps // 2), args.warmup, "bicgstab")
         bt = sum(sum(s[3] for s in step) for step in resb)
         bd = sum(sum(s[1] * s[2] for s in step) for step in resb)
-        bicg_out = {"value": world * bd / bt, "unit": "DOF-iter/s (BiCGStab iterations)",
+        bu, btx = aggregate(bd, bt, dev)
+        bicg_out = {"value": bu / btx, "unit": "DOF-iter/s (BiCGStab iterations)",
                     "iters": {str(s[0]): s[2] for s in resb[-1]},
                     "relres_true": {str(s[0]): s[4] for s in resb[-1]},
                     "p50_ms": percentile([s[3] * 1e3 for st in resb for s in st], 50),
