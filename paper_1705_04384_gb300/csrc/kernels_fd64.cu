@@ -106,13 +106,16 @@ __global__ void __launch_bounds__(kThreads)
 // grid sized to the SM count takes an equal contiguous range of it: each SM sub-partition
 // receives the same number of FMAs whatever M and n are.  A warp forms the folded
 // A-fragment of a k-step once and feeds up to kMmaNGB column groups of the same row tile
-// and block with it.  A block's last group, when it has fewer than 8 columns, is padded
-// to a full MMA group with zero factor entries.  FP64 FMAs and MMAs share the FP64 pipe
-// of an SM sub-partition and their pipe times add (measured on GB300: 619 cycles per
-// m8n8k4, 81 per warp FMA), but computing the partial group on FMAs instead, as an item
-// of its own, measured slower (the FMA items' latency lands in the tail of the split).
-// Each output is written by one lane, in a fixed order: the results are bitwise
-// reproducible.
+// and block with it.  FP64 FMAs and MMAs share the FP64 pipe of an SM sub-partition and
+// their pipe times add (measured on GB300: 619 cycles per m8n8k4, 81 per warp FMA, and a
+// batch of fewer than eight FMAs among a warp's MMAs costs an MMA slot).  So the last
+// K mod 4 entries of a contraction (n = 65: the middle entry of the even block) run as
+// FMAs on the accumulator fragments, in one batch after the run's MMAs, instead of an MMA
+// k-step that would be mostly zero padding.  A block's last group, when it has fewer than
+// 8 columns, is padded to a full MMA group with zero factor entries: computing it on FMAs
+// as an item of its own measured slower (the FMA items' latency lands in the tail of the
+// work split).  Each output is written by one lane, in a fixed order: the results are
+// bitwise reproducible.
 constexpr int kMmaWarps = 4, kMmaRows = 8, kMmaNGB = 4;
 
 __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, double b) {
@@ -142,22 +145,24 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int j = 0; j < kMmaNGB; ++j) acc[u][j][0] = acc[u][j][1] = 0.0;
+  // the folded input entry k of contraction u (k < that contraction's length)
+  auto a_at = [&](int u, int k) -> double {
+    if (!rv) return 0.0;
+    if (DIR != 0) return x[(u ? ne : 0) + k];
+    if (!blk) return k < h ? x[k] + x[n - 1 - k] : x[h];
+    return x[k] - x[n - 1 - k];
+  };
 #pragma unroll
   for (int u = 0; u < (DIR == 1 ? 2 : 1); ++u) {
     // DIR 0: one contraction of length Nb over the block's folded entries;
-    // DIR 1: pe over k < ne (u = 0), po over k >= ne (u = 1); DIR 2: k < n
+    // DIR 1: pe over k < ne (u = 0), po over k >= ne (u = 1); DIR 2: k < n.
+    // The MMAs take the whole k-steps; the last K mod 4 entries follow on FMAs.
     const int kb = DIR == 0 ? (blk ? ne : 0) : (u ? ne : 0);
-    const int K = DIR == 1 ? (u ? no : ne) : Nb;
+    const int K4 = (DIR == 1 ? (u ? no : ne) : Nb) & ~3;
 #pragma unroll 2
-    for (int s = 0; s < K; s += 4) {
+    for (int s = 0; s < K4; s += 4) {
       const int k = s + t;
-      const bool kv = k < K;
-      double a = 0.0;
-      if (rv && kv) {
-        if (DIR != 0) a = x[kb + k];
-        else if (!blk) a = k < h ? x[k] + x[n - 1 - k] : x[h];
-        else a = x[k] - x[n - 1 - k];
-      }
+      const double a = a_at(u, k);
 #pragma unroll
       for (int j = 0; j < kMmaNGB; ++j) {
         // DIR 1: a group starting at or past h holds only the middle index (n odd),
@@ -165,9 +170,31 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
         if (j < len && (DIR != 1 || u == 0 || c0 + 8 * j < h)) {
           // columns past the block's end (its last group may be partial) multiply zeros
           const int cl = c0 + 8 * j + g;
-          const double b =
-              (kv && cl < Nb) ? __ldg(Bt + (long long)(brow0 + cl) * n + kb + k) : 0.0;
+          const double b = cl < Nb ? __ldg(Bt + (long long)(brow0 + cl) * n + kb + k) : 0.0;
           dmma_m8n8k4(acc[u][j][0], acc[u][j][1], a, b);
+        }
+      }
+    }
+  }
+  // The last K mod 4 entries of each contraction (n = 65: the middle entry of the even
+  // block) on FP64 FMAs into the accumulator fragments (lane (g, t) holds row g, columns
+  // 2t and 2t+1), one batch after all of the run's MMAs: 2 FMAs per group and entry in
+  // place of an MMA whose k-step would be mostly zero padding.
+#pragma unroll
+  for (int u = 0; u < (DIR == 1 ? 2 : 1); ++u) {
+    const int kb = DIR == 0 ? (blk ? ne : 0) : (u ? ne : 0);
+    const int K = DIR == 1 ? (u ? no : ne) : Nb;
+    for (int k = K & ~3; k < K; ++k) {
+      const double a = a_at(u, k);
+#pragma unroll
+      for (int j = 0; j < kMmaNGB; ++j) {
+        if (j < len && (DIR != 1 || u == 0 || c0 + 8 * j < h)) {
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const int cl = c0 + 8 * j + 2 * t + i;
+            const double b = cl < Nb ? __ldg(Bt + (long long)(brow0 + cl) * n + kb + k) : 0.0;
+            acc[u][j][i] = fma(a, b, acc[u][j][i]);
+          }
         }
       }
     }
@@ -201,14 +228,20 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
   }
 }
 
-// Cost of column group j of a row tile in MMAs: one per k-step of its contraction(s);
-// a partial last group is padded to a full MMA group.
+// Cost of a contraction of length K for one column group, in eighths of an MMA (about one
+// warp FMA each): an MMA per whole k-step and two FMAs per remaining entry.
+__device__ __forceinline__ int contraction_cost(int K) { return 8 * (K >> 2) + 2 * (K & 3); }
+
+// Cost of column group j of a row tile: its contraction(s) (a partial last group is padded
+// to a full MMA group) plus, in the forward product, the fold add of each k-step shared by
+// a run of up to four groups.
 __device__ __forceinline__ int fold_group_cost(int DIR, int j, int n, int ne, int g0) {
   const int no = n - ne;
   const int blk = j >= g0 ? 1 : 0;
   const int Nb = (DIR == 0 && blk) ? no : ne;
-  if (DIR != 1) return (Nb + 3) / 4;
-  return (ne + 3) / 4 + (8 * j < n / 2 ? (no + 3) / 4 : 0);
+  if (DIR == 2) return contraction_cost(Nb);
+  if (DIR == 0) return contraction_cost(Nb) + (Nb >> 2) / 2;
+  return contraction_cost(ne) + (8 * j < n / 2 ? contraction_cost(no) : 0);
 }
 
 // First item of the cost share `target` (0 <= target <= total): the smallest item i with
