@@ -111,17 +111,93 @@ __global__ void __launch_bounds__(kThreads)
 // batch of fewer than eight FMAs among a warp's MMAs costs an MMA slot).  So the last
 // K mod 4 entries of a contraction (n = 65: the middle entry of the even block) run as
 // FMAs on the accumulator fragments, in one batch after the run's MMAs, instead of an MMA
-// k-step that would be mostly zero padding.  A block's last group, when it has fewer than
-// 8 columns, is padded to a full MMA group with zero factor entries: computing it on FMAs
-// as an item of its own measured slower (the FMA items' latency lands in the tail of the
-// work split).  Each output is written by one lane, in a fixed order: the results are
-// bitwise reproducible.
-constexpr int kMmaWarps = 4, kMmaRows = 8, kMmaNGB = 4;
+// k-step that would be mostly zero padding.  A block's last group, when it has at most
+// kPartFma columns and the contraction is at most kPartFmaMaxK long (n = 65: the 33rd even
+// column), also runs on FMAs at the end of the run (fold_partial_fma, the column count a
+// template argument); otherwise it is padded to a full MMA group with zero factor entries.
+// The work split counts both kinds of work in eighths of an MMA.  Each output is written by
+// one lane, in a fixed order: the results are bitwise reproducible.
+constexpr int kMmaWarps = 4, kMmaWps = 2, kMmaRows = 8, kMmaNGB = 4, kPartFma = 5,
+              kPartFmaMaxK = 128;
 
 __device__ __forceinline__ void dmma_m8n8k4(double &c0, double &c1, double a, double b) {
   asm("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
       : "+d"(c0), "+d"(c1)
       : "d"(a), "d"(b));
+}
+
+// A block's last column group when it holds PC <= kPartFma columns (cp0 .. cp0+PC-1), on
+// FP64 FMAs: lane (g, t) takes row g and the entries k = t (mod 4) of each contraction, four
+// of them per batch (loads first), and two xor-shuffles finish the sums.  PC is a
+// template argument so that no FMA is issued for a column that does not exist.
+template <class Tout, int DIR, int PC>
+__device__ __forceinline__ void fold_partial_fma(const double *__restrict__ x, bool rv, int row,
+                                                 const double *__restrict__ Bt,
+                                                 Tout *__restrict__ O, int n, int ne, int blk,
+                                                 int cp0, int Nb, int rows_per,
+                                                 const FdScale &sc, int has_scale) {
+  const int t = threadIdx.x & 3;
+  const int h = n / 2, no = n - ne;
+  const int brow0 = (DIR == 0 && blk) ? ne : 0;
+  double acc[2][PC];
+#pragma unroll
+  for (int c = 0; c < PC; ++c) acc[0][c] = acc[1][c] = 0.0;
+#pragma unroll
+  for (int u = 0; u < (DIR == 1 ? 2 : 1); ++u) {
+    if (DIR == 1 && u == 1 && cp0 >= h) break;  // only the middle index: no odd part
+    const int K = DIR == 1 ? (u ? no : ne) : Nb;
+    const int kb = DIR == 0 ? (blk ? ne : 0) : (u ? ne : 0);
+    for (int k0 = t; k0 < K; k0 += 16) {
+      double a[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + 4 * q;
+        a[q] = 0.0;
+        if (rv && k < K) {
+          if (DIR != 0) a[q] = x[kb + k];
+          else if (!blk) a[q] = k < h ? x[k] + x[n - 1 - k] : x[h];
+          else a[q] = x[k] - x[n - 1 - k];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + 4 * q;
+        if (k < K) {
+#pragma unroll
+          for (int c = 0; c < PC; ++c)
+            if (DIR != 1 || u == 0 || cp0 + c < h)
+              acc[u][c] = fma(a[q], __ldg(Bt + (long long)(brow0 + cp0 + c) * n + kb + k),
+                              acc[u][c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < (DIR == 1 ? 2 : 1); ++u)
+#pragma unroll
+    for (int c = 0; c < PC; ++c) {
+      acc[u][c] += __shfl_xor_sync(0xffffffffu, acc[u][c], 1);
+      acc[u][c] += __shfl_xor_sync(0xffffffffu, acc[u][c], 2);
+    }
+  if (!rv) return;
+  const int rl = row % rows_per, rr = row / rows_per;
+  const long long base = rl + (long long)rows_per * (long long)n * rr;
+#pragma unroll
+  for (int c = 0; c < PC; ++c) {
+    if ((c & 3) != t) continue;
+    const int cl = cp0 + c;
+    if (DIR != 1) {
+      const int col = brow0 + cl;
+      double v = acc[0][c];
+      if (has_scale) v *= __ldg(sc.dinv + rl + (long long)rows_per * col);
+      O[base + (long long)rows_per * col] = (Tout)v;
+    } else if (cl < h) {
+      O[base + (long long)rows_per * cl] = (Tout)(acc[0][c] + acc[1][c]);
+      O[base + (long long)rows_per * (n - 1 - cl)] = (Tout)(acc[0][c] - acc[1][c]);
+    } else {
+      O[base + (long long)rows_per * cl] = (Tout)acc[0][c];  // middle index, n odd
+    }
+  }
 }
 
 // One run: column groups cg .. cg+len-1 of block blk for the 8 rows of row tile rt.
@@ -140,6 +216,12 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
   const double *__restrict__ x = A + (long long)(rv ? row : 0) * n;
   const int c0 = cg * 8;                         // first block-local column of the run
   const int brow0 = (DIR == 0 && blk) ? ne : 0;  // factor row of block-local column 0
+  // a run that ends with the block's last group, when that group holds at most kPartFma
+  // columns and the contraction is short (its FMA chains are latency bound: 2D n = 513
+  // measured 4 % slower on FMAs), computes it on FMAs (fold_partial_fma), the rest on MMAs
+  const int gb = (Nb + 7) >> 3, pcl = Nb - 8 * (gb - 1);
+  const bool part = cg + len == gb && pcl <= kPartFma && Nb <= kPartFmaMaxK;
+  if (part) --len;
   double acc[2][kMmaNGB][2];
 #pragma unroll
   for (int u = 0; u < 2; ++u)
@@ -199,6 +281,16 @@ __device__ __forceinline__ void fold_mma_run(const double *__restrict__ A,
       }
     }
   }
+  if (part) {
+    const int cp0 = 8 * (gb - 1);
+    switch (pcl) {
+      case 1: fold_partial_fma<Tout, DIR, 1>(x, rv, row, Bt, O, n, ne, blk, cp0, Nb, rows_per, sc, has_scale); break;
+      case 2: fold_partial_fma<Tout, DIR, 2>(x, rv, row, Bt, O, n, ne, blk, cp0, Nb, rows_per, sc, has_scale); break;
+      case 3: fold_partial_fma<Tout, DIR, 3>(x, rv, row, Bt, O, n, ne, blk, cp0, Nb, rows_per, sc, has_scale); break;
+      case 4: fold_partial_fma<Tout, DIR, 4>(x, rv, row, Bt, O, n, ne, blk, cp0, Nb, rows_per, sc, has_scale); break;
+      default: fold_partial_fma<Tout, DIR, 5>(x, rv, row, Bt, O, n, ne, blk, cp0, Nb, rows_per, sc, has_scale); break;
+    }
+  }
   if (!rv) return;
   const int rl = row % rows_per, rr = row / rows_per;
   const long long base = rl + (long long)rows_per * (long long)n * rr;
@@ -239,6 +331,15 @@ __device__ __forceinline__ int fold_group_cost(int DIR, int j, int n, int ne, in
   const int no = n - ne;
   const int blk = j >= g0 ? 1 : 0;
   const int Nb = (DIR == 0 && blk) ? no : ne;
+  const int jl = blk ? j - g0 : j, gb = (Nb + 7) >> 3, pc = Nb - 8 * (gb - 1);
+  if (jl == gb - 1 && pc <= kPartFma && Nb <= kPartFmaMaxK) {
+    // fold_partial_fma: per batch of 4 entries, a fold add (forward) and pc FMAs
+    auto fcost = [&](int K) { return 4 * ((((K + 3) >> 2) + 3) >> 2); };
+    const int h = n / 2, cp0 = 8 * (gb - 1);
+    if (DIR != 1) return fcost(Nb) * (pc + (DIR == 0 ? 1 : 0)) + 2 * pc;
+    const int pairs = max(0, min(Nb, h) - cp0);
+    return fcost(ne) * pc + (pairs ? fcost(no) * pairs : 0) + 2 * pc + 2 * pairs;
+  }
   if (DIR == 2) return contraction_cost(Nb);
   if (DIR == 0) return contraction_cost(Nb) + (Nb >> 2) / 2;
   return contraction_cost(ne) + (8 * j < n / 2 ? contraction_cost(no) : 0);
@@ -259,7 +360,7 @@ __device__ long long fold_item_at(int DIR, long long target, long long C, int gp
 // share an SM sub-partition take adjacent cost shares, so every sub-partition receives
 // the same FP64 work (up to one item) whatever the item costs are.
 template <class Tout, int DIR>
-__global__ void __launch_bounds__(kMmaWarps * 32 * 4)
+__global__ void __launch_bounds__(kMmaWarps * 32 * kMmaWps)
     fd_fold_mma_kernel(IdxPtr<const double> Ap, const double *__restrict__ Bt, IdxPtr<Tout> Op,
                        int M, int n, int ne, int g0, int g1, long long nrt, int rows_per,
                        FdScale sc, int has_scale) {
@@ -316,7 +417,7 @@ void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, Id
   const long long nrt = (M + kMmaRows - 1) / kMmaRows;
   // two warps per SM sub-partition: while one waits on its loads the other keeps the
   // sub-partition's FP64 MMA unit busy
-  constexpr int wps = 2;
+  constexpr int wps = kMmaWps;
   const dim3 grid(num_sms()), block(32 * kMmaWarps * wps);
   FdScale sc = scale ? *scale : FdScale{nullptr, nullptr, nullptr, 1};
   if (dir == 0)
@@ -335,7 +436,7 @@ void launch_gemm_fp64_dense_mma(IdxPtr<const double> A, const double *Bt, IdxPtr
                                 int M, int n, const FdScale *scale, cudaStream_t s, int nrhs) {
   const int g0 = (n + 7) / 8;
   const long long nrt = (M + kMmaRows - 1) / kMmaRows;
-  constexpr int wps = 2;
+  constexpr int wps = kMmaWps;
   const dim3 grid(num_sms()), block(32 * kMmaWarps * wps);
   FdScale sc = scale ? *scale : FdScale{nullptr, nullptr, nullptr, 1};
   launch_pdl(kPdlFd64, fd_fold_mma_kernel<Tout, 2>, grid, block, 0, s, A, Bt, out, M, n, n, g0, 0,
