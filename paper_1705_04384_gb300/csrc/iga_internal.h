@@ -43,16 +43,19 @@ extern thread_local long long g_launch_count;
 
 // ---------------------------------------------------------------- dependent launch
 // Programmatic dependent launch: a kernel launched with it may be scheduled as soon as
-// every block of the previous kernel in the stream has started; it lets its own
-// successor be scheduled likewise and waits (griddepcontrol.wait) for the previous
-// kernel to complete and its writes to be visible before it touches global memory.
+// every block of the previous kernel in the stream has triggered; it waits
+// (griddepcontrol.wait) for the previous kernel to complete and its writes to be visible
+// before it touches global memory, and then triggers its own successor.
 // In a captured graph the edges become programmatic edges.  Every per-iteration kernel
 // calls pdl_entry() first (a no-op when it was launched without the attribute);
 // launch_pdl is followed by IGA_LAUNCH_CHECK() like <<<>>>.
 #ifdef __CUDACC__
 __device__ __forceinline__ void pdl_entry() {
-  asm volatile("griddepcontrol.launch_dependents;");
+  // wait first: a kernel lets its successor start only once it runs itself, so at most one
+  // kernel waits ahead (triggering before the wait let successive launches cascade and
+  // settle unevenly on the SMs: back-to-back FD applies ran 2x slower)
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
 }
 #endif
 

@@ -364,10 +364,11 @@ __global__ void __launch_bounds__(kMmaWarps * 32 * kMmaWps)
     fd_fold_mma_kernel(IdxPtr<const double> Ap, const double *__restrict__ Bt, IdxPtr<Tout> Op,
                        int M, int n, int ne, int g0, int g1, long long nrt, int rows_per,
                        FdScale sc, int has_scale) {
-  // programmatic dependent launch: the next mode product of the chain may be scheduled
-  // at once (its blocks wait in griddepcontrol.wait until this grid has completed), and
-  // this grid computes its work split before waiting for the previous product's output
-  asm volatile("griddepcontrol.launch_dependents;");
+  // programmatic dependent launch: this grid computes its work split before waiting for
+  // the previous product's output, then lets the next product be scheduled (its blocks
+  // wait in griddepcontrol.wait until this grid has completed).  Triggering only after
+  // the wait keeps at most one product waiting ahead: triggered at entry, back-to-back FD
+  // applies let launches cascade and settle unevenly on the SMs (2x slower).
   const int wpb = blockDim.x >> 5, wps = wpb / kMmaWarps, wi = threadIdx.x >> 5;
   const long long W = (long long)gridDim.x * wpb;
   const long long v = ((long long)blockIdx.x * kMmaWarps + wi % kMmaWarps) * wps + wi / kMmaWarps;
@@ -380,6 +381,7 @@ __global__ void __launch_bounds__(kMmaWarps * 32 * kMmaWps)
       fold_item_at(DIR, total * (v + 1) / W, C, gpr, n, ne, g0);
   const int no = n - ne;
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;");
   const double *__restrict__ A = Ap.get();
   Tout *__restrict__ O = Op.get();
   while (it < iend) {  // warp-uniform
