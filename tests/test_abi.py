@@ -75,3 +75,33 @@ def test_invalid_arguments_rejected_on_host(lib):
     w.wind[1] = float("inf")
     assert lib.iga_setup(2, 32, 3, ctypes.byref(w), 0, None, ctypes.byref(h)) == 1
     assert b"wind" in lib.iga_last_error()
+
+
+def test_every_handle_entry_point_rejects_a_null_handle(lib):
+    """Argument checks happen on the host before any device work (so they run here)."""
+    null = None
+    calls = [
+        ("iga_collocation_points", (null, null)),
+        ("iga_get_factor", (null, 0, 0, null)),
+        ("iga_apply_operator", (null, null, null)),
+        ("iga_precond_apply", (null, null, null)),
+        ("iga_solve_host", (null, null, null, 1e-8, 10, None, null, None)),
+        ("iga_solve_multi", (null, 1, null, null, 0, 1e-8, 10, null, null, null, null)),
+        ("iga_solve_async", (null, 1, null, null, 0, 1e-8, 10)),
+        ("iga_solve_ready", (null, None)),
+        ("iga_solve_collect", (null, null, null, null, null)),
+        ("iga_launch_counts", (null, None, None)),
+        ("iga_prepare", (null, 1, 10)),
+        ("iga_solve_bicgstab", (null, null, null, 0, 1e-8, 10, None, null, None)),
+    ]
+    for name, args in calls:
+        assert getattr(lib, name)(*args) == 1, name  # IGA_ERR_INVALID_ARG
+        assert lib.iga_last_error(), name
+
+
+def test_batch_and_noalloc_argument_checks(lib):
+    assert lib.iga_solve_batched(0, None, None, None, None, 1e-8, 10, None, None, None) == 1
+    assert b"batch" in lib.iga_last_error()
+    # d outside 2..3, then a null factor pointer
+    assert lib.iga_precond_apply_noalloc(4, 10, None, None, None, None, None, None) == 1
+    assert lib.iga_precond_apply_noalloc(3, 10, None, None, None, None, None, None) == 1
