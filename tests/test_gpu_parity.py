@@ -89,7 +89,14 @@ def test_operator_ragged_annulus_radii():
 
 
 @pytest.mark.parametrize("d,ne,p", [(2, 40, 3), (2, 95, 5), (2, 150, 2), (3, 9, 3), (3, 14, 6),
-                                     (3, 20, 4)])
+                                     (3, 20, 4),
+                                     # every branch of the FP64 FD kernel's work split: blocks
+                                     # shorter than one k-step (n = 3, 4), a partial last group
+                                     # of 4 columns (n = 8), exact 8-column groups (n = 16, 256),
+                                     # a 1-column partial group on FMAs (n = 130) and one past the
+                                     # FMA length limit, padded (n = 259)
+                                     (2, 3, 2), (3, 3, 3), (3, 5, 5), (2, 14, 4), (2, 255, 3),
+                                     (2, 130, 2), (2, 258, 3)])
 def test_fd_matches_oracle(d, ne, p):
     R = ref(d, ne, p, assemble=False)
     with _problem(d, ne, p) as P:
