@@ -89,3 +89,34 @@ def test_history_and_true_residual_at_tolerance():
     assert len(out["hist"]) == out["steps"] + 1
     assert out["hist"][-1] <= 1e-8 and np.all(out["hist"][:-1] > 1e-8)
     assert out["relres_true"] <= 1.05e-8
+
+
+def _sec5_table():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sec5_bicgstab_iterations.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            dom, hinv, p, its = line.split()
+            rows.append((dom, int(hinv), int(p), float(its)))
+    return rows
+
+
+def test_iteration_counts_of_the_sec5_tables():
+    """The oracle's BiCGStab + FD on the configurations of Sec. 5's Tables 2 and 4
+    (tests/golden/sec5_bicgstab_iterations.txt) lands within 2.5 iterations of every
+    printed count and within 1.5 on average.  The paper leaves the tolerance and the
+    source term open (f = 1 and 1e-6 here), so the counts are compared with a margin;
+    a wrong operator, preconditioner or iteration count would miss it by far more."""
+    diffs = []
+    for dom, hinv, p, paper in _sec5_table():
+        d, kind = (2, "annulus") if dom == "quarter" else (3, "revolved")
+        spaces = [C.Space1D(hinv, p) for _ in range(d)]
+        fmap = Geo.make_map(kind, d, 1.0, 2.0)
+        A = C.assemble_collocation(spaces, fmap)
+        o = B.bicgstab(A, np.ones(A.shape[0]), M=F.FD(spaces), tol=1e-6, max_iter=200)
+        assert o["flag"] == 0
+        assert abs(o["iters"] - paper) <= 2.5, (dom, hinv, p, o["iters"], paper)
+        diffs.append(abs(o["iters"] - paper))
+    assert np.mean(diffs) <= 1.5
