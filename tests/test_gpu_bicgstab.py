@@ -123,3 +123,29 @@ def test_full_size_3d_ne64():
     assert info["status"] == 0 and abs(info["half_steps"] - want["steps"]) <= 1
     true = np.linalg.norm(b - R.A @ x.cpu().numpy()) / np.linalg.norm(b)
     assert true <= 1.05e-8
+
+
+def test_iteration_counts_of_the_sec5_tables():
+    """The GPU BiCGStab on the smaller configurations of Sec. 5's Tables 2 and 4 (the
+    printed counts in tests/golden/sec5_bicgstab_iterations.txt; f = 1, tol 1e-6, the
+    oracle pinned to them in test_oracle_bicgstab.py): within 2.5 iterations of the
+    paper's count and within one half step of the oracle's."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "sec5_bicgstab_iterations.txt")
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        dom, hinv, p, paper = line.split()
+        hinv, p, paper = int(hinv), int(p), float(paper)
+        if hinv not in (128, 16):
+            continue
+        d, geo = (2, "annulus") if dom == "quarter" else (3, "revolved")
+        R = ref(d, hinv, p, geo)
+        b = np.ones(R.N)
+        want = OB.bicgstab(R.A, b, M=R.fd, tol=1e-6, max_iter=200)
+        with _problem(d, hinv, p, geo) as P:
+            _, info = P.solve_bicgstab(torch.from_numpy(b).cuda(), tol=1e-6, max_iter=200)
+        assert info["status"] == 0
+        assert abs(info["iters"] - paper) <= 2.5, (dom, hinv, p, info["iters"], paper)
+        assert abs(info["half_steps"] - want["steps"]) <= 1
