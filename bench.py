@@ -421,6 +421,11 @@ def run_ours(args):
                      "p50_ms": percentile([s[3] * 1e3 for st in resm for s in st], 50),
                      "p99_ms": percentile([s[3] * 1e3 for st in resm for s in st], 99),
                      "time_to_solution_ms_per_step": 1e3 * mt / len(resm)}
+        # error of the precision form's solution against the FP64 form's (the FP64 GPU
+        # solution equals the oracle's at a fixed step count to 1e-10; both stop at 1e-8)
+        mixed_out["rel_err_vs_fp64"] = {
+            str(p): float(torch.linalg.vector_norm(xm - x) / torch.linalg.vector_norm(x))
+            for (p, _, _, x), (_, _, _, xm) in zip(fp64, mixed)}
 
     # Sec. 5's solver on the same problems: BiCGStab + FP64 FD; an iteration is a BiCG
     # step and a GMRES(1) step (two FD solves, two operator applications), counted in
