@@ -289,6 +289,198 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, (uint32_t)tmem_cols);
 }
 
+// ------------------------------------------------------------------ persistent GEMM kernel
+// The same product with a grid of at most (SMs x resident CTAs) that loops over the tiles,
+// row tile fastest (the order in which the one-tile grid above is launched).  Per CTA the
+// setup (barriers, TMEM allocation, tensor-map fetch) is paid once, the TMA ring runs
+// ahead across tile boundaries, and two TMEM accumulators let the epilogue of tile i
+// overlap the main loop of tile i + 1: at the bench's shapes the one-tile CTA spends most
+// of its life filling its ring and draining TMEM with the tensor pipe idle.
+//   warp 0 / lane 0   TMA producer over the CTA's (tile, chunk) sequence;
+//   warp 1            allocates 2 x tmem_cols TMEM columns; lane 0 issues the MMAs of the
+//                     CTA's i-th tile into accumulator i & 1 once the epilogue has drained
+//                     it, commits each ring stage back to the producer and the finished
+//                     accumulator to the epilogue;
+//   warps 2..5        epilogue; warp w may access TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.
+// Selected per shape by the autotuner, and only with IGA_TC_PERSISTENT=1 until it has
+// been checked against the one-tile kernel on a GB300.  Its barrier protocol (ring
+// phases, accumulator hand-over) is simulated on the host in
+// tests/test_tc_persistent_protocol.py.
+constexpr int kTcpThreads = 192;
+constexpr int kTcpMaxStages = 8;
+constexpr size_t kTcpRingBytes = 200 * 1024;  // ring budget per CTA (stages x stage bytes)
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Epilogue of one 128 x n_tile tile for the 32 rows (TMEM lanes) of one warp: tcgen05.ld of
+// 16 columns at a time, optional FD diagonal, conversion, stores in the rotated layout.
+__device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c0, int N,
+                                              int n_tile, const TcEpi &epi) {
+  long long obase = 0;
+  const float *dinv_row = nullptr;
+  if (row < M) {
+    const int a = row % epi.n, rest = row / epi.n;
+    const int m = rest % epi.nmid, rr = rest / epi.nmid;
+    obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
+    if (epi.dinv) dinv_row = epi.dinv + a + (long long)epi.n * m;
+  }
+  const long long cstride = (long long)epi.ld_out * epi.nmid;
+  const long long dstride = (long long)epi.n * epi.nmid;
+  const long long off = epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0;
+  for (int cc = 0; cc < n_tile; cc += 16) {
+    uint32_t v[16];
+    tmem_ld16(tl + (uint32_t)cc, v);
+    if (row < M) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c0 + cc + j;
+        if (col < N) {
+          float x = __uint_as_float(v[j]);
+          if (dinv_row) x *= __ldg(dinv_row + dstride * col);
+          const long long o = off + obase + cstride * col;
+          if (epi.kind == kOutF32) {
+            ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
+          } else if (epi.kind == kOutBF16) {
+            ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
+          } else {
+            ((double *)epi.out)[o] = (double)x;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcpThreads, 1)
+    tc_gemm_persistent_kernel(const __grid_constant__ CUtensorMap mapA,
+                              const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
+                              int n_tile, int tmem_cols, uint32_t idesc, int nstage, TcEpi epi) {
+  pdl_entry();  // before any global access, TMEM allocation included
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[kTcpMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kTcpMaxStages];
+  __shared__ __align__(8) uint64_t accf_bar[2];  // accumulator b holds a finished tile
+  __shared__ __align__(8) uint64_t acce_bar[2];  // accumulator b drained by the epilogue
+  __shared__ __align__(8) uint64_t fin_bar;      // every MMA of this CTA has completed
+  __shared__ uint32_t tmem_base;
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_bytes = kTileM * 128, b_bytes = (uint32_t)n_tile * 128;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kbox = KIND == 0 ? 32 : 64;  // elements per 128-byte row
+  constexpr int kmma = KIND == 0 ? 8 : 16;   // K per instruction (32 bytes)
+  const int nchunks = (K + kbox - 1) / kbox;
+  const int nmt = (M + kTileM - 1) / kTileM, nnt = (N + n_tile - 1) / n_tile;
+  const long long ntiles = (long long)nmt * nnt;
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + nstage * a_bytes;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < nstage; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(&fin_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 2u * (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;  // chunks issued so far (ring slot g % nstage, use g / nstage)
+      bool ok = true;
+      for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const int m0 = (int)(tile % nmt) * kTileM, c0 = (int)(tile / nmt) * n_tile;
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int s = (int)(g % nstage);
+          const long long use = g / nstage;
+          if (use > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+            atomicExch(epi.err, 4);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full_bar[s], a_bytes + b_bytes);
+          tma_load_2d(sA + s * a_bytes, &mapA, &full_bar[s], c * kbox, m0);
+          tma_load_2d(sB + s * b_bytes, &mapB, &full_bar[s], c * kbox, c0);
+        }
+      }
+      // no copy may be in flight when the CTA exits: wait (bounded) until the last nstage
+      // chunks issued have landed (on the normal path the MMAs have consumed them all)
+      for (long long h = g > nstage ? g - nstage : 0; h < g; ++h)
+        mbar_wait(&full_bar[h % nstage], (uint32_t)((h / nstage) & 1));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long g = 0;
+      int i = 0;  // tiles of this CTA so far
+      bool ok = true;
+      for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++i) {
+        const int b = i & 1, ub = i >> 1;
+        if (ub > 0 && !mbar_wait(&acce_bar[b], (uint32_t)((ub - 1) & 1))) {
+          atomicExch(epi.err, 5);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(b * tmem_cols);
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int s = (int)(g % nstage);
+          const long long use = g / nstage;
+          if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
+            atomicExch(epi.err, 6);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int rem = K - c * kbox;
+          const int ksteps = min(kbox / kmma, (rem + kmma - 1) / kmma);
+          const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
+          for (int j = 0; j < ksteps; ++j)
+            mma_issue<KIND>(dt, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc,
+                            (c > 0 || j > 0) ? 1u : 0u);
+          mma_commit(&empty_bar[s]);
+        }
+        if (ok) mma_commit(&accf_bar[b]);
+      }
+      // tensor memory is freed only after every MMA issued here has completed
+      mma_commit(&fin_bar);
+      if (!mbar_wait(&fin_bar, 0)) atomicExch(epi.err, 8);
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    int i = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+      const int b = i & 1, ub = i >> 1;
+      // warp-uniform so that the .sync.aligned tensor-memory loads stay convergent
+      const bool have =
+          __all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (uint32_t)(ub & 1)) ? 1 : 0) != 0;
+      if (!have) {
+        if (lane == 0) atomicExch(epi.err, 7);
+        break;
+      }
+      tc_fence_after();
+      const int m0 = (int)(tile % nmt) * kTileM, c0 = (int)(tile / nmt) * n_tile;
+      tc_store_rows(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * tmem_cols),
+                    m0 + q * 32 + lane, M, c0, N, n_tile, epi);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce_bar[b]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 2u * (uint32_t)tmem_cols);
+}
+
 // FP64 vector (unpadded) -> TF32-rounded FP32 / BF16 tensor with padded fastest index.
 template <class T>
 __global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, unsigned N,
@@ -312,6 +504,9 @@ struct TcFd {
   int R_max = 1;
   int esize = 4, n_tile = 0, n_ntiles = 0, tmem_cols = 0;
   size_t smem = 0;
+  // persistent kernel (tc_gemm_persistent_kernel): ring depth, shared memory, CTAs per SM
+  int persistent = 0, p_nstage = 0, p_cps = 0;
+  size_t p_smem = 0;
   uint32_t idesc = 0;
   DevBuf<uint8_t> P0, Ta, Tb;
   DevBuf<int> err;
@@ -325,11 +520,22 @@ static void make_map(CUtensorMap &m, const void *base, int elem_bf16, long long 
 static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi, int R,
                  cudaStream_t s);
 
+static int num_sms_tc() {
+  int dev = 0, nsm = 0;
+  IGA_CUDA_TRY(cudaGetDevice(&dev));
+  IGA_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  return nsm;
+}
+
 // Column-tile shape of the mode products: N = n_tile output columns per CTA (a
 // multiple of 16, <= 256), the factor's TMA box and the instruction descriptor follow.
-static void set_tile(TcFd &t, int n_tile) {
+// persistent: the tile loop of tc_gemm_persistent_kernel, with the deepest ring that fits
+// kTcpRingBytes and as many CTAs per SM as shared memory and tensor memory (two
+// accumulators of tmem_cols columns each, 512 columns per SM) allow.
+static void set_tile(TcFd &t, int n_tile, int persistent = 0) {
   const bool bf = t.prec == IGA_PREC_BF16;
   t.n_tile = n_tile;
+  t.persistent = persistent;
   t.n_ntiles = (t.n + n_tile - 1) / n_tile;
   t.tmem_cols = 32;
   while (t.tmem_cols < n_tile) t.tmem_cols *= 2;
@@ -341,6 +547,24 @@ static void set_tile(TcFd &t, int n_tile) {
             ((uint32_t)(kTileM >> 4) << 24);
   make_map(t.mapVt, t.vt_dev, bf, t.n, t.n, t.kpad, n_tile);
   make_map(t.mapU, t.u_dev, bf, t.n, t.n, t.kpad, n_tile);
+  if (persistent) {
+    const size_t stage = (size_t)kTileM * 128 + (size_t)n_tile * 128;
+    t.p_nstage = (int)std::max<size_t>(2, std::min<size_t>(kTcpMaxStages, kTcpRingBytes / stage));
+    t.p_smem = 1024 + (size_t)t.p_nstage * stage;
+    int cps = 0;
+    if (bf)
+      IGA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &cps, tc_gemm_persistent_kernel<1>, kTcpThreads, t.p_smem));
+    else
+      IGA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &cps, tc_gemm_persistent_kernel<0>, kTcpThreads, t.p_smem));
+    t.p_cps = std::max(1, std::min(cps, 512 / (2 * t.tmem_cols)));
+  }
+}
+
+static bool persistent_enabled() {
+  const char *e = std::getenv("IGA_TC_PERSISTENT");
+  return e && e[0] == '1';
 }
 
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
@@ -350,7 +574,7 @@ static void set_tile(TcFd &t, int n_tile) {
 // problem of one shape runs the same kernels.
 static void autotune(TcFd &t, cudaStream_t s) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int, int>, int> cache;
+  static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
   const auto key = std::make_tuple(dev, t.d, t.n, t.prec, t.R_max);
@@ -358,28 +582,33 @@ static void autotune(TcFd &t, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      set_tile(t, it->second);
+      set_tile(t, it->second.first, it->second.second);
       return;
     }
   }
-  std::vector<int> cand;
+  std::vector<int> widths;
   if (t.n <= 256) {
     for (int parts = 1; parts <= 6; ++parts) {
       const int nt = ((t.n + parts - 1) / parts + 15) / 16 * 16;
-      if (std::find(cand.begin(), cand.end(), nt) == cand.end()) cand.push_back(nt);
+      if (std::find(widths.begin(), widths.end(), nt) == widths.end()) widths.push_back(nt);
     }
   } else {
-    cand = {256, 128, 64};
+    widths = {256, 128, 64};
   }
-  int best = cand[0];
+  // (column tile, persistent kernel)
+  std::vector<std::pair<int, int>> cand;
+  for (int nt : widths) cand.push_back({nt, 0});
+  if (persistent_enabled())
+    for (int nt : widths) cand.push_back({nt, 1});
+  std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
     std::lock_guard<std::mutex> dlk(device_mutex());
     cudaEvent_t e0, e1;
     IGA_CUDA_TRY(cudaEventCreate(&e0));
     IGA_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    for (int nt : cand) {
-      set_tile(t, nt);
+    for (const auto &cd : cand) {
+      set_tile(t, cd.first, cd.second);
       TcEpi e{};
       e.kind = t.prec == IGA_PREC_BF16 ? kOutBF16 : kOutF32;
       e.n = t.n;
@@ -401,18 +630,20 @@ static void autotune(TcFd &t, cudaStream_t s) {
       IGA_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best_ms) {
         best_ms = ms;
-        best = nt;
+        best = cd;
       }
       const char *verbose = std::getenv("IGA_VERBOSE");
       if (verbose && verbose[0] == '1')
-        std::fprintf(stderr, "iga autotune d=%d n=%d prec=%d R=%d n_tile=%d: %.1f us/apply\n",
-                     t.d, t.n, t.prec, t.R_max, nt, 1000.f * ms / 3);
+        std::fprintf(stderr,
+                     "iga autotune d=%d n=%d prec=%d R=%d n_tile=%d%s: %.1f us/apply\n", t.d,
+                     t.n, t.prec, t.R_max, cd.first, cd.second ? " persistent" : "",
+                     1000.f * ms / 3);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     IGA_CUDA_TRY(cudaMemsetAsync(t.err.ptr, 0, sizeof(int), s));
   }
-  set_tile(t, best);
+  set_tile(t, best.first, best.second);
   std::lock_guard<std::mutex> lk(mu);
   cache[key] = best;
 }
@@ -496,6 +727,15 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        if (persistent_enabled()) {
+          const int max_smem_p = (int)(1024 + kTcpRingBytes);
+          IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_persistent_kernel<0>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            max_smem_p));
+          IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_persistent_kernel<1>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            max_smem_p));
+        }
         smem_set[dev] = true;
       }
     }
@@ -513,6 +753,18 @@ void destroy_tc_fd(TcFd *fd) { delete fd; }
 static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi, int R,
                  cudaStream_t s) {
   const int M = R * t.M;
+  if (t.persistent) {
+    const long long ntiles = (long long)((M + kTileM - 1) / kTileM) * t.n_ntiles;
+    const dim3 pgrid((unsigned)std::min<long long>(ntiles, (long long)num_sms_tc() * t.p_cps));
+    if (t.prec == IGA_PREC_BF16)
+      launch_pdl(kPdlTensorCore, tc_gemm_persistent_kernel<1>, pgrid, dim3(kTcpThreads),
+                 t.p_smem, s, A, B, M, t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, t.p_nstage, epi);
+    else
+      launch_pdl(kPdlTensorCore, tc_gemm_persistent_kernel<0>, pgrid, dim3(kTcpThreads),
+                 t.p_smem, s, A, B, M, t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, t.p_nstage, epi);
+    IGA_LAUNCH_CHECK();
+    return;
+  }
   dim3 grid((M + kTileM - 1) / kTileM, t.n_ntiles);
   if (t.prec == IGA_PREC_BF16)
     launch_pdl(kPdlTensorCore, tc_gemm_kernel<1>, grid, dim3(kTcThreads), t.smem, s, A, B, M,
@@ -610,6 +862,10 @@ void preload_kernels_fd_tc() {
   cudaFuncAttributes a;
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<0>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<1>));
+  if (persistent_enabled()) {
+    IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<0>));
+    IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<1>));
+  }
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<float>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<__nv_bfloat16>));
 }
