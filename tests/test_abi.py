@@ -105,3 +105,15 @@ def test_batch_and_noalloc_argument_checks(lib):
     # d outside 2..3, then a null factor pointer
     assert lib.iga_precond_apply_noalloc(4, 10, None, None, None, None, None, None) == 1
     assert lib.iga_precond_apply_noalloc(3, 10, None, None, None, None, None, None) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback of any kind: without libiga_fd.so the binding raises and names the build."""
+    from paper_1705_04384_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libiga_fd.so"))
+    with pytest.raises(ImportError, match="build"):
+        _lib.load()
+    from paper_1705_04384_gb300.api import Problem
+    with pytest.raises(ImportError, match="missing"):
+        Problem(2, 8, 3)
