@@ -294,8 +294,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // row tile fastest (the order in which the one-tile grid above is launched).  Per CTA the
 // setup (barriers, TMEM allocation, tensor-map fetch) is paid once, the TMA ring runs
 // ahead across tile boundaries, and two TMEM accumulators let the epilogue of tile i
-// overlap the main loop of tile i + 1: at the bench's shapes the one-tile CTA spends most
-// of its life filling its ring and draining TMEM with the tensor pipe idle.
+// overlap the main loop of tile i + 1.  The one-tile kernel runs its phases in series:
+// measured at 2D n = 1025 with 8 right-hand sides, its tensor pipe is busy 27 % of the
+// cycles its CTAs are resident, with L2 at 18 % and DRAM at 6 % of their peaks.
 //   warp 0 / lane 0   TMA producer over the CTA's (tile, chunk) sequence;
 //   warp 1            allocates 2 x tmem_cols TMEM columns; lane 0 issues the MMAs of the
 //                     CTA's i-th tile into accumulator i & 1 once the epilogue has drained
