@@ -1,10 +1,15 @@
 """Benchmark: GMRES + FD time-to-1e-8 and DOF-iterations per second on one GB300.
 
 Workload (default): the 3D extruded thick quarter annulus r in [1,2], z in [0,1],
-64 elements per direction, p = 3, 4, 5 (N = 274,625 / 287,496 / 300,763), forcing
-from the manufactured solution plus the seeded 1e-3 perturbation, GMRES tol 1e-8,
-FP64 throughout.  One step = one solve for each p (cached setup).  The mixed
-(TF32-FD flexible GMRES) form of the same solves is reported beside it.
+128 elements per direction, p = 4, 5, 6 (N = 2,197,000 / 2,248,091 / 2,299,968), forcing
+from the manufactured solution plus the seeded 1e-3 perturbation, GMRES tol 1e-8.  One
+step = one solve for each p (setup cached).  Three forms of the same solves:
+  fp64  plain GMRES with the FP64 FD (the line's value),
+  tf32  flexible GMRES with the FD mode products on the tensor cores in TF32 ("mixed"),
+  bf16  the same with BF16 operands ("bf16"),
+each with per-solve p50/p99, time to solution with and without setup, the error against
+the FP64 oracle's solution (p = 4) and the roofline of its dominant kernel.  The FP64
+ceiling is measured in the same run (iga_fp64_probe).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -31,23 +36,31 @@ import workload as W  # noqa: E402
 
 METRIC = "GMRES+FD time-to-1e-8 residual, DOF-iter/s (mixed vs FP64, 1 GB300); p50/p99"
 UNIT = "DOF-iter/s"
-WORKLOAD = "3d_annulus_ne64"
+WORKLOAD = "3d_annulus_ne128"
 TOL = 1e-8
 MAX_ITER = 200
-FP64_PEAK_GFLOPS = 1250.0  # nominal GB300 FP64: 2 FMA/clk/SM x 152 SMs x 2.07 GHz x 2 FLOP
-CONFIG = {"workload": f"{WORKLOAD}: 3D extruded quarter annulus r in [1,2], z in [0,1], 64 "
-                      f"elements/dir, p=3,4,5 (N=274625/287496/300763), manufactured f + seeded "
-                      f"1e-3 perturbation, FP64 FD-GMRES to 1e-8",
-          "step": "one solve per p (setup cached)",
-          "l2": "flushed between steps (512 MB write)", "parallelism": "replicas"}
-REVOLVED_TEXT = ("3d_revolved_ne64: 3D quarter ring r in [1,2] revolved by pi/2 about the axis "
-                 "(0,1,0) through (-1,-1,-1), 64 elements/dir, p=3,4,5, f = 1 + seeded 1e-3 "
-                 "perturbation, FP64 FD-GMRES to 1e-8")
-
-
-WIND_TEXT = ("3d_wind_ne64: convection-diffusion -Lap + w.grad (Sec. 3.2) with w = (5,5,5) on "
-             "the 3D extruded quarter annulus, 64 elements/dir, p=3,4,5, f = 1 + seeded 1e-3 "
-             "perturbation, FD of the wind-shifted pencils, FP64 FD-GMRES to 1e-8")
+ORACLE_P = 4  # degree of the problem the oracle solves in full (error reference, CPU baseline)
+HBM_PEAK_FALLBACK = 6800.0  # GB/s, used only when MEASURED_PEAKS.json is absent
+TEXTS = {
+    "3d_annulus_ne128": "3d_annulus_ne128: 3D extruded quarter annulus r in [1,2], z in [0,1], 128 "
+                        "elements/dir, p=4,5,6 (N=2197000/2248091/2299968), manufactured f + seeded "
+                        "1e-3 perturbation, FD-GMRES to 1e-8 in FP64 (value), TF32 and BF16 "
+                        "(flexible GMRES, FD on the tensor cores)",
+    "3d_annulus_ne64": "3d_annulus_ne64: 3D extruded quarter annulus r in [1,2], z in [0,1], 64 "
+                       "elements/dir, p=3,4,5 (N=274625/287496/300763), manufactured f + seeded "
+                       "1e-3 perturbation, FD-GMRES to 1e-8",
+    "3d_revolved_ne64": "3d_revolved_ne64: 3D quarter ring r in [1,2] revolved by pi/2 about the "
+                        "axis (0,1,0) through (-1,-1,-1), 64 elements/dir, p=3,4,5, f = 1 + seeded "
+                        "1e-3 perturbation, FD-GMRES to 1e-8",
+    "3d_wind_ne64": "3d_wind_ne64: convection-diffusion -Lap + w.grad (Sec. 3.2) with w = (5,5,5) "
+                    "on the 3D extruded quarter annulus, 64 elements/dir, p=3,4,5, f = 1 + seeded "
+                    "1e-3 perturbation, FD of the wind-shifted pencils, FP64 FD-GMRES to 1e-8",
+}
+CONFIG = {"workload": TEXTS[WORKLOAD],
+          "step": "one solve per p (setup cached); per form",
+          "l2": "flushed between steps (512 MB write); inputs (17.6-18.4 MB per vector, Krylov "
+                "bases of 0.4-0.9 GB) exceed L2 anyway",
+          "parallelism": "replicas"}
 
 
 def geometry_of(c):
@@ -61,12 +74,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="FP64 form only")
     ap.add_argument("--no-bicgstab", action="store_true")
-    ap.add_argument("--workload", default="3d_ne64",
-                    choices=["3d_ne64", "3d_revolved_ne64", "3d_wind_ne64", "batched", "served"],
-                    help="3d_ne64 (default bench line), 3d_revolved_ne64 (Sec. 5's revolved "
-                         "ring, same measurement), 3d_wind_ne64 (Sec. 3.2 convection-diffusion), "
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 3d_annulus_ne64 (config 2) secondary line")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-form key of the default line")
+    ap.add_argument("--workload", default="3d_ne128",
+                    choices=["3d_ne128", "3d_ne64", "3d_revolved_ne64", "3d_wind_ne64", "batched",
+                             "served"],
+                    help="3d_ne128 (default bench line), 3d_ne64 (config 2), 3d_revolved_ne64 "
+                         "(Sec. 5's revolved ring), 3d_wind_ne64 (Sec. 3.2 convection-diffusion), "
                          "batched (256 2D problems x 8 rhs), served (Poisson request stream)")
     ap.add_argument("--precision", default="tf32", help="preconditioner precision for the "
                                                         "batched / served forms")
@@ -135,11 +153,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------- helpers
-def kernel_source_hash():
-    """Hash of the dominant kernel's source file with comments and blank space removed, so
-    that an edit of its comments does not void the committed counters."""
+def kernel_source_hash(files=("kernels_fd64.cu",)):
+    """Hash of a kernel's source file(s) with comments and blank space removed, so that an
+    edit of comments does not void the committed counters."""
     h = hashlib.sha256()
-    for f in ("kernels_fd64.cu",):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1705_04384_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].strip()
@@ -148,9 +166,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(summary="fd_fold_mma_3d_ne64.md"):
-    """dram bytes per launch of the dominant kernel from the committed ncu summary,
-    or None when the kernel source changed since the capture."""
+def committed_traffic(summary="fd_fold_mma_3d_ne128.md", files=("kernels_fd64.cu",)):
+    """dram bytes per launch of a kernel from its committed ncu summary, or None when the
+    kernel source changed since the capture (or there is no summary)."""
     path = os.path.join(ROOT, "profiles", summary)
     vals = {}
     try:
@@ -162,9 +180,17 @@ def committed_traffic(summary="fd_fold_mma_3d_ne64.md"):
                     vals[k] = v.strip()
     except OSError:
         return None
-    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash(files):
         return None
     return float(vals["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in vals else None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 def aggregate(units, seconds, device=None):
@@ -189,26 +215,68 @@ def percentile(vals, q):
     return float(np.percentile(np.asarray(vals, dtype=np.float64), q)) if vals else None
 
 
-# ------------------------------------------------------------------------- reference arm
+def fold_flops_per_launch(n, d=3):
+    """Algorithmic FLOPs of one folded FP64 FD mode product, averaged over the d forward
+    (even block ne x ne, odd block no x no) and d inverse (ne pairs x n) launches."""
+    ne, no = (n + 1) // 2, n // 2
+    rows = n ** (d - 1)
+    return 0.5 * (2.0 * rows * (ne * ne + no * no) + 2.0 * rows * ne * n)
+
+
+def operator_flops_per_dof(W_band, d=3):
+    """Algorithmic FLOPs per DOF of the operator on the extruded annulus (fields 11, 22, 33
+    and the first-order term 1): 2 band passes along direction 3, 3 along direction 2 and 4
+    band passes contracted along direction 1, each 2W FLOPs, plus 2 per contracted term."""
+    assert d == 3
+    return 2.0 * W_band * (2 + 3 + 4) + 2.0 * 4
+
+
+# ------------------------------------------------------------------------- oracle (CPU)
+def oracle_problem(name, p):
+    """The oracle's view of one problem of a named 3D workload: spaces, matrix-free A_C
+    (the definition of eq. collocation applied through the Kronecker identity: the CSR
+    matrix of config 3 has about 8e8 non-zeros), the FD preconditioner and the rhs."""
+    from oracle import collocation as C, fd as F, geometry as Geo
+    c = W.CONFIGS[name]
+    spaces = [C.Space1D(c["n_elem"], p) for _ in range(c["d"])]
+    fmap = Geo.make_map(geometry_of(c), c["d"], c["r0"], c["r1"])
+    A = C.CollocationOperator(spaces, fmap, c.get("wind"))
+    pts = C.physical_points_grid(fmap, [s.tau for s in spaces])
+    b = W.config_rhs(name, pts, c["ps"].index(p))
+    fd = F.FD(spaces, c.get("wind"))
+    return A, fd, b
+
+
+def oracle_solve(name=None, p=ORACLE_P):
+    """One full oracle GMRES+FD solve to 1e-8 (iteration phase timed) on the host cores."""
+    from oracle import gmres as G
+    name = name or WORKLOAD
+    t0 = time.perf_counter()
+    A, fd, b = oracle_problem(name, p)
+    setup = time.perf_counter() - t0
+    t0, c0 = time.perf_counter(), time.process_time()
+    r = G.gmres(A, b, M=fd, tol=TOL, max_iter=MAX_ITER)
+    dt, dc = time.perf_counter() - t0, time.process_time() - c0
+    return dict(x=r["x"], iters=r["iters"], relres_true=r["relres_true"], seconds=dt,
+                cpu_seconds=dc, setup_s=setup, N=b.shape[0], hist_last=float(r["hist"][-1]))
+
+
 def run_reference(args):
-    """Time the FP64 CPU oracle on a bounded sample of the same workload."""
+    """The oracle timed on the host cores, one bounded sample of the workload per step:
+    REF_ITERS GMRES+FD iterations of the p = ORACLE_P problem (Arnoldi by modified
+    Gram-Schmidt, the FD solve of eq. FD3D, the matrix-free A_C)."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    from oracle import collocation as C, fd as F, geometry as Geo, gmres as G
-    c = W.CONFIGS[WORKLOAD]
-    p = c["ps"][0]
-    spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
-    fmap = Geo.make_map(geometry_of(c), 3, c["r0"], c["r1"])
-    A = C.assemble_collocation(spaces, fmap, c.get("wind"))
-    pts = C.physical_points(fmap, [s.tau for s in spaces])
-    b = W.config_rhs(WORKLOAD, pts, 0)
-    fd = F.FD(spaces, c.get("wind"))
-    N = A.shape[0]
+    from oracle import gmres as G
+    A, fd, b = oracle_problem(WORKLOAD, ORACLE_P)
+    N = b.shape[0]
+    ref_iters = 3
     times, cpu_s, dofit = [], 0.0, 0
+    r = None
     for it in range(args.warmup + args.steps):
         t0, c0 = time.perf_counter(), time.process_time()
-        r = G.gmres(A, b, M=fd, tol=TOL, max_iter=MAX_ITER)
+        r = G.gmres(A, b, M=fd, tol=0.0, max_iter=ref_iters)
         dt, dc = time.perf_counter() - t0, time.process_time() - c0
         if it >= args.warmup:
             times.append(dt)
@@ -217,9 +285,10 @@ def run_reference(args):
     tot = sum(times)
     value = dofit / tot
     cores = os.cpu_count()
-    sample = (f"oracle GMRES+FD, one full solve to 1e-8 of the p={p} problem (N={N}, "
-              f"{r['iters']} iterations) per step; iteration phase only (CSR assembly and "
-              f"eigendecomposition are setup, outside the timer)")
+    sample = (f"oracle GMRES+FD, {ref_iters} Arnoldi iterations per step of the p={ORACLE_P} "
+              f"problem of {WORKLOAD} (N={N}), x0 = 0, matrix-free A_C (eq. collocation via the "
+              f"Kronecker identity), FD of eq. FD3D, modified Gram-Schmidt; iteration phase only "
+              f"(fields and eigendecomposition are setup)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -233,36 +302,6 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline_sample(budget_s=15.0):
-    """The oracle as it stands on the host cores, bounded: full GMRES+FD solves to
-    1e-8 of the p = 3 problem of the workload (iteration phase; CSR assembly and the
-    eigendecomposition are setup), repeated until about ``budget_s`` seconds."""
-    from oracle import collocation as C, fd as F, geometry as Geo, gmres as G
-    c = W.CONFIGS[WORKLOAD]
-    p = c["ps"][0]
-    spaces = [C.Space1D(c["n_elem"], p) for _ in range(3)]
-    fmap = Geo.make_map(geometry_of(c), 3, c["r0"], c["r1"])
-    A = C.assemble_collocation(spaces, fmap, c.get("wind"))
-    pts = C.physical_points(fmap, [s.tau for s in spaces])
-    b = W.config_rhs(WORKLOAD, pts, 0)
-    fd = F.FD(spaces, c.get("wind"))
-    N = A.shape[0]
-    dofit, spent, cpu_s, solves, its = 0, 0.0, 0.0, 0, 0
-    while spent < budget_s and solves < 50:
-        t0, c0 = time.perf_counter(), time.process_time()
-        r = G.gmres(A, b, M=fd, tol=TOL, max_iter=MAX_ITER)
-        spent += time.perf_counter() - t0
-        cpu_s += time.process_time() - c0
-        dofit += N * r["iters"]
-        its = r["iters"]
-        solves += 1
-    return {"value": dofit / spent, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{solves} full solves to 1e-8 ({its} iterations each) of {WORKLOAD} p={p}, "
-                      f"N={N}, iteration phase only; {spent:.1f} s; numpy/OpenBLAS threads = cores, "
-                      f"scipy CSR matvec single-threaded",
-            "busy_cores": cpu_s / spent}
-
-
 # ------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -272,61 +311,108 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    from paper_1705_04384_gb300.api import Problem
+    from paper_1705_04384_gb300.api import Problem, measure_fp64_peak
 
     c = W.CONFIGS[WORKLOAD]
+    d = c["d"]
     stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)
+    hbm_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
+
+    # the FP64 ceiling of this GPU, measured now (iga_fp64_probe, best of 5 launches each)
+    fp64 = measure_fp64_peak(reps=1000, trials=5, stream=stream)
+    fp64_peak = fp64["peak"]
 
     def make(prec):
+        """Set up one problem per degree; setup time = iga_setup + iga_prepare (workspace and
+        solve-graph capture), time to solution with setup = that + the first solve."""
         probs = []
         for i, p in enumerate(c["ps"]):
-            P = Problem(3, c["n_elem"], p, geometry_of(c), c["r0"], c["r1"], precision=prec,
-                        wind=c.get("wind"),
-                        device=dev, stream=stream)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            P = Problem(d, c["n_elem"], p, geometry_of(c), c["r0"], c["r1"], precision=prec,
+                        wind=c.get("wind"), device=dev, stream=stream)
+            P.prepare(1, MAX_ITER)
+            torch.cuda.synchronize(dev)
+            t_setup = time.perf_counter() - t0
             pts = P.collocation_points()
             rhs = torch.from_numpy(W.config_rhs(WORKLOAD, pts, i)).to(dev)
-            probs.append((p, P, rhs, torch.empty_like(rhs)))
+            x = torch.empty_like(rhs)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            _, info = P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+            t_first = time.perf_counter() - t0
+            probs.append(dict(p=p, P=P, rhs=rhs, x=x, setup_s=t_setup, first_s=t_first))
         return probs
 
-    t_setup = time.perf_counter()
-    fp64 = make("fp64")
-    t_setup = time.perf_counter() - t_setup
-    mixed = None
-    if not args.no_mixed:
-        try:
-            mixed = make("tf32")
-        except Exception as e:  # the mixed form is reported when it is built
-            mixed = None
-            mixed_err = str(e)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def run_step(probs, record, solver="gmres"):
+    def run_step(probs, solver="gmres"):
         per = []
-        for p, P, rhs, x in probs:
+        for q in probs:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             if solver == "gmres":
-                _, info = P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+                _, info = q["P"].solve(q["rhs"], tol=TOL, max_iter=MAX_ITER, out=q["x"])
             else:
-                _, info = P.solve_bicgstab(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+                _, info = q["P"].solve_bicgstab(q["rhs"], tol=TOL, max_iter=MAX_ITER, out=q["x"])
             e1.record(stream)
-            per.append((p, P, info, e0, e1))
+            per.append((q, info, e0, e1))
         torch.cuda.synchronize(dev)
-        out = []
-        for p, P, info, e0, e1 in per:
-            out.append((p, P.N, info["iters"], e0.elapsed_time(e1) * 1e-3, info["relres_true"]))
-        return out
+        return [(q["p"], q["P"].N, info["iters"], e0.elapsed_time(e1) * 1e-3, info["relres_true"])
+                for q, info, e0, e1 in per]
 
     def timed(probs, steps, warmup, solver="gmres"):
         for _ in range(warmup):
-            run_step(probs, False, solver)
+            run_step(probs, solver)
         results = []
         for _ in range(steps):
             flush.fill_(1.0)  # L2 flush between steps, outside the timed solves
             torch.cuda.synchronize(dev)
-            results.append(run_step(probs, True, solver))
+            results.append(run_step(probs, solver))
         return results
+
+    def summarise(probs, res):
+        t = sum(sum(s[3] for s in step) for step in res)
+        u = sum(sum(s[1] * s[2] for s in step) for step in res)
+        units, tt = aggregate(u, t, dev)
+        solve_ms = [s[3] * 1e3 for st in res for s in st]
+        by_p = {}
+        for q in probs:
+            ms = [s[3] * 1e3 for st in res for s in st if s[0] == q["p"]]
+            by_p[str(q["p"])] = {"p50_ms": percentile(ms, 50), "p99_ms": percentile(ms, 99),
+                                 "setup_ms": 1e3 * q["setup_s"],
+                                 "tts_with_setup_ms": 1e3 * (q["setup_s"] + q["first_s"])}
+        return {"value": units / tt, "unit": UNIT,
+                "iters": {str(s[0]): s[2] for s in res[-1]},
+                "relres_true": {str(s[0]): s[4] for s in res[-1]},
+                "p50_ms": percentile(solve_ms, 50), "p99_ms": percentile(solve_ms, 99),
+                "tts_warm_ms_per_step": 1e3 * tt / len(res), "by_p": by_p,
+                "_units": units, "_t": tt}
+
+    def launches_of(probs, res):
+        tot = 0
+        for step in res:
+            for q, s in zip(probs, step):
+                f, it = q["P"].launch_counts()
+                tot += f + it * s[2]
+        return tot
+
+    def time_calls(fn, reps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) * 1e-3 / reps
+
+    forms = ["fp64"] if args.no_mixed else ["fp64", "tf32", "bf16"]
+    probs = {f: make(f) for f in forms}
 
     if world > 1:
         import torch.distributed as dist
@@ -334,64 +420,67 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local_rank)
     clocks.start()
-    res64 = timed(fp64, args.steps, args.warmup)
+    res = {f: timed(probs[f], args.steps, args.warmup) for f in forms}
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
-    step_times = [sum(s[3] for s in step) for step in res64]
-    dof_iters = [sum(s[1] * s[2] for s in step) for step in res64]
-    all_units, total_t = aggregate(sum(dof_iters), sum(step_times), dev)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    value = all_units / total_t
-    solve_ms = [s[3] * 1e3 for step in res64 for s in step]
-    iters = {str(s[0]): s[2] for s in res64[-1]}
-    relres = {str(s[0]): s[4] for s in res64[-1]}
-    launches = 0
-    for step in res64:
-        for (p, P, rhs, x), s in zip(fp64, step):
-            f, it = P.launch_counts()
-            launches += f + it * s[2]
+    out = {f: summarise(probs[f], res[f]) for f in forms}
+    for f in forms:
+        out[f]["gpu_launches"] = launches_of(probs[f], res[f])
+    main = out["fp64"]
 
-    # dominant kernel: the FP64 FD mode-product GEMM (6 launches per FD apply)
-    p0, P0, rhs0, x0 = fp64[0]
-    reps = 20
-    flush.fill_(1.0)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    buf = torch.empty_like(rhs0)
-    e0.record(stream)
-    for _ in range(reps):
-        P0.precond_apply(rhs0, out=buf)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_launch = e0.elapsed_time(e1) * 1e-3 / (reps * 6)
-    n = P0.n
-    ne, no = (n + 1) // 2, n // 2
-    rows = n ** 2  # 3D: one row per (i2, i3) fiber
-    # algorithmic FLOPs of one folded mode product, averaged over the d forward
-    # (even block ne x ne, odd block no x no) and d inverse (ne pairs x n) launches
-    flops = 0.5 * (2.0 * rows * (ne * ne + no * no) + 2.0 * rows * ne * n)
-    achieved = flops / t_launch / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
-                "traffic": committed_traffic(),
-                "kernel": "fd_fold_mma_kernel (folded FD mode product, FP64 mma.sync m8n8k4)",
-                "per_launch_us": t_launch * 1e6, "flops_per_launch": flops,
-                "dense_equivalent_flops_per_launch": 2.0 * n ** 4,
-                "peak_note": "nominal GB300 FP64 1.25 TFLOP/s (2 FMA/clk/SM x 152 SMs x 2.07 GHz); "
-                             "of nominal. An FP64 mma.sync throughput probe on this GPU reached "
-                             "1050 GFLOP/s"}
+    # dominant kernels, timed live on the bench stream (the p = ORACLE_P problem, n = 130)
+    q4 = {f: next(q for q in probs[f] if q["p"] == ORACLE_P) for f in forms}
+    P4 = q4["fp64"]["P"]
+    n4, N4 = P4.n, P4.N
+    buf = torch.empty_like(q4["fp64"]["rhs"])
+    # FP64 form: the folded FD mode product (6 launches per FD apply)
+    t_launch = time_calls(lambda: P4.precond_apply(q4["fp64"]["rhs"], out=buf), 10) / (2 * d)
+    fl = fold_flops_per_launch(n4, d)
+    main["roofline"] = {
+        "bound": "alu", "achieved": fl / t_launch / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+        "frac": fl / t_launch / 1e9 / fp64_peak,
+        "traffic": committed_traffic("fd_fold_mma_3d_ne128.md", ("kernels_fd64.cu",)),
+        "kernel": "fd_fold_mma_kernel (folded FD mode product, FP64 mma.sync m8n8k4)",
+        "per_launch_us": t_launch * 1e6, "flops_per_launch": fl,
+        "dense_equivalent_flops_per_launch": 2.0 * n4 ** (d + 1),
+        "peak_note": f"of measured: FP64 ceiling of this GPU measured in this run by "
+                     f"iga_fp64_probe (mma.sync .f64 {fp64['dmma']:.0f}, FP64 FMA "
+                     f"{fp64['fma']:.0f} GFLOP/s; the larger is the peak)"}
+    # operator (FP64 unit), the same in every form
+    t_op = time_calls(lambda: P4.apply_operator(q4["fp64"]["rhs"], out=buf), 10)
+    opf = operator_flops_per_dof(P4.p + 1, d) * N4
+    main["roofline_operator"] = {
+        "bound": "alu", "achieved": opf / t_op / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+        "frac": opf / t_op / 1e9 / fp64_peak, "kernel": "band_pass + band_pass_multi + "
+        "contract_pass (one operator application, 3 launches)", "per_apply_us": t_op * 1e6,
+        "flops_per_apply": opf}
+    # precision forms: one FD apply (pack + 2d tensor-core mode products), graded against
+    # the fused three-pass HBM floor of the FD (3 x 8 bytes per DOF)
+    for f in forms[1:]:
+        Pf = q4[f]["P"]
+        t_fd = time_calls(lambda: Pf.precond_apply(q4[f]["rhs"], out=buf), 20)
+        by = 24.0 * N4
+        tfl = 2.0 * d * 2.0 * n4 ** (d + 1)
+        out[f]["roofline"] = {
+            "bound": "hbm", "achieved": by / t_fd / 1e9, "peak": hbm_peak, "unit": "GB/s",
+            "frac": by / t_fd / 1e9 / hbm_peak, "traffic": None,
+            "kernel": "pack_kernel + 6 x tc_gemm_kernel (one FD apply, tcgen05 " + f + ")",
+            "per_apply_us": t_fd * 1e6, "bytes_per_apply": by,
+            "tensor_tflops": tfl / t_fd / 1e12,
+            "peak_note": hbm_note + " HBM copy bandwidth; bytes = the fused three-pass FD "
+                         "floor (3 x 8 B/DOF)"}
 
-    # end to end through the host-buffer entry point
+    # end to end through the host-buffer entry point (FP64 form)
     e2e_times, e2e_dofit, h2d, d2h = [], 0, 0, 0
     host = []
-    for p, P, rhs, x in fp64:
-        hr = torch.empty(P.N, dtype=torch.float64, pin_memory=True)
-        hr.copy_(rhs.cpu())
-        hx = torch.empty(P.N, dtype=torch.float64, pin_memory=True)
-        host.append((P, hr, hx))
+    for q in probs["fp64"]:
+        hr = torch.empty(q["P"].N, dtype=torch.float64, pin_memory=True)
+        hr.copy_(q["rhs"].cpu())
+        hx = torch.empty(q["P"].N, dtype=torch.float64, pin_memory=True)
+        host.append((q["P"], hr, hx))
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -409,54 +498,77 @@ def run_ours(args):
     eu, et = aggregate(e2e_dofit, sum(e2e_times), dev)
     e2e = {"value": eu / et, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    mixed_out = None
-    if mixed is not None:
-        resm = timed(mixed, args.steps, args.warmup)
-        mt = sum(sum(s[3] for s in step) for step in resm)
-        md = sum(sum(s[1] * s[2] for s in step) for step in resm)
-        mu, mtx = aggregate(md, mt, dev)
-        mixed_out = {"value": mu / mtx, "unit": UNIT,
-                     "iters": {str(s[0]): s[2] for s in resm[-1]},
-                     "relres_true": {str(s[0]): s[4] for s in resm[-1]},
-                     "p50_ms": percentile([s[3] * 1e3 for st in resm for s in st], 50),
-                     "p99_ms": percentile([s[3] * 1e3 for st in resm for s in st], 99),
-                     "time_to_solution_ms_per_step": 1e3 * mt / len(resm)}
-        # error of the precision form's solution against the FP64 form's (the FP64 GPU
-        # solution equals the oracle's at a fixed step count to 1e-10; both stop at 1e-8)
-        mixed_out["rel_err_vs_fp64"] = {
-            str(p): float(torch.linalg.vector_norm(xm - x) / torch.linalg.vector_norm(x))
-            for (p, _, _, x), (_, _, _, xm) in zip(fp64, mixed)}
+    # precision forms against the FP64 form's solution of the same right-hand side
+    for f in forms[1:]:
+        out[f]["rel_err_vs_fp64"] = {
+            str(qa["p"]): float(torch.linalg.vector_norm(qb["x"] - qa["x"]) /
+                                torch.linalg.vector_norm(qa["x"]))
+            for qa, qb in zip(probs["fp64"], probs[f])}
+        out[f]["speedup_vs_fp64_tts_warm"] = (main["tts_warm_ms_per_step"] /
+                                              out[f]["tts_warm_ms_per_step"])
 
-    # Sec. 5's solver on the same problems: BiCGStab + FP64 FD; an iteration is a BiCG
-    # step and a GMRES(1) step (two FD solves, two operator applications), counted in
-    # halves as the paper does
+    # Sec. 5's solver on the same problems: BiCGStab + FP64 FD, counted in halves
     bicg_out = None
     if not args.no_bicgstab:
-        resb = timed(fp64, max(1, args.steps // 2), args.warmup, "bicgstab")
-        bt = sum(sum(s[3] for s in step) for step in resb)
-        bd = sum(sum(s[1] * s[2] for s in step) for step in resb)
-        bu, btx = aggregate(bd, bt, dev)
-        bicg_out = {"value": bu / btx, "unit": "DOF-iter/s (BiCGStab iterations)",
-                    "iters": {str(s[0]): s[2] for s in resb[-1]},
-                    "relres_true": {str(s[0]): s[4] for s in resb[-1]},
-                    "p50_ms": percentile([s[3] * 1e3 for st in resb for s in st], 50),
-                    "time_to_solution_ms_per_step": 1e3 * bt / len(resb)}
+        resb = timed(probs["fp64"], max(1, args.steps // 4), 1, "bicgstab")
+        bs = summarise(probs["fp64"], resb)
+        bicg_out = {"value": bs["value"], "unit": "DOF-iter/s (BiCGStab iterations)",
+                    "iters": bs["iters"], "relres_true": bs["relres_true"],
+                    "p50_ms": bs["p50_ms"], "tts_warm_ms_per_step": bs["tts_warm_ms_per_step"]}
+
+    x4 = {f: q4[f]["x"].double().cpu().numpy() for f in forms}
+    for f in forms:
+        for q in probs[f]:
+            q["P"].close()
+    probs = None
+
+    # config 2 (3d_annulus_ne64, FP64 and TF32), a secondary key
+    secondary = None
+    if not args.no_secondary:
+        secondary = run_secondary(args, dev, stream, flush)
+
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = run_batched(args, steps=3, warmup=1, emit=False)
 
     if rank != 0:
         return 0
     cpu = None
+    oracle_err = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_sample()
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(res64),
+        o = oracle_solve(WORKLOAD, ORACLE_P)
+        cpu = {"value": o["N"] * o["iters"] / o["seconds"], "unit": UNIT,
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one full oracle GMRES+FD solve to 1e-8 of the p={ORACLE_P} problem of "
+                         f"{WORKLOAD} (N={o['N']}, {o['iters']} iterations, {o['seconds']:.1f} s); "
+                         f"matrix-free A_C (eq. collocation via the Kronecker identity), FD of eq. "
+                         f"FD3D, modified Gram-Schmidt; iteration phase only; numpy/OpenBLAS "
+                         f"threads = cores",
+               "busy_cores": o["cpu_seconds"] / o["seconds"]}
+        xo = o["x"]
+        nx = float(np.linalg.norm(xo))
+        oracle_err = {"p": ORACLE_P, "oracle_iters": o["iters"],
+                      "oracle_relres_true": o["relres_true"]}
+        for f in forms:
+            e = float(np.linalg.norm(x4[f] - xo) / nx)
+            out[f]["rel_err_vs_oracle"] = {str(ORACLE_P): e}
+            oracle_err[f] = e
+    for f in forms:
+        out[f].pop("_units", None)
+        out[f].pop("_t", None)
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main["tts_warm_ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": CONFIG,
-            "p50_ms": percentile(solve_ms, 50), "p99_ms": percentile(solve_ms, 99),
-            "iters": iters, "relres_true": relres, "setup_s_cold": t_setup,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "mixed": mixed_out, "bicgstab": bicg_out}
-    if mixed_out is None and not args.no_mixed:
-        line["mixed_unavailable"] = mixed_err if "mixed_err" in locals() else "not built"
+            "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+            "iters": main["iters"], "relres_true": main["relres_true"], "by_p": main["by_p"],
+            "roofline": main["roofline"], "roofline_operator": main["roofline_operator"],
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["gpu_launches"],
+            "clocks": clk, "fp64_peak_gflops": fp64,
+            "rel_err_vs_oracle": oracle_err,
+            "mixed": out.get("tf32"), "bf16": out.get("bf16"), "bicgstab": bicg_out,
+            "config2_3d_annulus_ne64": secondary, "batched": batched}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -464,12 +576,55 @@ def run_ours(args):
     return 0
 
 
+def run_secondary(args, dev, stream, flush, name="3d_annulus_ne64"):
+    """Config 2 (3D, 64 elements, p = 3, 4, 5): FP64 and TF32 forms, a few steps."""
+    import torch
+    from paper_1705_04384_gb300.api import Problem
+    c = W.CONFIGS[name]
+    out = {}
+    for prec in ("fp64", "tf32"):
+        probs = []
+        for i, p in enumerate(c["ps"]):
+            P = Problem(3, c["n_elem"], p, geometry_of(c), c["r0"], c["r1"], precision=prec,
+                        device=dev, stream=stream)
+            rhs = torch.from_numpy(W.config_rhs(name, P.collocation_points(), i)).to(dev)
+            probs.append((p, P, rhs, torch.empty_like(rhs)))
+        for _ in range(2):
+            for p, P, rhs, x in probs:
+                P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+        times, units, its, ms = 0.0, 0.0, {}, []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize(dev)
+            for p, P, rhs, x in probs:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, info = P.solve(rhs, tol=TOL, max_iter=MAX_ITER, out=x)
+                e1.record(stream)
+                e1.synchronize()
+                dt = e0.elapsed_time(e1) * 1e-3
+                times += dt
+                ms.append(dt * 1e3)
+                units += P.N * info["iters"]
+                its[str(p)] = info["iters"]
+        out[prec] = {"value": units / times, "unit": UNIT, "iters": its,
+                     "p50_ms": percentile(ms, 50), "p99_ms": percentile(ms, 99)}
+        for p, P, rhs, x in probs:
+            P.close()
+    out["workload"] = TEXTS[name]
+    return out
+
+
 # ------------------------------------------------------------------------- batched form
-def run_batched(args):
+def run_batched(args, steps=None, warmup=None, emit=True):
     """256 independent 2D quarter-annulus problems (n_elem ~ U{32..512}, p ~ U{2..6},
     r0 ~ U[0.5,1.5], r1 = r0 + 1), 8 seeded Gaussian right-hand sides each, all solved
     by one iga_solve_batched call per step (every problem's 8 rhs in lockstep in one
-    graph, problems concurrent on their own streams)."""
+    graph, problems concurrent on their own streams).  Prints its own line (emit) or
+    returns it as a dict (the batched key of the default line)."""
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     import torch
     from paper_1705_04384_gb300.api import Problem, solve_batched
     dev = torch.device("cuda", 0)
@@ -489,12 +644,12 @@ def run_batched(args):
     torch.cuda.synchronize(dev)
     setup_s = time.perf_counter() - t0
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         solve_batched(probs, rhs, outs, tol=TOL, max_iter=max_iter)
     clocks = ClockSampler(0)
     clocks.start()
     times, dofit, res = [], 0.0, None
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)
         torch.cuda.synchronize(dev)
         t = time.perf_counter()
@@ -509,7 +664,7 @@ def run_batched(args):
     tot = sum(times)
     nsolves = int(res["nrhs"].sum())
     line = {"metric": METRIC + " [batched form]", "value": dofit / tot, "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "dtype": f"f64 outer, {args.precision} FD", "data": "synthetic",
             "config": {"workload": f"batched: {len(probs)} 2D quarter-annulus problems, n_elem "
@@ -523,9 +678,13 @@ def run_batched(args):
             "relres_true_max": float(res["relres_true"].max()),
             "not_converged": int((res["status"] != 0).sum()),
             "setup_s": setup_s, "clocks": clk}
-    print(json.dumps(line), flush=True)
     for P in probs:
         P.close()
+    del flush
+    torch.cuda.empty_cache()
+    if not emit:
+        return line
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -632,19 +791,25 @@ def run_served(args):
 
 def main():
     args = parse()
-    if args.workload in ("3d_revolved_ne64", "3d_wind_ne64"):
-        global WORKLOAD
-        WORKLOAD = args.workload
-        CONFIG["workload"] = REVOLVED_TEXT if args.workload == "3d_revolved_ne64" else WIND_TEXT
-        if args.workload == "3d_wind_ne64":
+    global WORKLOAD
+    named = {"3d_ne128": "3d_annulus_ne128", "3d_ne64": "3d_annulus_ne64",
+             "3d_revolved_ne64": "3d_revolved_ne64", "3d_wind_ne64": "3d_wind_ne64"}
+    if args.workload in named:
+        WORKLOAD = named[args.workload]
+        CONFIG["workload"] = TEXTS[WORKLOAD]
+        if WORKLOAD != "3d_annulus_ne128":
+            args.no_secondary = True
+            args.no_batched = True
+        if WORKLOAD == "3d_wind_ne64":
             args.no_mixed = True  # the wind path runs the FP64 FD only
-        args.workload = "3d_ne64"
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload != "3d_ne64":
+    if args.workload in ("batched", "served"):
         # more hardware queues for many concurrent streams (read at CUDA init)
         os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
         return run_batched(args) if args.workload == "batched" else run_served(args)
+    if not args.no_batched:
+        os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     return run_ours(args)
 
 

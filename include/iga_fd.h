@@ -191,10 +191,15 @@ iga_status iga_solve_collect(iga_handle h, int *iters, double *res_hist_host, do
  * lockstep) and then collected, so the problems overlap on the device.
  *   rhs_dev[q], x_dev[q]     nrhs[q] x N_q doubles (device)
  *   iters, true_relres, status  (host, may be NULL) sum(nrhs) entries, problem-major
+ *   res_hist_host            (host, may be NULL) sum(nrhs) x (max_iter + 1) residual
+ *                            estimates |g_j| / ||rhs||, problem-major, right-hand side r
+ *                            of the whole batch at res_hist_host + r (max_iter + 1);
+ *                            entries past that right-hand side's iterations are 0
  * Returns the worst status as iga_solve_multi does.                          */
 iga_status iga_solve_batched(int nprob, const iga_handle *handles, const int *nrhs,
                              const double *const *rhs_dev, double *const *x_dev, double tol,
-                             int max_iter, int *iters, double *true_relres, int *status);
+                             int max_iter, int *iters, double *res_hist_host,
+                             double *true_relres, int *status);
 
 /* iga_solve with host buffers: copies rhs_host (N doubles) to the device, solves
  * with x0 = 0, and copies the solution to x_host (N doubles).  Same outputs and
@@ -208,24 +213,30 @@ iga_status iga_solve_host(iga_handle h, const double *rhs_host, double *x_host,
  * and one Arnoldi step); builds the graph if no solve has run yet.           */
 iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration);
 
-/* s = P^{-1} b by the same FP64 FD mode-product chain as iga_precond_apply, for
- * callers that cannot allocate device memory when they apply the preconditioner
- * (a fixed memory budget reserved up front, an allocator-free real-time loop, or a
- * host whose own allocator owns the device).  The paper has no counterpart; this
- * is a deployment variant.  No handle is needed and nothing is allocated: the two
- * intermediate tensors live in a static device array of 2 x 2^21 doubles (32 MiB)
- * inside the library, which each GPU that runs this call keeps until exit.
+/* s = P^{-1} b by the FP64 FD method, eq. (FD2D) / (FD3D), for callers that cannot
+ * allocate device memory when they apply the preconditioner (a fixed memory budget
+ * reserved up front, an allocator-free real-time loop, or a host whose own allocator owns
+ * the device).  The paper has no counterpart; this is a deployment variant.  No handle is
+ * needed and nothing is allocated: the two intermediate tensors live in a static device
+ * array of 2 x 2^21 doubles (32 MiB) inside the library.  That array is reserved on a
+ * device when the library's module is loaded there: with CUDA's default lazy loading at
+ * the first call of this function on that device, with CUDA_MODULE_LOADING=EAGER on every
+ * device the library initialises; it stays reserved until the process exits.
  *   d          2 or 3;  n  DOFs per direction; N = n^d must be <= 2097152
- *   Vt_dev     n x n row-major V^T = (M U)^{-1}   (iga_get_factor IGA_FACTOR_VT)
- *   U_dev      n x n row-major U                  (iga_get_factor IGA_FACTOR_U)
- *   lam_dev    n eigenvalues                      (iga_get_factor IGA_FACTOR_LAMBDA)
+ *   Vt_dev     d matrices V_l^T = (M_l U_l)^{-1}, n x n row-major each, direction l at
+ *              Vt_dev + l n^2 (iga_get_factor IGA_FACTOR_VT of direction l)
+ *   U_dev      d matrices U_l, n x n row-major, direction l at U_dev + l n^2
+ *              (IGA_FACTOR_U of direction l)
+ *   lam_dev    d x n eigenvalues, direction l at lam_dev + l n (IGA_FACTOR_LAMBDA)
+ *              Each direction has its own factors: the Poisson pencils of all directions
+ *              coincide on these uniform meshes, the wind-shifted pencils of Sec. 3.2 do not.
  *   b_dev, s_dev  N doubles, must not overlap; all pointers are the caller's
  *   stream     cudaStream_t (NULL = default stream); asynchronous, stream-ordered
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls that overlap on the GPU (other
- * streams, other host threads) race on it and give wrong results.  The array
- * needs no clearing: every entry is written before it is read.
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (other streams, other host
+ * threads) race on it and give wrong results.  The array needs no clearing: every
+ * entry is written before it is read.
  * Errors: INVALID_ARG (bad d, n, null pointer, N above the limit), CUDA.      */
 iga_status iga_precond_apply_noalloc(int d, int n, const double *Vt_dev, const double *U_dev,
                                      const double *lam_dev, const double *b_dev, double *s_dev,
@@ -267,6 +278,25 @@ iga_status iga_set_grid_mode(iga_handle h, iga_grid_mode mode);
  * capture the solve graph now, so that the first solve of that size does no setup.
  * Synchronous; must not be called while a solve is in flight on the handle.  */
 iga_status iga_prepare(iga_handle h, int nrhs, int max_iter);
+
+/* FP64 throughput probe (a measurement utility; the paper has no counterpart): enqueues
+ * one launch that keeps every SM's FP64 unit busy and returns the FLOPs it performs, so
+ * that the caller can time it (CUDA events on `stream`) and obtain the device's FP64
+ * ceiling, against which the FP64 kernels of this library are graded.
+ *   kind   0: mma.sync m8n8k4 .f64 (the FP64 tensor path), 1: FP64 FMAs
+ *   reps   1..2^24 loop turns (each launch runs for about reps x 10 us on a GB300)
+ *   stream cudaStream_t (NULL = default stream); asynchronous
+ *   flops  (host, may be NULL) FLOPs of the launch
+ * Writes no caller memory.  Errors: INVALID_ARG, CUDA.                       */
+iga_status iga_fp64_probe(int kind, int reps, void *stream, double *flops);
+
+/* Test hook (not part of the method): writes `code` into the handle's device error word
+ * -- the word a tensor-core FD kernel sets when one of its bounded waits runs out -- by a
+ * host-to-device copy on the handle's stream, so that a test can check, without making
+ * any device wait run out, that the next solve returns IGA_ERR_DEVICE_TIMEOUT, clears the
+ * word, and that the handle stays usable.  Synchronous.  Only TF32 / BF16 handles have
+ * the word.  Errors: INVALID_ARG (null handle, no tensor-core FD, solve in flight), CUDA. */
+iga_status iga_test_set_device_error(iga_handle h, int code);
 
 /* Release everything the handle owns.  NULL is accepted. */
 iga_status iga_destroy(iga_handle h);

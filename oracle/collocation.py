@@ -20,7 +20,9 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import bspline
-from .geometry import pullback_coefficients, wind_coefficients
+from .fd import kron_apply
+from .geometry import (pullback_coefficients, pullback_coefficients_many, wind_coefficients,
+                       wind_coefficients_many)
 
 
 class Space1D:
@@ -68,6 +70,11 @@ def tensor_points(taus):
 def physical_points(fmap, taus):
     """F(tau_I) for every collocation point, shape (N, d)."""
     return np.array([fmap.F(x) for x in tensor_points(taus)])
+
+
+def physical_points_grid(fmap, taus):
+    """``physical_points`` with the map evaluated on all points at once."""
+    return np.asarray(fmap.F(tensor_points(taus).T), dtype=np.float64).T.copy()
 
 
 def coefficient_fields(fmap, taus):
@@ -169,3 +176,43 @@ def collocation_rows(spaces, fmap, rows, wind=None):
             add(Lv[c], orders)
         out[r] = row
     return out
+
+
+class CollocationOperator:
+    """A_C applied to a vector without assembling it: the definition used by
+    ``assemble_collocation`` (eq. collocation),
+
+        (A_C u)_I = - sum_{a,b} G^{ab}(tau_I) (d_a d_b u_h)(tau_I) - sum_c L_c(tau_I) (d_c u_h)(tau_I),
+
+    where each derivative of u_h = sum_J u_J B_J at the tensor grid of collocation points
+    is the Kronecker product of the 1D matrices B[order] (eq. univariatecolloc) applied to
+    u, evaluated mode by mode (the Kronecker identity).  With a constant wind (Sec. 3.2)
+    the first-order coefficients gain + (J^{-1} w)_c.  For problems whose CSR matrix
+    is too large to assemble in reasonable time."""
+
+    def __init__(self, spaces, fmap, wind=None):
+        self.spaces = spaces
+        self.d = len(spaces)
+        self.shape = tuple(s.n for s in spaces)[::-1]
+        pts = tensor_points([s.tau for s in spaces])
+        G, L = pullback_coefficients_many(fmap, pts)
+        if wind is not None:
+            L = L - wind_coefficients_many(fmap, pts, wind)
+        self.terms = []
+        for a, b in itertools.product(range(self.d), range(self.d)):
+            orders = [0] * self.d
+            orders[a] += 1
+            orders[b] += 1
+            self.terms.append((G[:, a, b].copy(), orders))
+        for c in range(self.d):
+            orders = [0] * self.d
+            orders[c] = 1
+            self.terms.append((L[:, c].copy(), orders))
+
+    def __call__(self, u):
+        u = np.asarray(u, dtype=np.float64)
+        out = np.zeros_like(u)
+        for coef, orders in self.terms:
+            mats = [self.spaces[l].B[orders[l]] for l in range(self.d)]
+            out -= coef * kron_apply(mats, u, self.shape)
+        return out

@@ -25,7 +25,11 @@ import numpy as np
 
 
 class Map:
-    """Analytic map with F(xi), J(xi) (d x d) and Hess(xi) (d x d x d, [k, a, b])."""
+    """Analytic map with F(xi), J(xi) (d x d) and Hess(xi) (d x d x d, [k, a, b]).
+
+    ``xi`` may also be an array of shape (d, ...) holding many points; the results then
+    carry the same trailing axes (F: (d, ...), J: (d, d, ...), H: (d, d, d, ...)).
+    """
 
     d = 0
 
@@ -47,10 +51,15 @@ class Identity(Map):
         return np.array(xi, dtype=np.float64)
 
     def J(self, xi):
-        return np.eye(self.d)
+        xi = np.asarray(xi, dtype=np.float64)
+        out = np.zeros((self.d, self.d) + xi.shape[1:])
+        for a in range(self.d):
+            out[a, a] = 1.0
+        return out
 
     def H(self, xi):
-        return np.zeros((self.d, self.d, self.d))
+        xi = np.asarray(xi, dtype=np.float64)
+        return np.zeros((self.d, self.d, self.d) + xi.shape[1:])
 
 
 class QuarterAnnulus(Map):
@@ -68,18 +77,18 @@ class QuarterAnnulus(Map):
 
     def J(self, xi):
         R = self.r1 - self.r0
-        r = self.r0 + R * xi[0]
-        th = 0.5 * np.pi * xi[1]
+        r = self.r0 + R * np.asarray(xi[0], dtype=np.float64)
+        th = 0.5 * np.pi * np.asarray(xi[1], dtype=np.float64)
         w = 0.5 * np.pi
         return np.array([[R * np.cos(th), -r * w * np.sin(th)],
                          [R * np.sin(th), r * w * np.cos(th)]])
 
     def H(self, xi):
         R = self.r1 - self.r0
-        r = self.r0 + R * xi[0]
-        th = 0.5 * np.pi * xi[1]
+        r = self.r0 + R * np.asarray(xi[0], dtype=np.float64)
+        th = 0.5 * np.pi * np.asarray(xi[1], dtype=np.float64)
         w = 0.5 * np.pi
-        h = np.zeros((2, 2, 2))
+        h = np.zeros((2, 2, 2) + np.shape(th))
         # F_x = r cos(th): d_xi d_eta = -R w sin, d_eta d_eta = -r w^2 cos
         h[0, 0, 1] = h[0, 1, 0] = -R * w * np.sin(th)
         h[0, 1, 1] = -r * w * w * np.cos(th)
@@ -99,16 +108,18 @@ class ExtrudedAnnulus(Map):
 
     def F(self, xi):
         xy = self.ring.F(xi[:2])
-        return np.array([xy[0], xy[1], xi[2]])
+        return np.array([xy[0], xy[1], np.asarray(xi[2], dtype=np.float64)])
 
     def J(self, xi):
-        j = np.zeros((3, 3))
+        xi = np.asarray(xi, dtype=np.float64)
+        j = np.zeros((3, 3) + xi.shape[1:])
         j[:2, :2] = self.ring.J(xi[:2])
         j[2, 2] = 1.0
         return j
 
     def H(self, xi):
-        h = np.zeros((3, 3, 3))
+        xi = np.asarray(xi, dtype=np.float64)
+        h = np.zeros((3, 3, 3) + xi.shape[1:])
         h[:2, :2, :2] = self.ring.H(xi[:2])
         return h
 
@@ -134,7 +145,7 @@ class RevolvedAnnulus(Map):
         a = X - self.c[0]
         b = 0.0 - self.c[2]
         return np.array([self.c[0] + a * np.cos(phi) + b * np.sin(phi),
-                         Y,
+                         Y * np.ones_like(phi),
                          self.c[2] - a * np.sin(phi) + b * np.cos(phi)])
 
     def J(self, xi):
@@ -145,7 +156,7 @@ class RevolvedAnnulus(Map):
         a = X - self.c[0]
         b = 0.0 - self.c[2]
         c, s = np.cos(phi), np.sin(phi)
-        j = np.zeros((3, 3))
+        j = np.zeros((3, 3) + np.shape(phi))
         j[0, 0:2] = c * jr[0, :]
         j[1, 0:2] = jr[1, :]
         j[2, 0:2] = -s * jr[0, :]
@@ -163,7 +174,7 @@ class RevolvedAnnulus(Map):
         a = X - self.c[0]
         b = 0.0 - self.c[2]
         c, s = np.cos(phi), np.sin(phi)
-        h = np.zeros((3, 3, 3))
+        h = np.zeros((3, 3, 3) + np.shape(phi))
         h[0, :2, :2] = c * hr[0]
         h[1, :2, :2] = hr[1]
         h[2, :2, :2] = -s * hr[0]
@@ -220,3 +231,30 @@ def annulus_closed_form(r0, r1, xi):
     G = np.array([[1.0 / R**2, 0.0], [0.0, 4.0 / (np.pi**2 * r * r)]])
     L = np.array([1.0 / (R * r), 0.0])
     return G, L
+
+
+# ----------------------------------------------------------------- many points at once
+# The same formulas as ``pullback_coefficients`` / ``wind_coefficients``, evaluated for an
+# array of parametric points (the maps broadcast over trailing axes).  Used to build the
+# coefficient fields of large problems in seconds; pinned point by point against the
+# single-point functions above.
+
+def pullback_coefficients_many(fmap, xis):
+    """xis: (N, d) parametric points.  Returns G (N, d, d) and Lvec (N, d), the same
+    quantities as ``pullback_coefficients`` at each point."""
+    X = np.asarray(xis, dtype=np.float64).T            # (d, N)
+    J = np.moveaxis(fmap.J(X), -1, 0)                 # (N, d, d)
+    H = np.moveaxis(fmap.H(X), -1, 0)                 # (N, d, d, d)
+    Ji = np.linalg.inv(J)
+    G = Ji @ np.swapaxes(Ji, 1, 2)
+    lap_F = np.einsum("nab,nkab->nk", G, H)
+    Lvec = -np.einsum("nck,nk->nc", Ji, lap_F)
+    return G, Lvec
+
+
+def wind_coefficients_many(fmap, xis, wind):
+    """J^{-1} w at each of the points xis (N, d), as ``wind_coefficients``."""
+    X = np.asarray(xis, dtype=np.float64).T
+    J = np.moveaxis(fmap.J(X), -1, 0)
+    w = np.broadcast_to(np.asarray(wind, dtype=np.float64), (J.shape[0], J.shape[1]))
+    return np.linalg.solve(J, w[..., None])[..., 0]

@@ -47,7 +47,8 @@ PROTOTYPES = {
     "iga_solve_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                                         ctypes.c_void_p]),
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "iga_test_set_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "iga_launch_counts": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p]),
     "iga_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "iga_set_grid_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -57,6 +58,7 @@ PROTOTYPES = {
     "iga_precond_apply_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "iga_fp64_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, c_double_p]),
     "iga_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "iga_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "iga_last_error": (ctypes.c_char_p, []),

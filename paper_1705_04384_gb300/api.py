@@ -221,6 +221,10 @@ class Problem:
         check(self.lib.iga_solve_ready(self.h, ctypes.byref(r)), "iga_solve_ready")
         return bool(r.value)
 
+    def test_set_device_error(self, code):
+        """Test hook: set the handle's device error word from the host."""
+        check(self.lib.iga_test_set_device_error(self.h, int(code)), "iga_test_set_device_error")
+
     def collect(self):
         nrhs, max_iter = self._pending
         iters = np.zeros(nrhs, dtype=np.int32)
@@ -234,10 +238,11 @@ class Problem:
         return dict(iters=iters, relres_true=rel, status=stat)
 
 
-def solve_batched(problems, rhs, out, tol=1e-8, max_iter=200):
+def solve_batched(problems, rhs, out, tol=1e-8, max_iter=200, history=False):
     """Batched form: problems[q] (distinct Problems, ideally on distinct streams),
     rhs[q] / out[q] device tensors (nrhs_q, N_q).  Returns per-rhs arrays
-    (problem-major) of iterations, true relative residuals and statuses."""
+    (problem-major) of iterations, true relative residuals and statuses, and with
+    ``history`` the residual estimates (sum(nrhs) x (max_iter + 1))."""
     lib = _lib.load()
     nprob = len(problems)
     H = (ctypes.c_void_p * nprob)(*[P.h.value for P in problems])
@@ -248,9 +253,49 @@ def solve_batched(problems, rhs, out, tol=1e-8, max_iter=200):
     iters = np.zeros(tot, dtype=np.int32)
     rel = np.zeros(tot, dtype=np.float64)
     stat = np.zeros(tot, dtype=np.int32)
+    hist = np.zeros((tot, max_iter + 1), dtype=np.float64) if history else None
     st = lib.iga_solve_batched(nprob, H, nr.ctypes.data_as(ctypes.c_void_p), R, X, float(tol),
                                int(max_iter), iters.ctypes.data_as(ctypes.c_void_p),
+                               hist.ctypes.data_as(ctypes.c_void_p) if history else None,
                                rel.ctypes.data_as(ctypes.c_void_p),
                                stat.ctypes.data_as(ctypes.c_void_p))
     check(st, "iga_solve_batched", (STATUS_NO_CONVERGENCE,))
-    return dict(iters=iters, relres_true=rel, status=stat, nrhs=nr)
+    out = dict(iters=iters, relres_true=rel, status=stat, nrhs=nr)
+    if history:
+        out["hist"] = hist
+    return out
+
+
+def fp64_probe(kind=0, reps=1000, stream=None):
+    """Enqueue one FP64 throughput probe launch (``iga_fp64_probe``: kind 0 = FP64
+    mma.sync, 1 = FP64 FMAs) on ``stream`` and return its FLOP count; time it with CUDA
+    events on the same stream."""
+    lib = _lib.load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    fl = ctypes.c_double()
+    check(lib.iga_fp64_probe(int(kind), int(reps), ctypes.c_void_p(stream.cuda_stream),
+                             ctypes.byref(fl)), "iga_fp64_probe")
+    return fl.value
+
+
+def measure_fp64_peak(reps=1000, trials=5, stream=None):
+    """FP64 ceiling of the current device in GFLOP/s: the best of ``trials`` timed launches
+    of each probe kind (after one warm-up launch each).  Returns dict(dmma, fma, peak)."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = {}
+    for kind, name in ((0, "dmma"), (1, "fma")):
+        fp64_probe(kind, reps, stream)
+        best = 0.0
+        for _ in range(trials):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fl = fp64_probe(kind, reps, stream)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, fl / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        out[name] = best
+    out["peak"] = max(out["dmma"], out["fma"])
+    return out

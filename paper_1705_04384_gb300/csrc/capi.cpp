@@ -193,7 +193,8 @@ iga_status iga_solve_collect(iga_handle h, int *iters, double *res_hist_host, do
 
 iga_status iga_solve_batched(int nprob, const iga_handle *handles, const int *nrhs,
                              const double *const *rhs_dev, double *const *x_dev, double tol,
-                             int max_iter, int *iters, double *true_relres, int *status) {
+                             int max_iter, int *iters, double *res_hist_host, double *true_relres,
+                             int *status) {
   return guarded([&]() -> iga_status {
     if (nprob < 1 || !handles || !nrhs || !rhs_dev || !x_dev)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad batch arguments"};
@@ -222,9 +223,10 @@ iga_status iga_solve_batched(int nprob, const iga_handle *handles, const int *nr
     }
     long long off = 0;
     for (int q = 0; q < nprob; ++q) {
-      const iga_status st = handles[q]->c.collect(iters ? iters + off : nullptr, nullptr,
-                                                  true_relres ? true_relres + off : nullptr,
-                                                  status ? status + off : nullptr);
+      const iga_status st = handles[q]->c.collect(
+          iters ? iters + off : nullptr,
+          res_hist_host ? res_hist_host + (size_t)off * (max_iter + 1) : nullptr,
+          true_relres ? true_relres + off : nullptr, status ? status + off : nullptr);
       if (st == IGA_ERR_NAN) overall = IGA_ERR_NAN;
       else if (st != IGA_OK && overall == IGA_OK) overall = st;
       off += nrhs[q];
@@ -291,6 +293,19 @@ iga_status iga_prepare(iga_handle h, int nrhs, int max_iter) {
     if (c.pending) throw iga::Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
     c.ensure_ws(max_iter, nrhs);
     c.graph_for(nrhs, 0);
+    IGA_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    return IGA_OK;
+  });
+}
+
+iga_status iga_test_set_device_error(iga_handle h, int code) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    iga::Ctx &c = h->c;
+    if (!c.tc) throw iga::Error{IGA_ERR_INVALID_ARG, "the handle has no tensor-core FD"};
+    if (c.pending) throw iga::Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
+    IGA_CUDA_TRY(cudaMemcpyAsync(iga::tc_fd_error_word(*c.tc), &code, sizeof(int),
+                                 cudaMemcpyHostToDevice, c.stream));
     IGA_CUDA_TRY(cudaStreamSynchronize(c.stream));
     return IGA_OK;
   });

@@ -13,8 +13,10 @@
 
 namespace iga {
 
-// Scratch capacity: two tensors of up to kNoAllocMaxN doubles (2 x 16 MiB).  Every
-// GPU on which this entry point runs keeps the array until the process exits.
+// Scratch capacity: two tensors of up to kNoAllocMaxN doubles (2 x 16 MiB).  The array is
+// reserved on a device when this file's module is loaded there -- with CUDA's default lazy
+// loading, at the first call on that device; with CUDA_MODULE_LOADING=EAGER, on every
+// device the library initialises -- and stays reserved until the process exits.
 constexpr long long kNoAllocMaxN = 1LL << 21;
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxN];
 
@@ -53,33 +55,48 @@ extern "C" iga_status iga_precond_apply_noalloc(int d, int n, const double *Vt_d
     if (n < 1) throw Error{IGA_ERR_INVALID_ARG, "n must be positive"};
     if (!Vt_dev || !U_dev || !lam_dev || !b_dev || !s_dev)
       throw Error{IGA_ERR_INVALID_ARG, "null argument"};
+    // N = n^d, checked after every factor so that no product can wrap around
     long long N = 1;
-    for (int l = 0; l < d; ++l) N *= n;
-    if (N > kNoAllocMaxN)
-      throw Error{IGA_ERR_INVALID_ARG,
-                  "N = n^d = " + std::to_string(N) +
-                      " exceeds the 2097152-value static scratch of iga_precond_apply_noalloc"};
+    for (int l = 0; l < d; ++l) {
+      if (n > kNoAllocMaxN || N * n > kNoAllocMaxN)
+        throw Error{IGA_ERR_INVALID_ARG,
+                    "N = n^d with n = " + std::to_string(n) + ", d = " + std::to_string(d) +
+                        " exceeds the 2097152-value static scratch of iga_precond_apply_noalloc"};
+      N *= n;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     double *t0 = noalloc_scratch();
     double *t1 = t0 + kNoAllocMaxN;
     // Every entry of t0 / t1 is written before it is read, so nothing needs clearing.
     const int M = (int)(N / n);
+    const size_t nn = (size_t)n * n;
+    // direction l's factors: V_l^T and U_l at l n^2, its eigenvalues at l n
+    const double *Vt[3], *U[3], *lam[3];
+    for (int l = 0; l < d; ++l) {
+      Vt[l] = Vt_dev + l * nn;
+      U[l] = U_dev + l * nn;
+      lam[l] = lam_dev + (size_t)l * n;
+    }
     auto P = [](double *p) { return plain_ptr<double>(p); };
     auto Pc = [](const double *p) { return plain_ptr<const double>(p); };
+    // The g-th forward product contracts direction g with V_g^T, the g-th inverse product
+    // with U_g (layout rotation: the contracted index is always the fastest); the diagonal
+    // 1 / (lambda_{0,k1} + lambda_{1,k2} (+ lambda_{2,k3})) is fused into the d-th forward
+    // product, whose rows are (k1, k2) in 3D (k1 in 2D) and whose columns are k_d.
     if (d == 2) {
-      const FdScale sc{lam_dev, nullptr, lam_dev, n};
-      launch_gemm_fp64<double>(Pc(b_dev), Vt_dev, P(t0), M, n, n, nullptr, s);
-      launch_gemm_fp64<double>(Pc(t0), Vt_dev, P(t1), M, n, n, &sc, s);
-      launch_gemm_fp64<double>(Pc(t1), U_dev, P(t0), M, n, n, nullptr, s);
-      launch_gemm_fp64<double>(Pc(t0), U_dev, P(s_dev), M, n, n, nullptr, s);
+      const FdScale sc{lam[0], nullptr, lam[1], n};
+      launch_gemm_fp64<double>(Pc(b_dev), Vt[0], P(t0), M, n, n, nullptr, s);
+      launch_gemm_fp64<double>(Pc(t0), Vt[1], P(t1), M, n, n, &sc, s);
+      launch_gemm_fp64<double>(Pc(t1), U[0], P(t0), M, n, n, nullptr, s);
+      launch_gemm_fp64<double>(Pc(t0), U[1], P(s_dev), M, n, n, nullptr, s);
     } else {
-      const FdScale sc{lam_dev, lam_dev, lam_dev, n};
-      launch_gemm_fp64<double>(Pc(b_dev), Vt_dev, P(t0), M, n, n, nullptr, s);
-      launch_gemm_fp64<double>(Pc(t0), Vt_dev, P(t1), M, n, n, nullptr, s);
-      launch_gemm_fp64<double>(Pc(t1), Vt_dev, P(t0), M, n, n, &sc, s);
-      launch_gemm_fp64<double>(Pc(t0), U_dev, P(t1), M, n, n, nullptr, s);
-      launch_gemm_fp64<double>(Pc(t1), U_dev, P(t0), M, n, n, nullptr, s);
-      launch_gemm_fp64<double>(Pc(t0), U_dev, P(s_dev), M, n, n, nullptr, s);
+      const FdScale sc{lam[0], lam[1], lam[2], n};
+      launch_gemm_fp64<double>(Pc(b_dev), Vt[0], P(t0), M, n, n, nullptr, s);
+      launch_gemm_fp64<double>(Pc(t0), Vt[1], P(t1), M, n, n, nullptr, s);
+      launch_gemm_fp64<double>(Pc(t1), Vt[2], P(t0), M, n, n, &sc, s);
+      launch_gemm_fp64<double>(Pc(t0), U[0], P(t1), M, n, n, nullptr, s);
+      launch_gemm_fp64<double>(Pc(t1), U[1], P(t0), M, n, n, nullptr, s);
+      launch_gemm_fp64<double>(Pc(t0), U[2], P(s_dev), M, n, n, nullptr, s);
     }
     return IGA_OK;
   } catch (const Error &e) {

@@ -192,12 +192,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint8_t *sA = smem;
   uint8_t *sB = smem + nstage * a_bytes;
 
+  __shared__ int mma_failed;
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstage; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&done_bar, 1);
+    mma_failed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(&tmem_base, (uint32_t)tmem_cols);
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = tmem_base;
 
   if (warp == 0 && lane == 0) {
+    int issued = 0;
     for (int c = 0; c < nchunks; ++c) {
       const int s = c % nstage, use = c / nstage;
       if (use > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
@@ -216,14 +219,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_expect_tx(&full_bar[s], a_bytes + b_bytes);
       tma_load_2d(sA + s * a_bytes, &mapA, &full_bar[s], c * kbox, m0);
       tma_load_2d(sB + s * b_bytes, &mapB, &full_bar[s], c * kbox, c0);
+      ++issued;
     }
+    // no copy may still be landing in shared memory when the CTA exits: wait (bounded)
+    // for the last uses of the ring (on the normal path the MMAs consumed them already)
+    for (int h = issued > nstage ? issued - nstage : 0; h < issued; ++h)
+      mbar_wait(&full_bar[h % nstage], (uint32_t)((h / nstage) & 1));
   } else if (warp == 1 && lane == 0) {
-    bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int s = c % nstage, use = c / nstage;
       if (!mbar_wait(&full_bar[s], (uint32_t)(use & 1))) {
         atomicExch(epi.err, 2);
-        ok = false;
+        mma_failed = 1;
         break;
       }
       tc_fence_after();
@@ -235,7 +242,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         (c > 0 || j > 0) ? 1u : 0u);
       mma_commit(&empty_bar[s]);
     }
-    if (ok) mma_commit(&done_bar);
+    // committed on every path: done_bar completes once every MMA issued above has, so
+    // tensor memory is never released under an MMA still writing it
+    mma_commit(&done_bar);
   }
   __syncwarp();
 
@@ -244,6 +253,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const bool have = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0) ? 1 : 0) != 0;
   if (!have) {
     if (lane == 0) atomicExch(epi.err, 3);
+  } else if (*(volatile int *)&mma_failed) {
+    // the accumulator is incomplete (the error word is already set): store nothing
   } else {
     tc_fence_after();
     // row = a + n (m + nmid r): a = fastest component, m = middle, r = right-hand side;
@@ -563,10 +574,13 @@ static void set_tile(TcFd &t, int n_tile, int persistent = 0) {
   }
 }
 
-static bool persistent_enabled() {
+// IGA_TC_PERSISTENT: unset or 0, one-tile kernel only; 1, the autotuner also times the
+// persistent kernel; 2, the persistent kernel only (to check it against the oracle).
+static int persistent_mode() {
   const char *e = std::getenv("IGA_TC_PERSISTENT");
-  return e && e[0] == '1';
+  return (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
 }
+static bool persistent_enabled() { return persistent_mode() != 0; }
 
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
 // candidate column tile -- the whole padded width, or 2, 3, 4 ... narrower tiles that
@@ -598,7 +612,8 @@ static void autotune(TcFd &t, cudaStream_t s) {
   }
   // (column tile, persistent kernel)
   std::vector<std::pair<int, int>> cand;
-  for (int nt : widths) cand.push_back({nt, 0});
+  if (persistent_mode() != 2)
+    for (int nt : widths) cand.push_back({nt, 0});
   if (persistent_enabled())
     for (int nt : widths) cand.push_back({nt, 1});
   std::pair<int, int> best = cand[0];

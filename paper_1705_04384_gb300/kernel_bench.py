@@ -2,6 +2,7 @@
 
     python -m paper_1705_04384_gb300.kernel_bench --op fd|operator|solve \
         --d 3 --ne 64 --p 3 --precision fp64 --reps 20
+    python -m paper_1705_04384_gb300.kernel_bench --op fp64peak
 
 Used to attribute time to kernels and as the small, self-contained command for
 ncu captures.  Prints one JSON line with the mean time per call.
@@ -13,12 +14,12 @@ import json
 import numpy as np
 import torch
 
-from .api import Problem
+from .api import Problem, measure_fp64_peak
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", default="fd", choices=["fd", "operator", "solve"])
+    ap.add_argument("--op", default="fd", choices=["fd", "operator", "solve", "fp64peak"])
     ap.add_argument("--d", type=int, default=3)
     ap.add_argument("--ne", type=int, default=64)
     ap.add_argument("--p", type=int, default=3)
@@ -27,6 +28,12 @@ def main():
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     a = ap.parse_args()
+    if a.op == "fp64peak":
+        # the FP64 ceiling (iga_fp64_probe): best of a.reps timed launches per probe kind
+        r = measure_fp64_peak(reps=1000, trials=a.reps)
+        print(json.dumps({"op": "fp64peak", "gflops_dmma": r["dmma"], "gflops_fma": r["fma"],
+                          "gflops_peak": r["peak"], "trials": a.reps}))
+        return
     P = Problem(a.d, a.ne, a.p, geometry=a.geometry, precision=a.precision)
     g = torch.Generator(device="cpu").manual_seed(0)
     b = torch.randn(P.N, dtype=torch.float64, generator=g).cuda()

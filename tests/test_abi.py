@@ -93,6 +93,7 @@ def test_every_handle_entry_point_rejects_a_null_handle(lib):
         ("iga_launch_counts", (null, None, None)),
         ("iga_prepare", (null, 1, 10)),
         ("iga_solve_bicgstab", (null, null, null, 0, 1e-8, 10, None, null, None)),
+        ("iga_test_set_device_error", (null, 1)),
     ]
     for name, args in calls:
         assert getattr(lib, name)(*args) == 1, name  # IGA_ERR_INVALID_ARG
@@ -100,11 +101,18 @@ def test_every_handle_entry_point_rejects_a_null_handle(lib):
 
 
 def test_batch_and_noalloc_argument_checks(lib):
-    assert lib.iga_solve_batched(0, None, None, None, None, 1e-8, 10, None, None, None) == 1
+    assert lib.iga_solve_batched(0, None, None, None, None, 1e-8, 10, None, None, None,
+                                 None) == 1
     assert b"batch" in lib.iga_last_error()
     # d outside 2..3, then a null factor pointer
     assert lib.iga_precond_apply_noalloc(4, 10, None, None, None, None, None, None) == 1
     assert lib.iga_precond_apply_noalloc(3, 10, None, None, None, None, None, None) == 1
+
+
+def test_fp64_probe_argument_checks(lib):
+    assert lib.iga_fp64_probe(2, 10, None, None) == 1
+    assert lib.iga_fp64_probe(0, 0, None, None) == 1
+    assert b"reps" in lib.iga_last_error()
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -1,9 +1,10 @@
 """The reference arm of bench.py on CPU: the oracle timed on the host cores, one JSON line.
 
 `bench.py --impl reference` times the FP64 oracle (GMRES + FD, Sec. 3-4) on a bounded sample
-of the benchmark workload and prints the same line as the GPU arm, with `"impl": "reference"`,
-a `cpu_baseline` that describes the run and an `e2e` object with no host-device bytes.  One
-step (about 20 s here) checks the keys, their types and that the sampled solve converged.
+of the benchmark workload (a few Arnoldi iterations of its p = 4 problem per step) and prints
+the same line as the GPU arm, with `"impl": "reference"`, a `cpu_baseline` that describes the
+run and an `e2e` object with no host-device bytes.  One step checks the keys, their types and
+that the sampled iterations reduced the residual.
 """
 
 import json
@@ -41,5 +42,6 @@ def test_reference_arm_prints_one_contract_line():
     e2e = line["e2e"]
     assert e2e == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}
-    # the sampled solve reached the GMRES target (Givens estimate of the relative residual)
-    assert line["last_relres_est"] <= bench.TOL
+    # the sampled Arnoldi iterations reduced the relative residual estimate (FD-preconditioned
+    # GMRES on this problem gains more than a digit in three steps)
+    assert 0 < line["last_relres_est"] < 0.1

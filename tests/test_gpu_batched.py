@@ -90,15 +90,22 @@ def test_batched_uneven_problems_match_individual_solves(prec):
         outs.append(torch.empty_like(B))
         refs.append(ref(d, ne, p, "annulus", r0, r0 + 1.0))
     torch.cuda.synchronize()
-    res = solve_batched(probs, rhs, outs, tol=1e-8, max_iter=200)
+    res = solve_batched(probs, rhs, outs, tol=1e-8, max_iter=200, history=True)
     torch.cuda.synchronize()
     assert np.all(res["status"] == 0)
+    assert res["hist"].shape == (int(res["nrhs"].sum()), 201)
     off = 0
     for P, B, X, R in zip(probs, rhs, outs, refs):
         nr = B.shape[0]
         Xi, info = P.solve_multi(B, tol=1e-8, max_iter=200)
         assert torch.equal(Xi, X)
         assert np.array_equal(info["iters"], res["iters"][off:off + nr])
+        for r in range(nr):
+            # the batch returns each right-hand side's residual history, bitwise the same as
+            # alone, zero past its last iteration
+            k = int(info["iters"][r])
+            assert np.array_equal(res["hist"][off + r, :k + 1], info["hist"][r])
+            assert not np.any(res["hist"][off + r, k + 1:])
         Bn, Xn = B.cpu().numpy(), X.cpu().numpy()
         for r in range(nr):
             assert np.linalg.norm(Bn[r] - R.A @ Xn[r]) / np.linalg.norm(Bn[r]) <= 1.05e-8

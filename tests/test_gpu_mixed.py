@@ -104,3 +104,21 @@ def test_mixed_full_size_3d_ne128(prec, p):
     assert diff <= 1e-7  # measured 1.3e-9 .. 1.6e-9
     # the outer iteration wins back the lost precision with a modest count increase
     assert info["iters"] <= 2 * info64["iters"] + 5
+
+
+def test_device_error_word_reports_timeout_and_handle_stays_usable():
+    """The tensor-core kernels report a bounded wait that ran out through a device error
+    word; the next collect maps it to IGA_ERR_DEVICE_TIMEOUT and clears it.  No wait is made
+    to run out here: the word is set from the host (iga_test_set_device_error)."""
+    from paper_1705_04384_gb300 import IgaError
+    with _problem(2, 24, 3, "tf32") as P:
+        b = torch.from_numpy(np.random.default_rng(3).standard_normal(P.N)).cuda()
+        x0, i0 = P.solve(b, tol=1e-8, max_iter=100)
+        x0 = x0.clone()
+        P.test_set_device_error(2)
+        with pytest.raises(IgaError) as e:
+            P.solve(b, tol=1e-8, max_iter=100)
+        assert e.value.status == 6 and "timed out" in str(e.value)
+        x1, i1 = P.solve(b, tol=1e-8, max_iter=100)
+        assert i1["status"] == 0 and i1["iters"] == i0["iters"]
+        assert torch.equal(x1, x0)

@@ -187,3 +187,42 @@ def test_collocation_rows_match_assembly(kind, d):
     rows = [0, 5, A.shape[0] - 1, A.shape[0] // 2]
     R = C.collocation_rows(spaces, fmap, rows)
     assert np.max(np.abs(R - A[rows])) < 1e-13 * np.max(np.abs(A))
+
+
+# ---------------------------------------------------------------- whole-grid evaluation
+@pytest.mark.parametrize("kind,d", [("identity", 2), ("identity", 3), ("annulus", 2),
+                                    ("annulus", 3), ("revolved", 3)])
+def test_many_point_geometry_matches_point_by_point(kind, d):
+    """pullback_coefficients_many / wind_coefficients_many / physical_points_grid evaluate
+    the same formulas on arrays of points: equal to the single-point functions (which the
+    closed-form and finite-difference pins above check)."""
+    fmap = Geo.make_map(kind, d, 0.8, 1.9)
+    xs = np.random.default_rng(5).uniform(size=(40, d))
+    G, L = Geo.pullback_coefficients_many(fmap, xs)
+    Wc = Geo.wind_coefficients_many(fmap, xs, [1.5, -2.0, 0.5][:d])
+    for i, x in enumerate(xs):
+        g, l = Geo.pullback_coefficients(fmap, x)
+        assert np.allclose(G[i], g, rtol=1e-13, atol=1e-13)
+        assert np.allclose(L[i], l, rtol=1e-13, atol=1e-13)
+        assert np.allclose(Wc[i], Geo.wind_coefficients(fmap, x, [1.5, -2.0, 0.5][:d]),
+                           rtol=1e-13, atol=1e-13)
+    taus = [C.Space1D(4 + l, 2).tau for l in range(d)]
+    assert np.array_equal(C.physical_points_grid(fmap, taus), C.physical_points(fmap, taus))
+
+
+@pytest.mark.parametrize("kind,d,wind", [("annulus", 2, None), ("annulus", 3, None),
+                                         ("revolved", 3, None), ("identity", 3, None),
+                                         ("annulus", 3, (1.0, -2.0, 3.0))])
+def test_matrix_free_operator_equals_assembled(kind, d, wind):
+    """CollocationOperator applies the definition of A_C through the Kronecker identity; it
+    equals the assembled CSR matrix (pinned above by exact polynomials, the polar form and
+    A = P on the identity map) applied to random vectors.  Directions of different sizes
+    catch a transposed mode order."""
+    spaces = [C.Space1D(5 + l, 3) for l in range(d)]
+    fmap = Geo.make_map(kind, d, 1.0, 2.0)
+    A = C.assemble_collocation(spaces, fmap, wind)
+    op = C.CollocationOperator(spaces, fmap, wind)
+    for seed in range(2):
+        u = np.random.default_rng(seed).standard_normal(A.shape[0])
+        ref_ = A @ u
+        assert np.max(np.abs(op(u) - ref_)) <= 1e-13 * np.max(np.abs(ref_))
