@@ -24,6 +24,10 @@ analysis" (arXiv:1705.04384), in numpy/scipy FP64:
                      flexible variant used for a variable preconditioner.
 * ``bicgstab``    -- right-preconditioned BiCGStab (van der Vorst 1992), the solver of
                      Sec. 5, with the paper's half-iteration counting.
+* ``wq``          -- the weighted-quadrature Galerkin discretization (Sec. 2.3, eq.
+                     WQapprox, eq. Q, eq. wq2D / wq3D): univariate rules exact on the
+                     spline space, the assembled A_wq, the exact Galerkin A_G, the
+                     Galerkin right-hand side and P_wq (symmetric FD of Sec. 4).
 * convection--diffusion (Sec. 3.2) with a constant wind: ``geometry.wind_coefficients``,
   the ``wind`` arguments of ``collocation`` and ``fd.FD``.
 
@@ -32,4 +36,4 @@ against closed forms, library routines, invariants or brute force; none is
 "parity unpinned".
 """
 
-from . import bspline, geometry, collocation, fd, gmres, bicgstab  # noqa: F401
+from . import bspline, geometry, collocation, fd, gmres, bicgstab, wq  # noqa: F401

@@ -92,3 +92,38 @@ def test_wrong_sign_or_transpose_of_wind_term_is_caught(monkeypatch):
                         lambda fmap, xi, w: np.linalg.solve(fmap.J(xi).T, np.asarray(w)))
     with pytest.raises(AssertionError):
         TW.test_convective_term_against_finite_differences()
+
+
+def test_swapped_mixed_wq_weights_are_caught(monkeypatch):
+    """Weighted quadrature (Sec. 2.3): using the (0, 1) rule where the (1, 0) rule belongs
+    breaks exactness for constant coefficients with off-diagonal Q."""
+    from oracle import wq as Q
+    import tests.test_oracle_wq as TW
+    orig = Q.WQSpace1D.weights
+
+    def swapped(self, s, t):
+        if (s, t) in ((0, 1), (1, 0)):
+            return orig(self, t, s)
+        return orig(self, s, t)
+
+    monkeypatch.setattr(Q.WQSpace1D, "weights", swapped)
+    with pytest.raises(AssertionError):
+        TW.test_constant_coefficients_are_integrated_exactly(2, [[1.3, 0.4], [-0.2, 0.9]])
+
+
+def test_wq_weights_outside_the_support_are_caught(monkeypatch):
+    """A rule spread over every quadrature point (still exact) is not a weighted quadrature of
+    the test function: the support pin fails."""
+    from oracle import wq as Q
+    import tests.test_oracle_wq as TW
+
+    def global_rule(self, s, t):
+        W = np.zeros((self.n, self.nq))
+        for r, i in enumerate(range(1, self.m - 1)):
+            E = self.Bq_full[t].T
+            W[r], *_ = np.linalg.lstsq(E, self.G[(s, t)][i], rcond=None)
+        return W
+
+    monkeypatch.setattr(Q.WQSpace1D, "weights", global_rule)
+    with pytest.raises(AssertionError):
+        TW.test_univariate_rules_are_exact_on_the_spline_space(8, 3)
