@@ -89,7 +89,22 @@ typedef enum {
   IGA_PREC_NONE = 3
 } iga_precision;
 
-/* Factor selectors for iga_get_factor (all n x n row-major unless noted). */
+/* Discretization scheme of iga_setup_scheme.
+ *  COLLOCATION   isogeometric collocation at the Greville points (Sec. 2.2, eq.
+ *                collocationsystem); preconditioner P_C of eq. colloc2D / colloc3D.
+ *  WQ_GALERKIN   Galerkin with weighted quadrature (Sec. 2.3, eq. WQapprox): test
+ *                function i's univariate rules w^{(s,t)} are exact on the spline space
+ *                (every overlapping basis function, value or derivative), live on the
+ *                quadrature points in its support and have minimum 2-norm; quadrature
+ *                points are the element end points and midpoints, with p equispaced
+ *                interior points in the first and last element; coefficients Q =
+ *                det(J) J^{-1} J^{-T} (eq. Q, K = I).  Preconditioner P_wq = P_G of eq.
+ *                wq2D / wq3D (univariate Galerkin M, K: the symmetric FD of Sec. 4).  No
+ *                wind.  The right-hand side is the caller's (see iga_wq_load).          */
+typedef enum { IGA_SCHEME_COLLOCATION = 0, IGA_SCHEME_WQ_GALERKIN = 1 } iga_scheme;
+
+/* Factor selectors for iga_get_factor (all n x n row-major unless noted).  For a
+ * WQ_GALERKIN problem M and K are the univariate Galerkin matrices of eq. (univariateWQ). */
 typedef enum {
   IGA_FACTOR_TAU = 0,    /* Greville points tau_i, eq. (greville): n values        */
   IGA_FACTOR_M = 1,      /* (M)_ij = B_j(tau_i), eq. (univariatecolloc)            */
@@ -114,13 +129,33 @@ typedef enum {
 iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom,
                      int precision, void *stream, iga_handle *out);
 
+/* iga_setup with a choice of discretization (iga_scheme); iga_setup is scheme
+ * COLLOCATION.  Same arguments, ownership and errors as iga_setup; WQ_GALERKIN rejects a
+ * nonzero wind (INVALID_ARG).                                                */
+iga_status iga_setup_scheme(int d, int n_elem, int p, const iga_geometry *geom, int scheme,
+                            int precision, void *stream, iga_handle *out);
+
 /* n (DOFs per direction) and N = n^d.  Either pointer may be NULL. */
 iga_status iga_dims(iga_handle h, int *n, long long *N);
 
 /* Physical collocation points F(tau_I) (eq. collocation), written as N x d
  * row-major doubles (point I at xyz_host[I*d .. I*d+d-1]) in DOF order.  The
- * right-hand side of eq. (collocationsystem) is f evaluated at these points. */
+ * right-hand side of eq. (collocationsystem) is f evaluated at these points.
+ * UNSUPPORTED for a WQ_GALERKIN problem.                                      */
 iga_status iga_collocation_points(iga_handle h, double *xyz_host);
+
+/* WQ_GALERKIN problems only (UNSUPPORTED otherwise): nq quadrature points per direction and
+ * Nq = nq^d; the physical quadrature points F(x_q), Nq x d row-major, direction 1 fastest
+ * (the order of the values iga_wq_load takes).                               */
+iga_status iga_quadrature_dims(iga_handle h, int *nq, long long *Nq);
+iga_status iga_quadrature_points(iga_handle h, double *xyz_host);
+
+/* WQ_GALERKIN problems only: the load vector f_I = sum_q w^{00}_{Iq} |det J(x_q)| g_q, the
+ * weighted-quadrature approximation of int g(F(xi)) B_I(xi) |det J(xi)| dxi (Sec. 2.3: the
+ * right-hand side of eq. WQsystem "by using again the WQ approach").  g_dev: Nq doubles
+ * (values of the source at iga_quadrature_points); f_dev: N doubles.  Stream-ordered,
+ * asynchronous.  Errors: INVALID_ARG, UNSUPPORTED (collocation problem), CUDA. */
+iga_status iga_wq_load(iga_handle h, const double *g_dev, double *f_dev);
 
 /* Copy a 1D factor of direction dir (0..d-1) to host memory (see iga_factor for
  * shapes).  Synchronous.                                                     */
@@ -128,8 +163,10 @@ iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host);
 
 /* Au = A_C u: the collocation matrix of eq. (collocationsystem), applied matrix-
  * free by sum factorization of the banded 1D factors and a pointwise contraction
- * with the geometry coefficients.  u_dev, Au_dev: N doubles, must not overlap.
- * Stream-ordered, asynchronous.                                              */
+ * with the geometry coefficients.  For a WQ_GALERKIN problem Au = A_wq u (eq.
+ * WQapprox), by sum factorization onto the quadrature grid and back (banded basis
+ * values / derivatives at the points, the Q field, banded univariate rules).
+ * u_dev, Au_dev: N doubles, must not overlap.  Stream-ordered, asynchronous.  */
 iga_status iga_apply_operator(iga_handle h, const double *u_dev, double *Au_dev);
 
 /* s = P^{-1} b by the FD method, eq. (FD2D) (d = 2) or eq. (FD3D) (d = 3), in the

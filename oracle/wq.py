@@ -228,3 +228,45 @@ def assemble_preconditioner_wq(spaces):
         term = kron_list([spaces[j].K if j == l else spaces[j].M for j in range(d)])
         P = term if P is None else P + term
     return P.tocsr()
+
+
+def quadrature_points_physical(spaces, fmap):
+    """F(x_q) on the tensor grid of WQ quadrature points (direction 1 fastest): (Nq, d)."""
+    return np.asarray(fmap.F(tensor_points([s.xq for s in spaces]).T), dtype=np.float64).T.copy()
+
+
+def wq_load(spaces, fmap, g):
+    """The WQ load vector (Sec. 2.3, the right-hand side 'by using again the WQ approach'):
+    f_I = sum_q w^{00}_{I q} |det J(x_q)| g_q for source values g at the quadrature points."""
+    pts = tensor_points([s.xq for s in spaces])
+    detJ = np.abs(np.linalg.det(np.moveaxis(fmap.J(pts.T), -1, 0)))
+    Wk = kron_list([s.W[(0, 0)] for s in spaces])
+    return Wk @ (detJ * np.asarray(g, dtype=np.float64))
+
+
+class WQOperator:
+    """A_wq applied without assembling it: the sum of eq. (WQapprox) written as
+    W_ab diag(Q_ab) B_b u per term (a, b), each tensor product applied mode by mode
+    (the Kronecker identity), for problems too large to assemble quickly."""
+
+    def __init__(self, spaces, fmap):
+        from .fd import kron_apply
+        self._kron_apply = kron_apply
+        self.spaces = spaces
+        self.d = len(spaces)
+        self.shape_n = tuple(s.n for s in spaces)[::-1]
+        self.shape_q = tuple(s.nq for s in spaces)[::-1]
+        pts = tensor_points([s.xq for s in spaces])
+        self.Q = q_coefficients_many(fmap, pts)
+
+    def __call__(self, u):
+        u = np.asarray(u, dtype=np.float64)
+        out = np.zeros_like(u)
+        d = self.d
+        for a, b in itertools.product(range(d), range(d)):
+            oa, ob = _orders(d, a), _orders(d, b)
+            y = self._kron_apply([self.spaces[l].Bq[ob[l]] for l in range(d)], u, self.shape_n)
+            y = self.Q[:, a, b] * y
+            out += self._kron_apply([self.spaces[l].W[(oa[l], ob[l])] for l in range(d)], y,
+                                    self.shape_q)
+        return out

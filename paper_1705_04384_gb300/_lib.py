@@ -24,7 +24,13 @@ class Geometry(ctypes.Structure):
 PROTOTYPES = {
     "iga_setup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Geometry),
                                  ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "iga_setup_scheme": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(Geometry), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "iga_dims": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_ll_p]),
+    "iga_quadrature_dims": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_ll_p]),
+    "iga_quadrature_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "iga_wq_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "iga_collocation_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "iga_get_factor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "iga_apply_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

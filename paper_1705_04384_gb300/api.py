@@ -16,6 +16,7 @@ GEOM = {"identity": 0, "annulus": 1, "revolved": 2}
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3}
 FACTOR = {"tau": 0, "M": 1, "B1": 2, "K": 3, "lambda": 4, "U": 5, "Vt": 6}
 GRID = {"latency": 0, "throughput": 1}
+SCHEME = {"collocation": 0, "wq": 1}
 STATUS_OK, STATUS_NO_CONVERGENCE, STATUS_NAN = 0, 5, 7
 
 
@@ -27,11 +28,13 @@ class Problem:
     """One collocation problem: ``iga_setup`` ... ``iga_destroy``."""
 
     def __init__(self, d, n_elem, p, geometry="annulus", r_inner=1.0, r_outer=2.0,
-                 precision="fp64", device="cuda", stream=None, grid="latency", wind=None):
+                 precision="fp64", device="cuda", stream=None, grid="latency", wind=None,
+                 scheme="collocation"):
         self.lib = _lib.load()
         self.device = torch.device(device)
         self.d, self.n_elem, self.p = d, n_elem, p
         self.precision = precision
+        self.scheme = scheme
         self.geometry = geometry
         self.r_inner, self.r_outer = r_inner, r_outer
         if stream is None:
@@ -44,9 +47,9 @@ class Problem:
                 g.wind[l] = w
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            check(self.lib.iga_setup(d, n_elem, p, ctypes.byref(g), PREC[precision],
-                                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
-                  "iga_setup")
+            check(self.lib.iga_setup_scheme(d, n_elem, p, ctypes.byref(g), SCHEME[scheme],
+                                            PREC[precision], ctypes.c_void_p(stream.cuda_stream),
+                                            ctypes.byref(h)), "iga_setup_scheme")
         self.h = h
         n = ctypes.c_int()
         N = ctypes.c_longlong()
@@ -77,6 +80,31 @@ class Problem:
         out = np.empty((self.N, self.d), dtype=np.float64)
         check(self.lib.iga_collocation_points(self.h, out.ctypes.data_as(ctypes.c_void_p)),
               "iga_collocation_points")
+        return out
+
+    def quadrature_dims(self):
+        """(nq, Nq) of a weighted-quadrature problem."""
+        nq, Nq = ctypes.c_int(), ctypes.c_longlong()
+        check(self.lib.iga_quadrature_dims(self.h, ctypes.byref(nq), ctypes.byref(Nq)),
+              "iga_quadrature_dims")
+        return nq.value, Nq.value
+
+    def quadrature_points(self):
+        """Physical WQ quadrature points, (Nq, d), direction 1 fastest."""
+        _, Nq = self.quadrature_dims()
+        out = np.empty((Nq, self.d), dtype=np.float64)
+        check(self.lib.iga_quadrature_points(self.h, out.ctypes.data_as(ctypes.c_void_p)),
+              "iga_quadrature_points")
+        return out
+
+    def wq_load(self, g, out=None):
+        """Load vector of a WQ problem from source values g at the quadrature points."""
+        _, Nq = self.quadrature_dims()
+        g = torch.as_tensor(g, dtype=torch.float64, device=self.device).contiguous()
+        if g.numel() != Nq:
+            raise ValueError(f"expected {Nq} values, got {g.numel()}")
+        out = torch.empty(self.N, dtype=torch.float64, device=self.device) if out is None else out
+        check(self.lib.iga_wq_load(self.h, _ptr(g), _ptr(out)), "iga_wq_load")
         return out
 
     def factor(self, which, direction=0):

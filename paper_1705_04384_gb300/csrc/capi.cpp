@@ -40,6 +40,11 @@ extern "C" {
 
 iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom, int precision,
                      void *stream, iga_handle *out) {
+  return iga_setup_scheme(d, n_elem, p, geom, IGA_SCHEME_COLLOCATION, precision, stream, out);
+}
+
+iga_status iga_setup_scheme(int d, int n_elem, int p, const iga_geometry *geom, int scheme,
+                            int precision, void *stream, iga_handle *out) {
   return guarded([&]() -> iga_status {
     if (!out || !geom) throw iga::Error{IGA_ERR_INVALID_ARG, "null pointer argument"};
     *out = nullptr;
@@ -49,6 +54,8 @@ iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom, int pre
       throw iga::Error{IGA_ERR_INVALID_ARG, "n_elem must be in 3..4096"};
     if (precision < IGA_PREC_FP64 || precision > IGA_PREC_NONE)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad precision"};
+    if (scheme != IGA_SCHEME_COLLOCATION && scheme != IGA_SCHEME_WQ_GALERKIN)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "bad discretization scheme"};
     if (geom->kind < IGA_GEOM_IDENTITY || geom->kind > IGA_GEOM_REVOLVED_ANNULUS)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad geometry kind"};
     if (geom->kind != IGA_GEOM_IDENTITY &&
@@ -60,9 +67,14 @@ iga_status iga_setup(int d, int n_elem, int p, const iga_geometry *geom, int pre
       if (!std::isfinite(geom->wind[l])) throw iga::Error{IGA_ERR_INVALID_ARG, "wind must be finite"};
     const double n = n_elem + p - 2;
     if (std::pow(n, d) > 2.0e9) throw iga::Error{IGA_ERR_INVALID_ARG, "problem too large"};
+    if (scheme == IGA_SCHEME_WQ_GALERKIN) {
+      // the quadrature grid has about 2 n_elem points per direction
+      const double nq = 2.0 * n_elem + 2.0 * p + 1.0;
+      if (std::pow(nq, d) > 2.0e9) throw iga::Error{IGA_ERR_INVALID_ARG, "problem too large"};
+    }
     iga_ctx *h = new iga_ctx();
     try {
-      h->c.setup(d, n_elem, p, *geom, precision, (cudaStream_t)stream);
+      h->c.setup(d, n_elem, p, *geom, precision, (cudaStream_t)stream, scheme);
     } catch (...) {
       delete h;
       throw;
@@ -89,6 +101,35 @@ iga_status iga_collocation_points(iga_handle h, double *xyz_host) {
   });
 }
 
+iga_status iga_quadrature_dims(iga_handle h, int *nq, long long *Nq) {
+  return guarded([&]() -> iga_status {
+    if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
+    if (h->c.scheme != IGA_SCHEME_WQ_GALERKIN)
+      throw iga::Error{IGA_ERR_UNSUPPORTED, "not a weighted-quadrature problem"};
+    if (nq) *nq = h->c.nq;
+    if (Nq) *Nq = h->c.Nq;
+    return IGA_OK;
+  });
+}
+
+iga_status iga_quadrature_points(iga_handle h, double *xyz_host) {
+  return guarded([&]() -> iga_status {
+    if (!h || !xyz_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    if (h->c.scheme != IGA_SCHEME_WQ_GALERKIN)
+      throw iga::Error{IGA_ERR_UNSUPPORTED, "not a weighted-quadrature problem"};
+    h->c.quadrature_points(xyz_host);
+    return IGA_OK;
+  });
+}
+
+iga_status iga_wq_load(iga_handle h, const double *g_dev, double *f_dev) {
+  return guarded([&]() -> iga_status {
+    if (!h || !g_dev || !f_dev) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
+    h->c.wq_load_vector(g_dev, f_dev, h->c.stream);
+    return IGA_OK;
+  });
+}
+
 iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host) {
   return guarded([&]() -> iga_status {
     if (!h || !out_host) throw iga::Error{IGA_ERR_INVALID_ARG, "null argument"};
@@ -102,11 +143,22 @@ iga_status iga_get_factor(iga_handle h, int dir, int which, double *out_host) {
         for (int t = 0; t < W; ++t)
           out_host[(size_t)i * n + f.start[i] + t] = sign * f.band[o][(size_t)i * W + t];
     };
+    auto gdense = [&](const std::vector<double> &band) {  // WQ Galerkin factor, banded
+      std::memset(out_host, 0, sizeof(double) * n * n);
+      for (int i = 0; i < n; ++i)
+        for (int t = 0; t < f.GW; ++t)
+          out_host[(size_t)i * n + f.gstart[i] + t] = band[(size_t)i * f.GW + t];
+    };
+    const bool wq = h->c.scheme == IGA_SCHEME_WQ_GALERKIN;
     switch (which) {
       case IGA_FACTOR_TAU: std::memcpy(out_host, f.tau.data(), sizeof(double) * n); break;
-      case IGA_FACTOR_M: dense(0, 1.0); break;
+      case IGA_FACTOR_M:
+        if (wq) gdense(f.gM); else dense(0, 1.0);
+        break;
       case IGA_FACTOR_B1: dense(1, 1.0); break;
-      case IGA_FACTOR_K: dense(2, -1.0); break;
+      case IGA_FACTOR_K:
+        if (wq) gdense(f.gK); else dense(2, -1.0);
+        break;
       case IGA_FACTOR_LAMBDA: std::memcpy(out_host, fd.lam.data(), sizeof(double) * n); break;
       case IGA_FACTOR_U: std::memcpy(out_host, fd.U.data(), sizeof(double) * n * n); break;
       case IGA_FACTOR_VT: std::memcpy(out_host, fd.Vt.data(), sizeof(double) * n * n); break;

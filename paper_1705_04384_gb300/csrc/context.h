@@ -34,6 +34,22 @@ struct OpPlan {
   ContractTerm terms[kMaxFields];
 };
 
+// One launch of the weighted-quadrature operator (kernels_wq.cu): banded products along
+// direction dir, either expansion onto the quadrature grid by the basis values /
+// derivatives (kind 0, band selector = derivative order) or contraction back to the test
+// functions by a univariate rule (kind 1, selector = 2 s + t).  Inputs and outputs are
+// scratch slots (-1: the chain's input / output vector).
+struct WqPass {
+  int dir = 0, kind = 0;
+  int ext_in[3] = {1, 1, 1}, ext_out[3] = {1, 1, 1};
+  int nterm = 0, nout = 0;
+  int in_slot[kWqMaxTerms] = {};
+  int sel[kWqMaxTerms] = {};
+  int coef[kWqMaxTerms] = {};
+  int out_of[kWqMaxTerms] = {};
+  int out_slot[kWqMaxOut] = {};
+};
+
 struct SolveGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -43,6 +59,16 @@ struct SolveGraph {
 struct Ctx {
   int d = 0, n_elem = 0, p = 0, n = 0;
   long long N = 0;
+  int scheme = 0;  // 0: collocation (Sec. 2.2), 1: weighted-quadrature Galerkin (Sec. 2.3)
+  // weighted quadrature: nq points per direction, Nq = nq^d; Q fields (+ |det J|) on that
+  // grid; the operator and load-vector pass chains and their scratch slots (per rhs)
+  int nq = 0;
+  long long Nq = 0, ldq = 0;
+  int wq_nf = 0;
+  bool wq_active[7] = {};
+  DevBuf<double> wq_fields, wq_scratch;
+  std::vector<WqPass> wq_op, wq_load;
+  std::vector<long long> wq_slot_size;
   iga_geometry geom{};
   int prec = IGA_PREC_FP64;
   cudaStream_t stream = nullptr;
@@ -106,7 +132,16 @@ struct Ctx {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
   ~Ctx();
-  void setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_);
+  void setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_,
+             int scheme_ = 0);
+  void setup_wq();
+  void setup_collocation_fields();
+  void build_wq_plan();
+  template <class Tin>
+  void run_wq(const std::vector<WqPass> &chain, IdxPtr<const Tin> in, double *out, int R,
+              cudaStream_t s);
+  void wq_load_vector(const double *g, double *f, cudaStream_t s);
+  void quadrature_points(double *xyz) const;
   void ensure_capacity(int R);
   template <class Tin>
   void apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t s);

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <memory>
 #include <mutex>
+#include <shared_mutex>
 #include <string>
 #include <vector>
 
@@ -178,6 +179,21 @@ struct Factor1D {
   DevBuf<double> d_Bf, d_Bi, d_lam_fold;
   // FD pencil (K + shift B', M): shift = w_l, the wind of the direction (Sec. 3.2)
   double shift = 0.0;
+
+  // Weighted-quadrature Galerkin data (scheme 1, Sec. 2.3).  Quadrature points xq (nq);
+  // the interior basis and its first derivative at them, banded: point q touches the
+  // interior functions qstart[q] .. qstart[q] + W - 1 (qband[b][q W + t]); the four
+  // univariate rules w^{(s,t)}, banded: test function i has weights on the points
+  // wstart[i] .. wstart[i] + WW - 1 (wband[2 s + t][i WW + u]); and the univariate
+  // Galerkin matrices M = int B_i B_j, K = int B_i' B_j' of the FD pencil, banded with
+  // width GW = 2p + 1 from column gstart[i] (eq. univariateWQ).
+  int scheme = 0;
+  int nq = 0, WW = 0, GW = 0;
+  std::vector<double> xq;
+  std::vector<int> qstart, wstart, gstart;
+  std::vector<double> qband[2], wband[4], gM, gK;
+  DevBuf<int> d_qstart, d_wstart;
+  DevBuf<double> d_qband[2], d_wband[4], d_xq;
 };
 
 struct FdScale;
@@ -188,17 +204,23 @@ template <class Tout>
 void launch_gemm_fp64_dense_mma(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
                                 int M, int n, const FdScale *scale, cudaStream_t s, int nrhs);
 
-// 1D factors of (n_elem, p) with the FD pencil (K + shift B', M), cached per device.
-std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, double shift = 0.0);
+// 1D factors of (n_elem, p) with the FD pencil (K + shift B', M), cached per device;
+// scheme 1: the weighted-quadrature Galerkin data and the Galerkin pencil (K^wq, M^wq).
+std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, double shift = 0.0,
+                                     int scheme = 0);
 void build_basis_1d(Factor1D &f);  // host part (knots, tau, bands)
+void build_wq_1d(Factor1D &f);     // host part of the WQ data (needs the knots)
+int find_span(const std::vector<double> &t, int p, int m, double x);
+void span_basis(const std::vector<double> &t, int p, int mu, double x, double out[3][kMaxBand]);
 
-// Operations that touch device-wide state -- stream capture of a solve graph, the
-// cuSOLVER eigensolves (which load library code on first use) and kernel attribute
-// changes -- are serialized by one process-wide lock, so that setups on several host
-// threads never disturb another thread's capture.  Every kernel of the library is
-// loaded once per device before the first problem is set up, so no code is loaded
-// while a capture is in progress.
-std::mutex &device_mutex();
+// Operations that touch device-wide state share one process-wide reader-writer lock, so
+// that setups on several host threads never disturb another thread's stream capture:
+// captures of solve graphs, kernel attribute changes and the tensor-core autotuner hold
+// it exclusively; the cuSOLVER eigensolves (which may load library code on first use)
+// hold it shared, so eigensolves of different shapes run concurrently but never while a
+// capture is in progress.  Every kernel of this library is loaded once per device before
+// the first problem is set up, so none of it is loaded during a capture.
+std::shared_mutex &device_mutex();
 void ensure_kernels_loaded();
 void preload_kernels_fd64();
 void preload_kernels_fd_tc();
@@ -279,6 +301,33 @@ void launch_fd_diag_inverse3(const double *lam1, const double *lam2, const doubl
 template <class Tout>
 void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out, int M, int N,
                       int K, const FdScale *scale, cudaStream_t s, int nrhs = 1);
+
+// ---------------------------------------------------------------- weighted quadrature
+// One launch of banded rectangular products along one direction (kernels_wq.cu): term t
+// reads in[t] (nullptr: the pass input vin), applies band rows start[c] .. + width - 1 of
+// the output coordinate c (values band + c * width), optionally times the pointwise
+// field coef (on the input grid), and adds into output out_of[t].
+constexpr int kWqMaxTerms = 9, kWqMaxOut = 9;
+template <class Tin> struct WqPassArgs {
+  IdxPtr<const Tin> vin;
+  const Tin *in[kWqMaxTerms];
+  const int *start[kWqMaxTerms];
+  const double *band[kWqMaxTerms];
+  const double *coef[kWqMaxTerms];
+  int width[kWqMaxTerms];
+  int out_of[kWqMaxTerms];
+  double *out[kWqMaxOut];
+  int nterm, nout;
+};
+template <class Tin>
+void launch_wq_pass(const WqPassArgs<Tin> &a, int dir, const int *ext_in, const int *ext_out,
+                    int R, cudaStream_t s);
+// Q = det(J) J^{-1} J^{-T} (eq. Q, K = I) at the tensor grid of WQ quadrature points:
+// 2D fields (11, 22, 12), 3D (11, 22, 33, 12, 13, 23), then |det J|; fields[f * ldf + i].
+void launch_wq_fields(int d, const iga_geometry &g, const double *x1, const double *x2,
+                      const double *x3, int n1, int n2, int n3, double *fields, long long ldf,
+                      cudaStream_t s);
+void preload_kernels_wq();
 
 // ---------------------------------------------------------------- Krylov kernels
 struct RhsState {

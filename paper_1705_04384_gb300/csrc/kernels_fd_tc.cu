@@ -618,7 +618,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
     for (int nt : widths) cand.push_back({nt, 1});
   std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
-    std::lock_guard<std::mutex> dlk(device_mutex());
+    std::unique_lock<std::shared_mutex> dlk(device_mutex());
     cudaEvent_t e0, e1;
     IGA_CUDA_TRY(cudaEventCreate(&e0));
     IGA_CUDA_TRY(cudaEventCreate(&e1));
@@ -736,7 +736,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
       static bool smem_set[64] = {};
       int dev = 0;
       IGA_CUDA_TRY(cudaGetDevice(&dev));
-      std::lock_guard<std::mutex> lk(device_mutex());
+      std::unique_lock<std::shared_mutex> lk(device_mutex());
       if (dev >= 0 && dev < 64 && !smem_set[dev]) {
         const int max_smem = 1024 + kStages * (kTileM * 128 + 256 * 128);
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>,

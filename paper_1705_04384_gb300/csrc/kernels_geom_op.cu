@@ -179,6 +179,64 @@ void launch_geometry_fields(int d, const iga_geometry &g, const double *tau1, co
   IGA_LAUNCH_CHECK();
 }
 
+// Weighted-quadrature Galerkin coefficients (eq. Q with K = I): Q = det(J) J^{-1} J^{-T} at
+// the tensor grid of quadrature points x1 x x2 (x x3), and |det J| for the load vector.
+__global__ void wq_fields_kernel(int d, int kind, double r0, double r1, const double *x1,
+                                 const double *x2, const double *x3, int n1, int n2, int n3,
+                                 double *fields, long long ldf) {
+  const long long N = (long long)n1 * n2 * n3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int i1 = (int)(i % n1);
+    const int i2 = (int)((i / n1) % n2);
+    const int i3 = (int)(i / ((long long)n1 * n2));
+    double xi[3] = {x1[i1], x2[i2], d == 3 ? x3[i3] : 0.0};
+    Geo3 g;
+    map_jh(kind, d, r0, r1, xi, g);
+    double Ji[3][3];
+    inv_small(d, g.J, Ji);
+    double det;
+    if (d == 2) {
+      det = g.J[0][0] * g.J[1][1] - g.J[0][1] * g.J[1][0];
+    } else {
+      det = g.J[0][0] * (g.J[1][1] * g.J[2][2] - g.J[1][2] * g.J[2][1]) -
+            g.J[0][1] * (g.J[1][0] * g.J[2][2] - g.J[1][2] * g.J[2][0]) +
+            g.J[0][2] * (g.J[1][0] * g.J[2][1] - g.J[1][1] * g.J[2][0]);
+    }
+    double Q[3][3];
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += Ji[a][k] * Ji[b][k];
+        Q[a][b] = det * s;
+      }
+    if (d == 2) {
+      fields[0 * ldf + i] = Q[0][0];
+      fields[1 * ldf + i] = Q[1][1];
+      fields[2 * ldf + i] = Q[0][1];
+      fields[3 * ldf + i] = fabs(det);
+    } else {
+      fields[0 * ldf + i] = Q[0][0];
+      fields[1 * ldf + i] = Q[1][1];
+      fields[2 * ldf + i] = Q[2][2];
+      fields[3 * ldf + i] = Q[0][1];
+      fields[4 * ldf + i] = Q[0][2];
+      fields[5 * ldf + i] = Q[1][2];
+      fields[6 * ldf + i] = fabs(det);
+    }
+  }
+}
+
+void launch_wq_fields(int d, const iga_geometry &g, const double *x1, const double *x2,
+                      const double *x3, int n1, int n2, int n3, double *fields, long long ldf,
+                      cudaStream_t s) {
+  const long long N = (long long)n1 * n2 * n3;
+  const int blocks = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
+  wq_fields_kernel<<<blocks, 256, 0, s>>>(d, g.kind, g.r_inner, g.r_outer, x1, x2, x3, n1, n2,
+                                          n3, fields, ldf);
+  IGA_LAUNCH_CHECK();
+}
+
 // ------------------------------------------------------------------ band passes
 template <class T> __device__ __forceinline__ double ld_val(const T *p) { return (double)__ldg(p); }
 
@@ -450,6 +508,7 @@ template <class Tin, int W> static void preload_op_w() {
 void preload_kernels_geom_op() {
   cudaFuncAttributes a;
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, geometry_fields_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, wq_fields_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, field_maxabs_kernel));
   preload_op_w<double, 3>();
   preload_op_w<double, 4>();

@@ -1,0 +1,96 @@
+// Matrix-free weighted-quadrature Galerkin operator (Sec. 2.3, eq. WQapprox) by sum
+// factorization:
+//   A_wq u = sum_{a,b} (W_d^{(a_d,b_d)} (x) .. (x) W_1^{(a_1,b_1)}) diag(Q_ab(x_q))
+//                      (B_d^{(b_d)} (x) .. (x) B_1^{(b_1)}) u,
+// a_l = [l == a], b_l = [l == b], Q = det(J) J^{-1} J^{-T} (eq. Q).  Every factor is a
+// banded rectangular matrix acting along one direction: the trial functions' values or
+// derivatives at the quadrature points (nq x n, expansion onto the quadrature grid) or
+// a univariate weighted-quadrature rule (n x nq, contraction back to the test
+// functions).  One launch applies several such banded products along one direction:
+// term t reads input in[t], applies the band rows of the output coordinate, optionally
+// multiplies the input by a pointwise factor first (the Q_ab field on the quadrature
+// grid, fused into the first contraction), and adds into output out_of[t].
+#include "iga_internal.h"
+
+namespace iga {
+
+template <class Tin> __device__ __forceinline__ double wq_ld(const Tin *p) {
+  return (double)__ldg(p);
+}
+
+// Output point o of one right-hand side = low + L (c + Dout high): low indexes the
+// directions faster than the pass, c the pass direction, high the slower ones; the
+// input rows of c are start[c] .. start[c] + width - 1 along the pass direction.
+template <class Tin>
+__global__ void __launch_bounds__(256)
+    wq_pass_kernel(WqPassArgs<Tin> a, unsigned Nout, unsigned L, unsigned Din, FastDiv divL,
+                   FastDiv divD, long long in_per_rhs, long long out_per_rhs) {
+  pdl_entry();
+  const int r = blockIdx.y;
+  const Tin *vin = a.vin.get();
+  for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < Nout; o += gridDim.x * blockDim.x) {
+    const unsigned rest = fdiv(o, divL), low = o - rest * L;
+    const unsigned high = fdiv(rest, divD), c = rest - high * divD.d;
+    const long long base = (long long)low + (long long)L * Din * high;
+    double acc[kWqMaxOut];
+#pragma unroll
+    for (int q = 0; q < kWqMaxOut; ++q) acc[q] = 0.0;
+#pragma unroll
+    for (int t = 0; t < kWqMaxTerms; ++t) {
+      if (t >= a.nterm) break;
+      const int st = __ldg(a.start[t] + c), w = a.width[t];
+      const double *bd = a.band[t] + (long long)c * w;
+      const Tin *src = (a.in[t] ? a.in[t] : vin) + r * in_per_rhs + base + (long long)L * st;
+      const double *cf = a.coef[t] ? a.coef[t] + base + (long long)L * st : nullptr;
+      double s = 0.0;
+      if (cf) {
+#pragma unroll 4
+        for (int u = 0; u < w; ++u)
+          s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L) * __ldg(cf + (long long)u * L), s);
+      } else {
+#pragma unroll 4
+        for (int u = 0; u < w; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
+      }
+      const int oq = a.out_of[t];
+#pragma unroll
+      for (int q = 0; q < kWqMaxOut; ++q)
+        if (q == oq) acc[q] += s;
+    }
+#pragma unroll
+    for (int q = 0; q < kWqMaxOut; ++q)
+      if (q < a.nout) a.out[q][r * out_per_rhs + o] = acc[q];
+  }
+}
+
+template <class Tin>
+void launch_wq_pass(const WqPassArgs<Tin> &a, int dir, const int *ext_in, const int *ext_out,
+                    int R, cudaStream_t s) {
+  if (a.nterm < 1 || a.nterm > kWqMaxTerms || a.nout < 1 || a.nout > kWqMaxOut)
+    throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: bad term or output count"};
+  long long L = 1, H = 1;
+  for (int l = 0; l < dir; ++l) L *= ext_in[l];
+  for (int l = dir + 1; l < 3; ++l) H *= ext_in[l];
+  const long long Din = ext_in[dir], Dout = ext_out[dir];
+  const long long Nout = L * Dout * H, Nin = L * Din * H;
+  if (Nout * R > kMaxIndex32 || Nin * R > kMaxIndex32)
+    throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per weighted-quadrature pass"};
+  const int threads = 256;
+  const int blocks = (int)std::min<long long>((Nout + threads - 1) / threads, 152LL * 16);
+  launch_pdl(kPdlOperator, wq_pass_kernel<Tin>, dim3(blocks, R), dim3(threads), 0, s, a,
+             (unsigned)Nout, (unsigned)L, (unsigned)Din, make_fastdiv((unsigned)L),
+             make_fastdiv((unsigned)Dout), Nin, Nout);
+  IGA_LAUNCH_CHECK();
+}
+
+template void launch_wq_pass<double>(const WqPassArgs<double> &, int, const int *, const int *,
+                                     int, cudaStream_t);
+template void launch_wq_pass<float>(const WqPassArgs<float> &, int, const int *, const int *, int,
+                                    cudaStream_t);
+
+void preload_kernels_wq() {
+  cudaFuncAttributes at;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&at, wq_pass_kernel<double>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&at, wq_pass_kernel<float>));
+}
+
+}  // namespace iga

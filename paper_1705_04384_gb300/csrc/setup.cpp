@@ -23,7 +23,7 @@ namespace iga {
 // ------------------------------------------------------------------ basis (host)
 // Span index mu (0-based knot index) with t[mu] <= x < t[mu+1], p <= mu <= m-1;
 // the right end x = t[m] belongs to the last span.
-static int find_span(const std::vector<double> &t, int p, int m, double x) {
+int find_span(const std::vector<double> &t, int p, int m, double x) {
   if (x >= t[m]) return m - 1;
   int lo = p, hi = m;  // invariant: t[lo] <= x < t[hi]
   while (hi - lo > 1) {
@@ -38,8 +38,8 @@ static int find_span(const std::vector<double> &t, int p, int m, double x) {
 // by the two-term recursion; derivatives of degree-p functions follow from the
 // derivative identity D B_{i,q} = q (B_{i,q-1}/(t_{i+q}-t_i) - B_{i+1,q-1}/(t_{i+q+1}-t_{i+1})),
 // applied once (D) or twice (D^2, through degree q-1 derivatives).
-static void span_basis(const std::vector<double> &t, int p, int mu, double x,
-                       double out[3][kMaxBand]) {
+void span_basis(const std::vector<double> &t, int p, int mu, double x,
+                double out[3][kMaxBand]) {
   double tab[kMaxDeg + 1][kMaxBand] = {};
   tab[0][0] = 1.0;
   for (int q = 1; q <= p; ++q) {
@@ -305,14 +305,26 @@ static void eig_all(SolverHandle &sh, const std::vector<double> &Kc, const std::
 }
 
 static void eigen_factors(Factor1D &f, cudaStream_t stream) {
-  const int n = f.n, W = f.W;
+  const int n = f.n;
+  // the FD pencil (K, M) as bands: the collocation factors of eq. (univariatecolloc)
+  // (K + shift B' for a wind, Sec. 3.2), or the WQ Galerkin factors of eq. (univariateWQ)
+  const bool gal = f.scheme == 1;
+  const int W = gal ? f.GW : f.W;
+  auto mstart = [&](int i) { return gal ? f.gstart[i] : f.start[i]; };
+  auto mval = [&](int i, int t) {
+    return gal ? f.gM[(size_t)i * W + t] : f.band[0][(size_t)i * W + t];
+  };
+  auto kval = [&](int i, int t) {
+    return gal ? f.gK[(size_t)i * W + t]
+               : -f.band[2][(size_t)i * W + t] + f.shift * f.band[1][(size_t)i * W + t];
+  };
   // dense column-major M and K
   std::vector<double> Mc((size_t)n * n, 0.0), Kc((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int t = 0; t < W; ++t) {
-      const int j = f.start[i] + t;
-      Mc[i + (size_t)n * j] = f.band[0][(size_t)i * W + t];
-      Kc[i + (size_t)n * j] = -f.band[2][(size_t)i * W + t] + f.shift * f.band[1][(size_t)i * W + t];
+      const int j = mstart(i) + t;
+      Mc[i + (size_t)n * j] = mval(i, t);
+      Kc[i + (size_t)n * j] = kval(i, t);
     }
   SolverHandle sh;
   CUSOLVER_TRY(cusolverDnCreate(&sh.h));
@@ -352,9 +364,9 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   std::vector<double> MUc((size_t)n * n, 0.0), Ic((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i)
     for (int t = 0; t < W; ++t) {
-      const double mv = f.band[0][(size_t)i * W + t];
+      const double mv = mval(i, t);
       if (mv == 0.0) continue;
-      const int k = f.start[i] + t;
+      const int k = mstart(i) + t;
       for (int j = 0; j < n; ++j) MUc[i + (size_t)n * j] += mv * f.U[(size_t)k * n + j];
     }
   for (int i = 0; i < n; ++i) Ic[i + (size_t)n * i] = 1.0;
@@ -384,8 +396,7 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   for (int i = 0; i < n; ++i)
     for (int r = 0; r < n; ++r) {
       const double a = f.Vt[(size_t)i * n + r];
-      for (int t = 0; t < W; ++t)
-        Uinv[(size_t)i * n + f.start[r] + t] += a * f.band[0][(size_t)r * W + t];
+      for (int t = 0; t < W; ++t) Uinv[(size_t)i * n + mstart(r) + t] += a * mval(r, t);
     }
   f.cond_U = norm2_est(f.U, n) * norm2_est(Uinv, n);
   if (!(f.cond_U <= 1e3))
@@ -478,13 +489,20 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
   upload(f.d_U32, u32, s);
   upload(f.d_Vt16, vt16, s);
   upload(f.d_U16, u16, s);
+  if (f.scheme == 1) {
+    upload(f.d_xq, f.xq, s);
+    upload(f.d_qstart, f.qstart, s);
+    upload(f.d_wstart, f.wstart, s);
+    for (int b = 0; b < 2; ++b) upload(f.d_qband[b], f.qband[b], s);
+    for (int k = 0; k < 4; ++k) upload(f.d_wband[k], f.wband[k], s);
+  }
   build_folded(f, s);
   IGA_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
 // ------------------------------------------------------------------ device-wide lock
-std::mutex &device_mutex() {
-  static std::mutex mu;
+std::shared_mutex &device_mutex() {
+  static std::shared_mutex mu;
   return mu;
 }
 
@@ -504,25 +522,27 @@ void ensure_kernels_loaded() {
   static bool loaded[64] = {};
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(device_mutex());
+  std::unique_lock<std::shared_mutex> lk(device_mutex());
   if (dev < 0 || dev >= 64 || loaded[dev]) return;
   preload_kernels_fd64();
   preload_kernels_fd_tc();
   preload_kernels_geom_op();
   preload_kernels_krylov();
   preload_kernels_bicgstab();
+  preload_kernels_wq();
   loaded[dev] = true;
 }
 
 // ------------------------------------------------------------------ factor cache
-std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, double shift) {
+std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, double shift,
+                                     int scheme) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, long long>, std::weak_ptr<Factor1D>> cache;
+  static std::map<std::tuple<int, int, int, long long, int>, std::weak_ptr<Factor1D>> cache;
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
   long long sbits = 0;
   std::memcpy(&sbits, &shift, sizeof(sbits));
-  const auto key = std::make_tuple(dev, n_elem, p, sbits);
+  const auto key = std::make_tuple(dev, n_elem, p, sbits, scheme);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -536,9 +556,11 @@ std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, dou
   f->n_elem = n_elem;
   f->p = p;
   f->shift = shift;
+  f->scheme = scheme;
   build_basis_1d(*f);
+  if (scheme == 1) build_wq_1d(*f);
   {
-    std::lock_guard<std::mutex> dlk(device_mutex());
+    std::shared_lock<std::shared_mutex> dlk(device_mutex());
     eigen_factors(*f, stream);
   }
   upload_factor(*f, stream);

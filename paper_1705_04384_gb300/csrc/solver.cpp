@@ -44,17 +44,21 @@ void Ctx::drop_graphs() {
 }
 
 // ------------------------------------------------------------------ setup
-void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_) {
+void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, cudaStream_t s_,
+                int scheme_) {
   d = d_;
   n_elem = n_elem_;
   p = p_;
   geom = g_;
   prec = prec_;
   stream = s_;
+  scheme = scheme_;
   ensure_kernels_loaded();
-  fac = get_factor(n_elem, p, stream);
   bool has_wind = false;
   for (int l = 0; l < d; ++l) has_wind = has_wind || geom.wind[l] != 0.0;
+  if (has_wind && scheme == 1)
+    throw Error{IGA_ERR_INVALID_ARG, "the weighted-quadrature scheme takes no wind"};
+  fac = get_factor(n_elem, p, stream, 0.0, scheme);
   if (has_wind && (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16))
     throw Error{IGA_ERR_INVALID_ARG, "a wind requires precision FP64 or NONE"};
   // per-direction FD factors: the pencil (K + w_l B', M) of Sec. 3.2 (w_l = 0: Poisson)
@@ -72,6 +76,30 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   IGA_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
   IGA_CUDA_TRY(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
 
+  if (scheme == 1) {
+    setup_wq();
+  } else {
+    setup_collocation_fields();
+  }
+  if (prec == IGA_PREC_FP64) {
+    // the FP64 chain uses the folded eigen-order when one factor set with parity serves
+    // every direction, else each direction's own eigenvalues
+    dinv.alloc(N);
+    if (fold_ok)
+      launch_fd_diag_inverse(fac->d_lam_fold.ptr, n, d, dinv.ptr, nullptr, stream);
+    else
+      launch_fd_diag_inverse3(facd[0]->d_lam.ptr, facd[1]->d_lam.ptr, facd[2]->d_lam.ptr, n, d,
+                              dinv.ptr, nullptr, stream);
+  } else if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) {
+    dinv32.alloc(N);
+    launch_fd_diag_inverse(fac->d_lam.ptr, n, d, nullptr, dinv32.ptr, stream);
+  }
+  ensure_capacity(1);
+  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+}
+
+// Geometry coefficient fields of the collocation operator and its pass plan.
+void Ctx::setup_collocation_fields() {
   // geometry coefficient fields at the collocation points
   const int nf = num_fields(d);
   ldf = (N + 31) / 32 * 32;
@@ -128,21 +156,6 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
     }
     plan.terms[plan.nterm++] = ContractTerm{input, fd.order[0], fields.ptr + active[a] * ldf};
   }
-  if (prec == IGA_PREC_FP64) {
-    // the FP64 chain uses the folded eigen-order when one factor set with parity serves
-    // every direction, else each direction's own eigenvalues
-    dinv.alloc(N);
-    if (fold_ok)
-      launch_fd_diag_inverse(fac->d_lam_fold.ptr, n, d, dinv.ptr, nullptr, stream);
-    else
-      launch_fd_diag_inverse3(facd[0]->d_lam.ptr, facd[1]->d_lam.ptr, facd[2]->d_lam.ptr, n, d,
-                              dinv.ptr, nullptr, stream);
-  } else if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) {
-    dinv32.alloc(N);
-    launch_fd_diag_inverse(fac->d_lam.ptr, n, d, nullptr, dinv32.ptr, stream);
-  }
-  ensure_capacity(1);
-  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
 }
 
 // Buffers whose size scales with the number of right-hand sides.
@@ -153,7 +166,13 @@ void Ctx::ensure_capacity(int R) {
   ws_max_iter = 0;  // the Krylov workspaces are rebuilt for the new capacity
   ws_R = 0;
   bicg_max_iter = 0;
-  op_scratch.alloc((size_t)(plan.nA + plan.nB) * R * N);
+  if (scheme == 1) {
+    long long per = 0;
+    for (long long sz : wq_slot_size) per += sz;
+    wq_scratch.alloc((size_t)per * R);
+  } else {
+    op_scratch.alloc((size_t)(plan.nA + plan.nB) * R * N);
+  }
   fd_scratch.alloc(2 * (size_t)R * N);
   b.alloc((size_t)R * N);
   x.alloc((size_t)R * N);
@@ -171,6 +190,10 @@ void Ctx::ensure_capacity(int R) {
 // ------------------------------------------------------------------ operator
 template <class Tin>
 void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t s) {
+  if (scheme == 1) {  // weighted-quadrature Galerkin, eq. (WQapprox)
+    run_wq<Tin>(wq_op, in, out, R, s);
+    return;
+  }
   double *TA[3], *TB[6];
   const size_t blk = (size_t)R * N;
   for (int q = 0; q < plan.nA; ++q) TA[q] = op_scratch.ptr + q * blk;
@@ -386,7 +409,7 @@ SolveGraph &Ctx::graph_for(int R, int use_x0) {
   const auto key = std::make_pair(R, use_x0);
   auto it = graphs.find(key);
   if (it != graphs.end()) return it->second;
-  std::lock_guard<std::mutex> dlk(device_mutex());
+  std::unique_lock<std::shared_mutex> dlk(device_mutex());
   ws.R = R;
   SolveGraph sg;
   cudaStream_t s = cap_stream;
@@ -531,6 +554,9 @@ iga_status Ctx::collect(int *iters, double *hist_out, double *relres, int *statu
 
 // ------------------------------------------------------------------ points (host)
 void Ctx::collocation_points(double *xyz) const {
+  if (scheme != 0)
+    throw Error{IGA_ERR_UNSUPPORTED, "collocation points of a weighted-quadrature problem: use "
+                                     "iga_quadrature_points"};
   const std::vector<double> &tau = fac->tau;
   const double r0 = geom.r_inner, r1 = geom.r_outer, w_ = 0.5 * M_PI;
   const long long n3 = d == 3 ? n : 1;

@@ -11,10 +11,12 @@ Problem handles are pooled by shape: a handle keeps its 1D factors, geometry
 fields, Krylov workspace and captured CUDA graph resident, so a later request of the
 same shape skips setup.  A shape seen for the first time is set up on a host worker
 thread (eigen-factors, fields, workspace, graph capture) while the loop keeps
-serving other requests; admission of new handles is bounded by a device-memory
-budget, and idle handles are evicted least-recently-used when a new shape does not
-fit.  Every kernel reduces in a fixed order, so a request's result does not depend
-on what else is in flight.
+serving other requests; several shapes set up at once (their eigensolves run
+concurrently on the device).  A waiting request whose shape already has an idle
+handle is admitted ahead of older requests that still wait for a setup.  Admission of
+new handles is bounded by a device-memory budget, and idle handles are evicted
+least-recently-used when a new shape does not fit.  Every kernel reduces in a fixed
+order, so a request's result does not depend on what else is in flight.
 """
 
 import collections
@@ -69,7 +71,7 @@ class Server:
 
     def __init__(self, precision="tf32", tol=1e-8, max_iter=100, max_inflight=32,
                  mem_budget=None, keep_solutions=False, device="cuda", setup_threads=4,
-                 lookahead=64, max_per_key=4, grid="throughput"):
+                 lookahead=4096, max_per_key=4, grid="throughput"):
         self.max_per_key = max_per_key
         self.grid = grid  # many solves run at once: few reduction blocks per solve
         self.precision, self.tol, self.max_iter = precision, tol, max_iter
@@ -86,6 +88,8 @@ class Server:
         self.reserved = 0
         self.setups = 0
         self.setup_s = 0.0
+        self.setup_threads = setup_threads
+        self.dropped = 0
         self.executor = ThreadPoolExecutor(max_workers=setup_threads)
 
     # ---------------------------------------------------------------- pool
@@ -119,22 +123,27 @@ class Server:
                 self.setup_s += dt
                 self.pool[key].append(slot)
 
-    def _slot_for(self, req):
-        """An idle handle of the request's shape, or None (a setup may be started)."""
-        for s in self.pool.get(req.key, []):
-            if not s.busy:
-                return s
-        if req.key in self.setting_up or len(self.pool.get(req.key, [])) >= self.max_per_key:
-            return None  # wait for a handle of this shape
+    def _needs_setup(self, key):
+        """True if a new handle of this shape should be set up now: none is being set up,
+        every existing one is busy, and the per-shape limit allows another."""
+        if key in self.setting_up:
+            return False
+        slots = self.pool.get(key, [])
+        return len(slots) < self.max_per_key and all(s.busy for s in slots)
+
+    def _start_setup(self, req):
+        """Reserve memory (evicting idle handles least recently used first) and submit the
+        setup of a handle of the request's shape; False if it does not fit now."""
         N = (req.n_elem + req.p - 2) ** req.d
         need = handle_bytes(req.d, N, self.max_iter, self.precision)
         if need > self.mem_budget:
             raise RuntimeError(f"request {req.rid} needs {need} bytes, above the budget")
-        if self._evict_until(need):
-            self.reserved += need
-            self.setups += 1
-            self.setting_up[req.key] = (self.executor.submit(self._setup, req.key, need), need)
-        return None
+        if not self._evict_until(need):
+            return False
+        self.reserved += need
+        self.setups += 1
+        self.setting_up[req.key] = (self.executor.submit(self._setup, req.key, need), need)
+        return True
 
     # ---------------------------------------------------------------- request life
     def _start(self, s, req, now):
@@ -166,23 +175,36 @@ class Server:
     def run(self, requests, realtime=True, time_limit=None):
         """Serve ``requests`` (t_arrival in seconds from the start).  With ``realtime``
         a request becomes visible at its arrival time; otherwise all are queued at
-        once.  Stops admitting at ``time_limit`` (then drains).  Returns the completed
-        requests."""
+        once.  Admission: a waiting request whose shape has an idle handle starts at once
+        (oldest first, up to ``max_inflight`` solves in flight); shapes without a free
+        handle get one set up on the worker threads, oldest waiting request first, at
+        most ``setup_threads`` setups at a time.  At ``time_limit`` no new request is
+        admitted: waiting ones are dropped (counted in ``self.dropped``) and the solves in
+        flight drain.  Returns the completed requests."""
         pending = collections.deque(sorted(requests, key=lambda r: r.t_arrival))
-        queue = []
+        waiting = {}                   # shape -> deque of requests, arrival order
+        order = collections.deque()    # every waiting request, arrival order (lazily pruned)
+        nwait = 0
         inflight = []
         done = []
+        self.dropped = 0
         t0 = time.perf_counter()
-        while pending or queue or inflight or self.setting_up:
+        while pending or nwait or inflight or self.setting_up:
             now = time.perf_counter()
             rel = now - t0
-            if time_limit is not None and rel > time_limit:
+            closed = time_limit is not None and rel > time_limit
+            if closed and (pending or nwait):
+                self.dropped += len(pending) + nwait
                 pending.clear()
-                queue.clear()
+                waiting.clear()
+                order.clear()
+                nwait = 0
             while pending and (not realtime or pending[0].t_arrival <= rel):
                 r = pending.popleft()
                 r.t_arrival = t0 + (r.t_arrival if realtime else 0.0)
-                queue.append(r)
+                waiting.setdefault(r.key, collections.deque()).append(r)
+                order.append(r)
+                nwait += 1
             still = []
             for s in inflight:
                 if s.P.ready():
@@ -193,16 +215,37 @@ class Server:
                     still.append(s)
             inflight = still
             self._harvest_setups()
-            i = 0
-            while i < len(queue) and i < self.lookahead and len(inflight) < self.max_inflight:
-                s = self._slot_for(queue[i])
-                if s is None:
-                    i += 1
-                    continue
-                req = queue.pop(i)
-                self._start(s, req, time.perf_counter())
-                inflight.append(s)
-            if not queue and not pending and not inflight and not self.setting_up:
+            # warm shapes: the oldest waiting request of every shape with an idle handle
+            cands = []
+            for key, dq in waiting.items():
+                if dq and any(not s.busy for s in self.pool.get(key, [])):
+                    cands.append((dq[0].t_arrival, dq[0].rid, key))
+            cands.sort()
+            for _, _, key in cands:
+                for s in self.pool[key]:
+                    if len(inflight) >= self.max_inflight or not waiting[key]:
+                        break
+                    if s.busy:
+                        continue
+                    req = waiting[key].popleft()
+                    nwait -= 1
+                    self._start(s, req, time.perf_counter())
+                    inflight.append(s)
+                if not waiting[key]:
+                    del waiting[key]
+            # cold shapes: set up handles for the oldest waiting requests that need one
+            while order and order[0].t_admit is not None:
+                order.popleft()
+            if not closed and len(self.setting_up) < self.setup_threads:
+                scanned = 0
+                for r in order:
+                    if len(self.setting_up) >= self.setup_threads or scanned >= self.lookahead:
+                        break
+                    scanned += 1
+                    if r.t_admit is None and self._needs_setup(r.key):
+                        if not self._start_setup(r):
+                            break
+            if not pending and not nwait and not inflight and not self.setting_up:
                 break
             time.sleep(0)
         return done

@@ -155,3 +155,46 @@ def test_bicgstab_iterations_flat_as_in_table3():
     for (ne, p), it in counts.items():
         if (ne, p) in paper:
             assert abs(it - paper[(ne, p)]) <= 1.0, (ne, p, it)
+
+
+@pytest.mark.parametrize("kind,d", [("annulus", 2), ("revolved", 3), ("identity", 3)])
+def test_matrix_free_wq_operator_equals_assembled(kind, d):
+    spaces = [Q.WQSpace1D(4 + l, 2 + l) for l in range(d)]
+    fmap = Geo.make_map(kind, d, 1.0, 2.0)
+    A = Q.assemble_wq(spaces, fmap)
+    op = Q.WQOperator(spaces, fmap)
+    u = np.random.default_rng(1).standard_normal(A.shape[0])
+    assert np.max(np.abs(op(u) - A @ u)) <= 1e-13 * np.max(np.abs(A @ u))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_wq_load_of_a_constant_is_exact(d):
+    """The (0, 0) rule is exact against the spline space, which contains the constants:
+    with |det J| g constant the load vector is g |det J| int B_I (int B_I = (t_{I+p+1} -
+    t_I) / (p + 1)), and it matches the Gauss-quadrature Galerkin load."""
+    A = np.diag([1.5, 0.75, 2.0][:d])
+    fmap = Affine(A)
+    spaces = [Q.WQSpace1D(5 + l, 3) for l in range(d)]
+    g = np.full(int(np.prod([s.nq for s in spaces])), 2.0)
+    f = Q.wq_load(spaces, fmap, g)
+    ints = []
+    for s in spaces:
+        ints.append(np.array([(s.t[j + s.p + 1] - s.t[j]) / (s.p + 1)
+                              for j in range(1, s.m - 1)]))
+    ref = ints[-1]
+    for v in reversed(ints[:-1]):
+        ref = np.kron(ref, v)
+    ref = 2.0 * abs(np.linalg.det(A)) * ref
+    assert np.max(np.abs(f - ref)) <= 1e-13 * np.max(np.abs(ref))
+    fg = Q.galerkin_rhs(spaces, fmap, lambda x: np.full(x.shape[0], 2.0))
+    assert np.max(np.abs(f - fg)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_quadrature_points_follow_the_map():
+    spaces = [Q.WQSpace1D(4, 2), Q.WQSpace1D(6, 3)]
+    fmap = Geo.make_map("annulus", 2, 1.0, 2.0)
+    X = Q.quadrature_points_physical(spaces, fmap)
+    xi = np.array([spaces[0].xq[1], spaces[1].xq[2]])
+    i = 1 + spaces[0].nq * 2
+    assert np.allclose(X[i], fmap.F(xi), rtol=0, atol=1e-15)
+    assert X.shape == (spaces[0].nq * spaces[1].nq, 2)
