@@ -384,10 +384,13 @@ def run_ours(args):
             by_p[str(q["p"])] = {"p50_ms": percentile(ms, 50), "p99_ms": percentile(ms, 99),
                                  "setup_ms": 1e3 * q["setup_s"],
                                  "tts_with_setup_ms": 1e3 * (q["setup_s"] + q["first_s"])}
+        p50 = percentile(solve_ms, 50)
         return {"value": units / tt, "unit": UNIT,
                 "iters": {str(s[0]): s[2] for s in res[-1]},
                 "relres_true": {str(s[0]): s[4] for s in res[-1]},
-                "p50_ms": percentile(solve_ms, 50), "p99_ms": percentile(solve_ms, 99),
+                "p50_ms": p50, "p99_ms": percentile(solve_ms, 99), "max_ms": max(solve_ms),
+                "solves": len(solve_ms),
+                "solves_over_1p5x_p50": sum(1 for t in solve_ms if t > 1.5 * p50),
                 "tts_warm_ms_per_step": 1e3 * tt / len(res), "by_p": by_p,
                 "_units": units, "_t": tt}
 

@@ -9,6 +9,7 @@
 // applied mode by mode (sum factorization); the contraction with the fields is pointwise.
 #include <cmath>
 
+#include "fp_widen.h"
 #include "iga_internal.h"
 
 namespace iga {
@@ -239,6 +240,10 @@ void launch_wq_fields(int d, const iga_geometry &g, const double *x1, const doub
 
 // ------------------------------------------------------------------ band passes
 template <class T> __device__ __forceinline__ double ld_val(const T *p) { return (double)__ldg(p); }
+// FP32 inputs (the precision form's vectors) are widened on the integer units (fp_widen.h)
+template <> __device__ __forceinline__ double ld_val<float>(const float *p) {
+  return widen_f32(__ldg(p));
+}
 
 // out[o][i] = sum_t band_{order[o]}[c * W + t] * in[i + (start[c] + t - c) * stride],
 // c = coordinate of i along dir.  One thread per output point; 32-bit indices

@@ -223,9 +223,15 @@ void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
 }
 
 // ------------------------------------------------------------------ CGS2
-// Dots of vectors V_r[j0 .. j0+cnt) with u over this block's rows, two rows per step
-// so that the loads of both are in flight together; block-reduced into partials.  Index
-// jself (if in range) stands for u itself: its dot is ||u||^2 over the rows.
+// The passes are bound by the FP64 unit (one FMA per vector entry read, against an FP64
+// rate of about 0.5 FMA per clock per SM sub-partition), with the memory traffic close
+// behind: every warp must keep loads in flight while its FMAs issue.  The loops below
+// therefore load the next step's operands before they issue the current step's FMAs.
+
+// Dots of vectors V_r[j0 .. j0+cnt) with u over this block's rows, one row per thread
+// and step, the next step's entries loaded before this step's FMAs (rows past the
+// block's end read as zero, which adds exact zeros); block-reduced into partials.
+// Index jself (if in range) stands for u itself: its dot is ||u||^2 over the rows.
 __device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, int cnt,
                                            const double *__restrict__ u, long long lo,
                                            long long hi, double *part, double (*red)[kJC],
@@ -237,78 +243,133 @@ __device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, in
     vb[q] = j == jself ? u : Vvec(ws, j, r);
   }
   double acc[kJC] = {};
+  double u0, a0[kJC];
+  auto load = [&](long long i, double &x, double (&b)[kJC]) {
+    const bool ok = i < hi;
+    x = ok ? u[i] : 0.0;
+#pragma unroll
+    for (int q = 0; q < kJC; ++q)
+      if (q < cnt) b[q] = ok ? vb[q][i] : 0.0;
+  };
   long long i = lo + threadIdx.x;
-  for (; i + kRT < hi; i += 2 * kRT) {
-    const double u0 = u[i], u1 = u[i + kRT];
-    double a0[kJC], a1[kJC];
+  load(i, u0, a0);
+  for (; i < hi; i += kRT) {
+    double nu, n0[kJC];
+    load(i + kRT, nu, n0);
 #pragma unroll
     for (int q = 0; q < kJC; ++q)
-      if (q < cnt) {
-        a0[q] = vb[q][i];
-        a1[q] = vb[q][i + kRT];
-      }
+      if (q < cnt) acc[q] = fma(a0[q], u0, acc[q]);
+    u0 = nu;
 #pragma unroll
-    for (int q = 0; q < kJC; ++q)
-      if (q < cnt) acc[q] = fma(a1[q], u1, fma(a0[q], u0, acc[q]));
-  }
-  if (i < hi) {
-    const double u0 = u[i];
-#pragma unroll
-    for (int q = 0; q < kJC; ++q)
-      if (q < cnt) acc[q] = fma(vb[q][i], u0, acc[q]);
+    for (int q = 0; q < kJC; ++q) a0[q] = n0[q];
   }
   block_store_partials(acc, cnt, j0, part, gridDim.x, red);
 }
 
-// dst[i] = (u_r[i] - sum_j V_r[j][i] h[j]) (* scale with kScale) for this block's rows,
-// two rows per step with two partial sums each (independent FMA chains).  dst may be u.
+// (V_r h)[i] and (V_r h)[i + kRT] for one row pair (rows past hi read as zero): kPG
+// vectors per group, the next group's entries loaded before this group's FMAs, kPG
+// independent FMA chains per row.  h is in shared memory.
+constexpr int kPG = 3;
+__device__ __forceinline__ void proj_rows(const KrylovWs &ws, int r, int nv,
+                                          const double *__restrict__ hs, long long i,
+                                          long long hi, double &p0, double &p1) {
+  const bool v0 = i < hi, v1 = i + kRT < hi;
+  double s0[kPG] = {}, s1[kPG] = {}, c0[kPG], c1[kPG];
+  auto load = [&](int j, double (&b0)[kPG], double (&b1)[kPG]) {
+#pragma unroll
+    for (int q = 0; q < kPG; ++q) {
+      const bool ok = j + q < nv;
+      const double *v = Vvec(ws, ok ? j + q : 0, r);
+      b0[q] = (ok && v0) ? v[i] : 0.0;
+      b1[q] = (ok && v1) ? v[i + kRT] : 0.0;
+    }
+  };
+  load(0, c0, c1);
+  for (int j = 0; j < nv; j += kPG) {
+    double n0[kPG], n1[kPG];
+    load(j + kPG, n0, n1);
+#pragma unroll
+    for (int q = 0; q < kPG; ++q) {
+      const double h = j + q < nv ? hs[j + q] : 0.0;
+      s0[q] = fma(c0[q], h, s0[q]);
+      s1[q] = fma(c1[q], h, s1[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kPG; ++q) {
+      c0[q] = n0[q];
+      c1[q] = n1[q];
+    }
+  }
+  p0 = s0[0];
+  p1 = s1[0];
+#pragma unroll
+  for (int q = 1; q < kPG; ++q) {
+    p0 += s0[q];
+    p1 += s1[q];
+  }
+}
+
+// dst[i] = (u_r[i] - sum_j V_r[j][i] h[j]) (* scale with kScale) for this block's rows.
+// dst may be u.  hs: the nv coefficients in shared memory.
 template <bool kScale = false>
 __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
-                                              const double *__restrict__ h, const double *u,
+                                              const double *__restrict__ hs, const double *u,
                                               long long lo, long long hi, double *dst,
                                               double scale = 1.0) {
-  long long i = lo + threadIdx.x;
-  for (; i + kRT < hi; i += 2 * kRT) {
-    double s0a = 0.0, s0b = 0.0, s1a = 0.0, s1b = 0.0;
-    int j = 0;
-    for (; j + 1 < nv; j += 2) {
-      const double h0 = __ldg(h + j), h1 = __ldg(h + j + 1);
-      const double *v0 = Vvec(ws, j, r), *v1 = Vvec(ws, j + 1, r);
-      s0a = fma(v0[i], h0, s0a);
-      s1a = fma(v0[i + kRT], h0, s1a);
-      s0b = fma(v1[i], h1, s0b);
-      s1b = fma(v1[i + kRT], h1, s1b);
-    }
-    if (j < nv) {
-      const double hj = __ldg(h + j);
-      const double *v0 = Vvec(ws, j, r);
-      s0a = fma(v0[i], hj, s0a);
-      s1a = fma(v0[i + kRT], hj, s1a);
-    }
-    double x0 = u[i] - (s0a + s0b), x1 = u[i + kRT] - (s1a + s1b);
-    if (kScale) {
-      x0 *= scale;
-      x1 *= scale;
-    }
-    dst[i] = x0;
-    dst[i + kRT] = x1;
-  }
-  if (i < hi) {
-    double sa = 0.0, sb = 0.0;
-    int j = 0;
-    for (; j + 1 < nv; j += 2) {
-      sa = fma(Vvec(ws, j, r)[i], __ldg(h + j), sa);
-      sb = fma(Vvec(ws, j + 1, r)[i], __ldg(h + j + 1), sb);
-    }
-    if (j < nv) sa = fma(Vvec(ws, j, r)[i], __ldg(h + j), sa);
-    double x0 = u[i] - (sa + sb);
+  for (long long i = lo + threadIdx.x; i < hi; i += 2 * kRT) {
+    double p0, p1;
+    proj_rows(ws, r, nv, hs, i, hi, p0, p1);
+    double x0 = u[i] - p0;
     if (kScale) x0 *= scale;
     dst[i] = x0;
+    if (i + kRT < hi) {
+      double x1 = u[i + kRT] - p1;
+      if (kScale) x1 *= scale;
+      dst[i + kRT] = x1;
+    }
+  }
+}
+
+// Pass 2 for nv + 1 <= NACC accumulators, reading V_r from memory once: per row pair,
+// w' = w - V_r h1 (proj_rows), then the dots of V_r and w' with w' (the row pair's V
+// entries were just read: cache hits), accumulated in registers over the block's rows.
+template <int NACC>
+__device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r, int nv,
+                                            const double *__restrict__ hs, double *w,
+                                            long long lo, long long hi, double *part,
+                                            double (*red)[kJC]) {
+  double acc[NACC] = {};
+  for (long long i = lo + threadIdx.x; i < hi; i += 2 * kRT) {
+    double p0, p1;
+    proj_rows(ws, r, nv, hs, i, hi, p0, p1);
+    const bool v1 = i + kRT < hi;
+    const double x0 = w[i] - p0;
+    const double x1 = v1 ? w[i + kRT] - p1 : 0.0;
+    w[i] = x0;
+    if (v1) w[i + kRT] = x1;
+#pragma unroll
+    for (int j = 0; j < NACC; ++j) {
+      if (j < nv) {
+        const double *v = Vvec(ws, j, r);
+        const double b0 = v[i], b1 = v1 ? v[i + kRT] : 0.0;
+        acc[j] = fma(b1, x1, fma(b0, x0, acc[j]));
+      } else if (j == nv) {
+        acc[j] = fma(x1, x1, fma(x0, x0, acc[j]));
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NACC / kJC; ++c) {
+    if (c * kJC > nv) break;
+    double a[kJC];
+#pragma unroll
+    for (int q = 0; q < kJC; ++q) a[q] = acc[c * kJC + q];
+    block_store_partials(a, min(kJC, nv + 1 - c * kJC), c * kJC, part, gridDim.x, red);
   }
 }
 
 // pass 1: h1 = V_r^T w_r -> H_r[0..k, k]
-__global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const double *__restrict__ w) {
+__global__ void __launch_bounds__(kRT, 2) cgs_pass1_kernel(KrylovWs ws, const double *__restrict__ w) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
   const int k = ws.st->k, nv = k + 1;
@@ -332,9 +393,10 @@ __global__ void __launch_bounds__(kRT) cgs_pass1_kernel(KrylovWs ws, const doubl
 // that pass 3 needs no reduction of its own.  After the first projection w_r is
 // orthogonal to V_r to working accuracy, ||h2|| <= ||w_r|| times a small multiple of the
 // unit roundoff, and the difference loses no significant digits.
-__global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w) {
+__global__ void __launch_bounds__(kRT, 2) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
+  extern __shared__ double hs[];  // max_iter + 1 coefficients
   const int k = ws.st->k, nv = k + 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) ws.st->kv = k;
   long long lo, hi;
@@ -344,9 +406,18 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
     double *wr = w + (long long)r * ws.N;
     const double *h1 = Hcol(ws, r, k);
     double *part = ws.partials + r * ws.pstride;
-    subtract_proj(ws, r, nv, h1, wr, lo, hi, wr);
-    for (int j0 = 0; j0 <= nv; j0 += kJC)
-      chunk_dots(ws, r, j0, min(kJC, nv + 1 - j0), wr, lo, hi, part, red, nv);
+    __syncthreads();  // hs of the previous right-hand side is no longer read
+    for (int j = threadIdx.x; j < nv; j += kRT) hs[j] = h1[j];
+    __syncthreads();
+    if (nv + 1 <= 8) {
+      pass2_fused<8>(ws, r, nv, hs, wr, lo, hi, part, red);
+    } else if (nv + 1 <= 16) {
+      pass2_fused<16>(ws, r, nv, hs, wr, lo, hi, part, red);
+    } else {
+      subtract_proj(ws, r, nv, hs, wr, lo, hi, wr);
+      for (int j0 = 0; j0 <= nv; j0 += kJC)
+        chunk_dots(ws, r, j0, min(kJC, nv + 1 - j0), wr, lo, hi, part, red, nv);
+    }
     if (!arrive_last(ws.counter + r)) continue;
     double *y = ws.y + r * (ws.max_iter + 2);
     last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, y);
@@ -372,8 +443,9 @@ __global__ void __launch_bounds__(kRT) cgs_pass2_kernel(KrylovWs ws, double *__r
 // Givens kernel of the same step, which advances k, sets the done flags and rotates H:
 // the step comes from kv and the norm from its copy in scal.  A right-hand side that the
 // Givens kernel has just retired may or may not get its v_{k+1}; it is never read.
-__global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, const double *__restrict__ w) {
+__global__ void __launch_bounds__(kRT, 2) cgs_pass3_kernel(KrylovWs ws, const double *__restrict__ w) {
   pdl_entry();
+  extern __shared__ double hs[];  // max_iter + 1 coefficients
   const int k = ws.st->kv, nv = k + 1;
   long long lo, hi;
   row_range(ws.N, lo, hi);
@@ -381,10 +453,13 @@ __global__ void __launch_bounds__(kRT) cgs_pass3_kernel(KrylovWs ws, const doubl
     if (ws.rs[r].done) continue;
     const double *wr = w + (long long)r * ws.N;
     const double *h2 = ws.y + r * (ws.max_iter + 2);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nv; j += kRT) hs[j] = h2[j];
+    __syncthreads();
     const double hn = ws.scal[8 * r + 4];
     const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
     double *v = ws.V + ((long long)(k + 1) * ws.R + r) * ws.N;
-    subtract_proj<true>(ws, r, nv, h2, wr, lo, hi, v, inv);
+    subtract_proj<true>(ws, r, nv, hs, wr, lo, hi, v, inv);
   }
 }
 
@@ -392,12 +467,14 @@ void launch_cgs2_coeffs(const KrylovWs &ws, double *w, cudaStream_t s) {
   const dim3 grid(ws.nblk);
   launch_pdl(kPdlKrylov, cgs_pass1_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
-  launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), 0, s, ws, w);
+  launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), (ws.max_iter + 1) * sizeof(double), s,
+             ws, w);
   IGA_LAUNCH_CHECK();
 }
 
 void launch_cgs2_vector(const KrylovWs &ws, const double *w, cudaStream_t s) {
-  launch_pdl(kPdlKrylov, cgs_pass3_kernel, dim3(ws.nblk), dim3(kRT), 0, s, ws, w);
+  launch_pdl(kPdlKrylov, cgs_pass3_kernel, dim3(ws.nblk), dim3(kRT),
+             (ws.max_iter + 1) * sizeof(double), s, ws, w);
   IGA_LAUNCH_CHECK();
 }
 

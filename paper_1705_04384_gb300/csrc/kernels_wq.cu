@@ -10,12 +10,17 @@
 // term t reads input in[t], applies the band rows of the output coordinate, optionally
 // multiplies the input by a pointwise factor first (the Q_ab field on the quadrature
 // grid, fused into the first contraction), and adds into output out_of[t].
+#include "fp_widen.h"
 #include "iga_internal.h"
 
 namespace iga {
 
 template <class Tin> __device__ __forceinline__ double wq_ld(const Tin *p) {
   return (double)__ldg(p);
+}
+// FP32 inputs are widened on the integer units (fp_widen.h)
+template <> __device__ __forceinline__ double wq_ld<float>(const float *p) {
+  return widen_f32(__ldg(p));
 }
 
 // Output point o of one right-hand side = low + L (c + Dout high): low indexes the
