@@ -55,6 +55,10 @@ TEXTS = {
     "3d_wind_ne64": "3d_wind_ne64: convection-diffusion -Lap + w.grad (Sec. 3.2) with w = (5,5,5) "
                     "on the 3D extruded quarter annulus, 64 elements/dir, p=3,4,5, f = 1 + seeded "
                     "1e-3 perturbation, FD of the wind-shifted pencils, FP64 FD-GMRES to 1e-8",
+    "3d_wq_revolved_ne64": "3d_wq_revolved_ne64: weighted-quadrature Galerkin (Sec. 2.3) on the 3D "
+                           "quarter ring revolved by pi/2 (Sec. 5), 64 elements/dir, p=3,4,5, WQ "
+                           "load of f = 1 + seeded 1e-3 perturbation, FD of the Galerkin pencils "
+                           "(P_wq), FD-GMRES to 1e-8 in FP64 (value), TF32 and BF16",
 }
 CONFIG = {"workload": TEXTS[WORKLOAD],
           "step": "one solve per p (setup cached); per form",
@@ -81,8 +85,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-form key of the default line")
     ap.add_argument("--workload", default="3d_ne128",
-                    choices=["3d_ne128", "3d_ne64", "3d_revolved_ne64", "3d_wind_ne64", "batched",
-                             "served"],
+                    choices=["3d_ne128", "3d_ne64", "3d_revolved_ne64", "3d_wind_ne64",
+                             "3d_wq_revolved_ne64", "batched", "served"],
                     help="3d_ne128 (default bench line), 3d_ne64 (config 2), 3d_revolved_ne64 "
                          "(Sec. 5's revolved ring), 3d_wind_ne64 (Sec. 3.2 convection-diffusion), "
                          "batched (256 2D problems x 8 rhs), served (Poisson request stream)")
@@ -235,9 +239,18 @@ def operator_flops_per_dof(W_band, d=3):
 def oracle_problem(name, p):
     """The oracle's view of one problem of a named 3D workload: spaces, matrix-free A_C
     (the definition of eq. collocation applied through the Kronecker identity: the CSR
-    matrix of config 3 has about 8e8 non-zeros), the FD preconditioner and the rhs."""
+    matrix of config 3 has about 8e8 non-zeros), the FD preconditioner and the rhs; for the
+    WQ workload the matrix-free A_wq (eq. WQapprox), the FD of P_wq and the WQ load."""
     from oracle import collocation as C, fd as F, geometry as Geo
     c = W.CONFIGS[name]
+    if c.get("scheme") == "wq":
+        from oracle import wq as Q
+        spaces = [Q.WQSpace1D(c["n_elem"], p) for _ in range(c["d"])]
+        fmap = Geo.make_map(geometry_of(c), c["d"], c["r0"], c["r1"])
+        nq = int(np.prod([s.nq for s in spaces]))
+        f = Q.wq_load(spaces, fmap, np.ones(nq))
+        b = W.perturb(f, c["sigma"], c["seed"] + c["ps"].index(p))
+        return Q.WQOperator(spaces, fmap), F.FD(spaces), b
     spaces = [C.Space1D(c["n_elem"], p) for _ in range(c["d"])]
     fmap = Geo.make_map(geometry_of(c), c["d"], c["r0"], c["r1"])
     A = C.CollocationOperator(spaces, fmap, c.get("wind"))
@@ -315,6 +328,7 @@ def run_ours(args):
 
     c = W.CONFIGS[WORKLOAD]
     d = c["d"]
+    oracle_p = ORACLE_P if ORACLE_P in c["ps"] else c["ps"][0]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     peaks = measured_peaks()
@@ -333,12 +347,18 @@ def run_ours(args):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             P = Problem(d, c["n_elem"], p, geometry_of(c), c["r0"], c["r1"], precision=prec,
-                        wind=c.get("wind"), device=dev, stream=stream)
+                        wind=c.get("wind"), device=dev, stream=stream,
+                        scheme=c.get("scheme", "collocation"))
             P.prepare(1, MAX_ITER)
             torch.cuda.synchronize(dev)
             t_setup = time.perf_counter() - t0
-            pts = P.collocation_points()
-            rhs = torch.from_numpy(W.config_rhs(WORKLOAD, pts, i)).to(dev)
+            if c.get("scheme") == "wq":
+                _, Nq = P.quadrature_dims()
+                f = P.wq_load(torch.ones(Nq, dtype=torch.float64, device=dev)).cpu().numpy()
+                rhs = torch.from_numpy(W.perturb(f, c["sigma"], c["seed"] + i)).to(dev)
+            else:
+                pts = P.collocation_points()
+                rhs = torch.from_numpy(W.config_rhs(WORKLOAD, pts, i)).to(dev)
             x = torch.empty_like(rhs)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -435,7 +455,7 @@ def run_ours(args):
     main = out["fp64"]
 
     # dominant kernels, timed live on the bench stream (the p = ORACLE_P problem, n = 130)
-    q4 = {f: next(q for q in probs[f] if q["p"] == ORACLE_P) for f in forms}
+    q4 = {f: next(q for q in probs[f] if q["p"] == oracle_p) for f in forms}
     P4 = q4["fp64"]["P"]
     n4, N4 = P4.n, P4.N
     buf = torch.empty_like(q4["fp64"]["rhs"])
@@ -454,12 +474,16 @@ def run_ours(args):
                      f"{fp64['fma']:.0f} GFLOP/s; the larger is the peak)"}
     # operator (FP64 unit), the same in every form
     t_op = time_calls(lambda: P4.apply_operator(q4["fp64"]["rhs"], out=buf), 10)
-    opf = operator_flops_per_dof(P4.p + 1, d) * N4
-    main["roofline_operator"] = {
-        "bound": "alu", "achieved": opf / t_op / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
-        "frac": opf / t_op / 1e9 / fp64_peak, "kernel": "band_pass + band_pass_multi + "
-        "contract_pass (one operator application, 3 launches)", "per_apply_us": t_op * 1e6,
-        "flops_per_apply": opf}
+    if c.get("scheme") == "wq" or geometry_of(c) != "annulus" or c.get("wind"):
+        main["roofline_operator"] = {"per_apply_us": t_op * 1e6,
+                                     "note": "FLOP count given for the extruded annulus only"}
+    else:
+        opf = operator_flops_per_dof(P4.p + 1, d) * N4
+        main["roofline_operator"] = {
+            "bound": "alu", "achieved": opf / t_op / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+            "frac": opf / t_op / 1e9 / fp64_peak, "kernel": "band_pass + band_pass_multi + "
+            "contract_pass (one operator application, 3 launches)", "per_apply_us": t_op * 1e6,
+            "flops_per_apply": opf}
     # precision forms: one FD apply (pack + 2d tensor-core mode products), graded against
     # the fused three-pass HBM floor of the FD (3 x 8 bytes per DOF)
     for f in forms[1:]:
@@ -539,10 +563,10 @@ def run_ours(args):
     cpu = None
     oracle_err = None
     if world == 1 and not args.no_cpu_baseline:
-        o = oracle_solve(WORKLOAD, ORACLE_P)
+        o = oracle_solve(WORKLOAD, oracle_p)
         cpu = {"value": o["N"] * o["iters"] / o["seconds"], "unit": UNIT,
                "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one full oracle GMRES+FD solve to 1e-8 of the p={ORACLE_P} problem of "
+               "sample": f"one full oracle GMRES+FD solve to 1e-8 of the p={oracle_p} problem of "
                          f"{WORKLOAD} (N={o['N']}, {o['iters']} iterations, {o['seconds']:.1f} s); "
                          f"matrix-free A_C (eq. collocation via the Kronecker identity), FD of eq. "
                          f"FD3D, modified Gram-Schmidt; iteration phase only; numpy/OpenBLAS "
@@ -550,11 +574,11 @@ def run_ours(args):
                "busy_cores": o["cpu_seconds"] / o["seconds"]}
         xo = o["x"]
         nx = float(np.linalg.norm(xo))
-        oracle_err = {"p": ORACLE_P, "oracle_iters": o["iters"],
+        oracle_err = {"p": oracle_p, "oracle_iters": o["iters"],
                       "oracle_relres_true": o["relres_true"]}
         for f in forms:
             e = float(np.linalg.norm(x4[f] - xo) / nx)
-            out[f]["rel_err_vs_oracle"] = {str(ORACLE_P): e}
+            out[f]["rel_err_vs_oracle"] = {str(oracle_p): e}
             oracle_err[f] = e
     for f in forms:
         out[f].pop("_units", None)
@@ -800,7 +824,8 @@ def main():
     args = parse()
     global WORKLOAD
     named = {"3d_ne128": "3d_annulus_ne128", "3d_ne64": "3d_annulus_ne64",
-             "3d_revolved_ne64": "3d_revolved_ne64", "3d_wind_ne64": "3d_wind_ne64"}
+             "3d_revolved_ne64": "3d_revolved_ne64", "3d_wind_ne64": "3d_wind_ne64",
+             "3d_wq_revolved_ne64": "3d_wq_revolved_ne64"}
     if args.workload in named:
         WORKLOAD = named[args.workload]
         CONFIG["workload"] = TEXTS[WORKLOAD]

@@ -237,11 +237,14 @@ def quadrature_points_physical(spaces, fmap):
 
 def wq_load(spaces, fmap, g):
     """The WQ load vector (Sec. 2.3, the right-hand side 'by using again the WQ approach'):
-    f_I = sum_q w^{00}_{I q} |det J(x_q)| g_q for source values g at the quadrature points."""
+    f_I = sum_q w^{00}_{I q} |det J(x_q)| g_q for source values g at the quadrature points,
+    the tensor-product rule applied mode by mode (the Kronecker identity)."""
+    from .fd import kron_apply
     pts = tensor_points([s.xq for s in spaces])
     detJ = np.abs(np.linalg.det(np.moveaxis(fmap.J(pts.T), -1, 0)))
-    Wk = kron_list([s.W[(0, 0)] for s in spaces])
-    return Wk @ (detJ * np.asarray(g, dtype=np.float64))
+    shape_q = tuple(s.nq for s in spaces)[::-1]
+    return kron_apply([s.W[(0, 0)] for s in spaces], detJ * np.asarray(g, dtype=np.float64),
+                      shape_q)
 
 
 class WQOperator:

@@ -314,9 +314,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 //                     it, commits each ring stage back to the producer and the finished
 //                     accumulator to the epilogue;
 //   warps 2..5        epilogue; warp w may access TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31.
-// Selected per shape by the autotuner, and only with IGA_TC_PERSISTENT=1 until it has
-// been checked against the one-tile kernel on a GB300.  Its barrier protocol (ring
-// phases, accumulator hand-over) is simulated on the host in
+// Selected per shape by the autotuner (see persistent_candidate); checked against the
+// oracle on a GB300 with IGA_TC_PERSISTENT=2 (tests/test_gpu_mixed.py), and its barrier
+// protocol (ring phases, accumulator hand-over) is simulated on the host in
 // tests/test_tc_persistent_protocol.py.
 constexpr int kTcpThreads = 192;
 constexpr int kTcpMaxStages = 8;
@@ -574,13 +574,21 @@ static void set_tile(TcFd &t, int n_tile, int persistent = 0) {
   }
 }
 
-// IGA_TC_PERSISTENT: unset or 0, one-tile kernel only; 1, the autotuner also times the
-// persistent kernel; 2, the persistent kernel only (to check it against the oracle).
+// Which kernels the autotuner times.  Measured on GB300 (2D n = 1025, TF32, fastest tile of
+// each): with one right-hand side the one-tile kernel is faster (85.5 against 118.7 us per
+// FD apply: 45 tiles leave no second tile per CTA to overlap), with eight the persistent
+// kernel is (287 against 311 us).  IGA_TC_PERSISTENT unset: the persistent kernel is a
+// candidate for problems set up for at least 4 right-hand sides; 0: never; 1: always;
+// 2: the only candidate (to check it against the oracle).
 static int persistent_mode() {
   const char *e = std::getenv("IGA_TC_PERSISTENT");
-  return (e && (e[0] == '1' || e[0] == '2')) ? e[0] - '0' : 0;
+  if (!e || !e[0]) return -1;
+  return (e[0] == '1' || e[0] == '2') ? e[0] - '0' : 0;
 }
-static bool persistent_enabled() { return persistent_mode() != 0; }
+static bool persistent_candidate(int R_max) {
+  const int m = persistent_mode();
+  return m > 0 || (m < 0 && R_max >= 4);
+}
 
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
 // candidate column tile -- the whole padded width, or 2, 3, 4 ... narrower tiles that
@@ -614,7 +622,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
   std::vector<std::pair<int, int>> cand;
   if (persistent_mode() != 2)
     for (int nt : widths) cand.push_back({nt, 0});
-  if (persistent_enabled())
+  if (persistent_candidate(t.R_max))
     for (int nt : widths) cand.push_back({nt, 1});
   std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
@@ -743,7 +751,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-        if (persistent_enabled()) {
+        {
           const int max_smem_p = (int)(1024 + kTcpRingBytes);
           IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_persistent_kernel<0>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -878,10 +886,8 @@ void preload_kernels_fd_tc() {
   cudaFuncAttributes a;
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<0>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<1>));
-  if (persistent_enabled()) {
-    IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<0>));
-    IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<1>));
-  }
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<0>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<1>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<float>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<__nv_bfloat16>));
 }

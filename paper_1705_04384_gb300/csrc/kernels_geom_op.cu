@@ -248,10 +248,12 @@ template <> __device__ __forceinline__ double ld_val<float>(const float *p) {
 // out[o][i] = sum_t band_{order[o]}[c * W + t] * in[i + (start[c] + t - c) * stride],
 // c = coordinate of i along dir.  One thread per output point; 32-bit indices
 // (N < 2^31): c = (i / divA) mod divB by multiply-shift division, divA = 1, n1 or n1 n2.
-template <class Tin, int W>
+// NOUT (1..3) is a template argument: a predicated-off FP64 FMA still takes an issue
+// slot on GB300's narrow FP64 unit, so no output's FMAs are issued when it does not exist.
+template <class Tin, int W, int NOUT>
 __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, double *out0,
                                                         double *out1, double *out2, int ord0,
-                                                        int ord1, int ord2, int nout, int dir,
+                                                        int ord1, int ord2, int dir,
                                                         unsigned N, int stride, FastDiv divA,
                                                         FastDiv divB, BandDev b) {
   pdl_entry();
@@ -270,12 +272,12 @@ __global__ void __launch_bounds__(256) band_pass_kernel(IdxPtr<const Tin> inp, d
 #pragma unroll
     for (int t = 0; t < W; ++t) a0 = fma(__ldg(B0 + c * W + t), v[t], a0);
     out0[i] = a0;
-    if (nout > 1) {
+    if constexpr (NOUT > 1) {
 #pragma unroll
       for (int t = 0; t < W; ++t) a1 = fma(__ldg(B1 + c * W + t), v[t], a1);
       out1[i] = a1;
     }
-    if (nout > 2) {
+    if constexpr (NOUT > 2) {
 #pragma unroll
       for (int t = 0; t < W; ++t) a2 = fma(__ldg(B2 + c * W + t), v[t], a2);
       out2[i] = a2;
@@ -293,6 +295,7 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
                       int nrhs) {
   const long long N = (long long)n1 * n2 * n3 * nrhs;
   if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per operator pass"};
+  if (nout < 1 || nout > 3) throw Error{IGA_ERR_INVALID_ARG, "band pass: 1..3 outputs"};
   const int threads = 256, blocks = grid_for(N, threads);
   double *o0 = outs[0], *o1 = nout > 1 ? outs[1] : nullptr, *o2 = nout > 2 ? outs[2] : nullptr;
   const int r0 = orders[0], r1 = nout > 1 ? orders[1] : 0, r2 = nout > 2 ? orders[2] : 0;
@@ -300,10 +303,14 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
   // c = (i / divA) mod divB: dir 0: i mod n1; dir 1: (i / n1) mod n2; dir 2: (i / n1 n2) mod n3
   const FastDiv divA = make_fastdiv(dir == 2 ? (unsigned)(n1 * n2) : (unsigned)n1);
   const FastDiv divB = make_fastdiv(dir == 0 ? (unsigned)n1 : (dir == 1 ? (unsigned)n2 : (unsigned)n3));
-#define IGA_BAND_CASE(WW)                                                                     \
-  case WW:                                                                                    \
-    launch_pdl(kPdlOperator, band_pass_kernel<Tin, WW>, dim3(blocks), dim3(threads), 0, s, in, \
-               o0, o1, o2, r0, r1, r2, nout, dir, (unsigned)N, stride, divA, divB, b);        \
+#define IGA_BAND_LAUNCH(WW, NO)                                                                \
+  launch_pdl(kPdlOperator, band_pass_kernel<Tin, WW, NO>, dim3(blocks), dim3(threads), 0, s, in, \
+             o0, o1, o2, r0, r1, r2, dir, (unsigned)N, stride, divA, divB, b)
+#define IGA_BAND_CASE(WW)                                     \
+  case WW:                                                    \
+    if (nout == 1) IGA_BAND_LAUNCH(WW, 1);                    \
+    else if (nout == 2) IGA_BAND_LAUNCH(WW, 2);               \
+    else IGA_BAND_LAUNCH(WW, 3);                              \
     break;
   switch (b.W) {
     IGA_BAND_CASE(3)
@@ -315,6 +322,7 @@ void launch_band_pass(IdxPtr<const Tin> in, double *const *outs, const int *orde
       throw Error{IGA_ERR_INVALID_ARG, "band width out of range"};
   }
 #undef IGA_BAND_CASE
+#undef IGA_BAND_LAUNCH
   IGA_LAUNCH_CHECK();
 }
 
@@ -505,7 +513,9 @@ void launch_field_maxabs(const double *fields, long long ldf, long long N, int n
 
 template <class Tin, int W> static void preload_op_w() {
   cudaFuncAttributes a;
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_kernel<Tin, W>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_kernel<Tin, W, 1>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_kernel<Tin, W, 2>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_kernel<Tin, W, 3>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, contract_pass_kernel<Tin, W>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, band_pass_multi_kernel<W>));
 }

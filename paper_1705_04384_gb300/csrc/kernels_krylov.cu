@@ -228,71 +228,105 @@ void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
 // behind: every warp must keep loads in flight while its FMAs issue.  The loops below
 // therefore load the next step's operands before they issue the current step's FMAs.
 
-// Dots of vectors V_r[j0 .. j0+cnt) with u over this block's rows, one row per thread
-// and step, the next step's entries loaded before this step's FMAs (rows past the
-// block's end read as zero, which adds exact zeros); block-reduced into partials.
-// Index jself (if in range) stands for u itself: its dot is ||u||^2 over the rows.
-__device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, int cnt,
-                                           const double *__restrict__ u, long long lo,
-                                           long long hi, double *part, double (*red)[kJC],
-                                           int jself = -1) {
-  const double *vb[kJC];
+// Exact counts.  A predicated-off FP64 instruction still takes its issue slot on GB300's
+// narrow FP64 unit (ncu: the passes ran the unit 85-88 % busy while doing 72-78 % useful
+// FMAs), so every loop over a runtime count of vectors or outputs is compiled for its exact
+// count (a template argument, chosen by a warp-uniform switch) instead of a fixed maximum
+// with a predicate.
+
+// Dots of vectors V_r[j0 .. j0+CNT) with u over this block's rows, one row per thread and
+// step, the next step's entries loaded before this step's FMAs (rows past the block's end
+// read as zero, which adds exact zeros); block-reduced into partials.  Index jself (if in
+// range) stands for u itself: its dot is ||u||^2 over the rows.
+template <int CNT>
+__device__ __forceinline__ void chunk_dots_n(const KrylovWs &ws, int r, int j0,
+                                             const double *__restrict__ u, long long lo,
+                                             long long hi, double *part, double (*red)[kJC],
+                                             int jself) {
+  const double *vb[CNT];
 #pragma unroll
-  for (int q = 0; q < kJC; ++q) {
-    const int j = j0 + min(q, cnt - 1);
+  for (int q = 0; q < CNT; ++q) {
+    const int j = j0 + q;
     vb[q] = j == jself ? u : Vvec(ws, j, r);
   }
   double acc[kJC] = {};
-  double u0, a0[kJC];
-  auto load = [&](long long i, double &x, double (&b)[kJC]) {
+  double u0, a0[CNT];
+  auto load = [&](long long i, double &x, double (&b)[CNT]) {
     const bool ok = i < hi;
     x = ok ? u[i] : 0.0;
 #pragma unroll
-    for (int q = 0; q < kJC; ++q)
-      if (q < cnt) b[q] = ok ? vb[q][i] : 0.0;
+    for (int q = 0; q < CNT; ++q) b[q] = ok ? vb[q][i] : 0.0;
   };
   long long i = lo + threadIdx.x;
   load(i, u0, a0);
   for (; i < hi; i += kRT) {
-    double nu, n0[kJC];
+    double nu, n0[CNT];
     load(i + kRT, nu, n0);
 #pragma unroll
-    for (int q = 0; q < kJC; ++q)
-      if (q < cnt) acc[q] = fma(a0[q], u0, acc[q]);
+    for (int q = 0; q < CNT; ++q) acc[q] = fma(a0[q], u0, acc[q]);
     u0 = nu;
 #pragma unroll
-    for (int q = 0; q < kJC; ++q) a0[q] = n0[q];
+    for (int q = 0; q < CNT; ++q) a0[q] = n0[q];
   }
-  block_store_partials(acc, cnt, j0, part, gridDim.x, red);
+  block_store_partials(acc, CNT, j0, part, gridDim.x, red);
+}
+
+__device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, int cnt,
+                                           const double *__restrict__ u, long long lo,
+                                           long long hi, double *part, double (*red)[kJC],
+                                           int jself = -1) {
+  switch (cnt) {
+    case 1: chunk_dots_n<1>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    case 2: chunk_dots_n<2>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    case 3: chunk_dots_n<3>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    case 4: chunk_dots_n<4>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    case 5: chunk_dots_n<5>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    case 6: chunk_dots_n<6>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    case 7: chunk_dots_n<7>(ws, r, j0, u, lo, hi, part, red, jself); break;
+    default: chunk_dots_n<8>(ws, r, j0, u, lo, hi, part, red, jself); break;
+  }
 }
 
 // (V_r h)[i] and (V_r h)[i + kRT] for one row pair (rows past hi read as zero): kPG
 // vectors per group, the next group's entries loaded before this group's FMAs, kPG
-// independent FMA chains per row.  h is in shared memory.
+// independent FMA chains per row; the last nv mod kPG vectors follow with their exact count.
+// h is in shared memory.
 constexpr int kPG = 3;
+template <int G>
+__device__ __forceinline__ void proj_group(const KrylovWs &ws, int r, int j,
+                                           const double *__restrict__ hs, long long i, bool v0,
+                                           bool v1, double (&s0)[kPG], double (&s1)[kPG]) {
+#pragma unroll
+  for (int q = 0; q < G; ++q) {
+    const double *v = Vvec(ws, j + q, r);
+    const double b0 = v0 ? v[i] : 0.0, b1 = v1 ? v[i + kRT] : 0.0;
+    s0[q] = fma(b0, hs[j + q], s0[q]);
+    s1[q] = fma(b1, hs[j + q], s1[q]);
+  }
+}
+
 __device__ __forceinline__ void proj_rows(const KrylovWs &ws, int r, int nv,
                                           const double *__restrict__ hs, long long i,
                                           long long hi, double &p0, double &p1) {
   const bool v0 = i < hi, v1 = i + kRT < hi;
   double s0[kPG] = {}, s1[kPG] = {}, c0[kPG], c1[kPG];
+  const int full = nv - nv % kPG;
   auto load = [&](int j, double (&b0)[kPG], double (&b1)[kPG]) {
 #pragma unroll
     for (int q = 0; q < kPG; ++q) {
-      const bool ok = j + q < nv;
-      const double *v = Vvec(ws, ok ? j + q : 0, r);
-      b0[q] = (ok && v0) ? v[i] : 0.0;
-      b1[q] = (ok && v1) ? v[i + kRT] : 0.0;
+      const double *v = Vvec(ws, j + q, r);
+      b0[q] = v0 ? v[i] : 0.0;
+      b1[q] = v1 ? v[i + kRT] : 0.0;
     }
   };
-  load(0, c0, c1);
-  for (int j = 0; j < nv; j += kPG) {
+  if (full > 0) load(0, c0, c1);
+  for (int j = 0; j < full; j += kPG) {
     double n0[kPG], n1[kPG];
-    load(j + kPG, n0, n1);
+    if (j + kPG < full) load(j + kPG, n0, n1);
 #pragma unroll
     for (int q = 0; q < kPG; ++q) {
-      const double h = j + q < nv ? hs[j + q] : 0.0;
-      s0[q] = fma(c0[q], h, s0[q]);
-      s1[q] = fma(c1[q], h, s1[q]);
+      s0[q] = fma(c0[q], hs[j + q], s0[q]);
+      s1[q] = fma(c1[q], hs[j + q], s1[q]);
     }
 #pragma unroll
     for (int q = 0; q < kPG; ++q) {
@@ -300,13 +334,10 @@ __device__ __forceinline__ void proj_rows(const KrylovWs &ws, int r, int nv,
       c1[q] = n1[q];
     }
   }
-  p0 = s0[0];
-  p1 = s1[0];
-#pragma unroll
-  for (int q = 1; q < kPG; ++q) {
-    p0 += s0[q];
-    p1 += s1[q];
-  }
+  if (nv - full == 1) proj_group<1>(ws, r, full, hs, i, v0, v1, s0, s1);
+  else if (nv - full == 2) proj_group<2>(ws, r, full, hs, i, v0, v1, s0, s1);
+  p0 = (s0[0] + s0[1]) + s0[2];
+  p1 = (s1[0] + s1[1]) + s1[2];
 }
 
 // dst[i] = (u_r[i] - sum_j V_r[j][i] h[j]) (* scale with kScale) for this block's rows.
@@ -330,41 +361,52 @@ __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
   }
 }
 
-// Pass 2 for nv + 1 <= NACC accumulators, reading V_r from memory once: per row pair,
-// w' = w - V_r h1 (proj_rows), then the dots of V_r and w' with w' (the row pair's V
-// entries were just read: cache hits), accumulated in registers over the block's rows.
-template <int NACC>
-__device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r, int nv,
+// (V_r h)[i] for one row (zero past hi), as proj_rows for a single row.
+__device__ __forceinline__ double proj_row(const KrylovWs &ws, int r, int nv,
+                                           const double *__restrict__ hs, long long i, bool ok) {
+  double s[kPG] = {}, c[kPG];
+  const int full = nv - nv % kPG;
+  auto load = [&](int j, double (&b)[kPG]) {
+#pragma unroll
+    for (int q = 0; q < kPG; ++q) b[q] = ok ? Vvec(ws, j + q, r)[i] : 0.0;
+  };
+  if (full > 0) load(0, c);
+  for (int j = 0; j < full; j += kPG) {
+    double n[kPG];
+    if (j + kPG < full) load(j + kPG, n);
+#pragma unroll
+    for (int q = 0; q < kPG; ++q) s[q] = fma(c[q], hs[j + q], s[q]);
+#pragma unroll
+    for (int q = 0; q < kPG; ++q) c[q] = n[q];
+  }
+  if (nv - full >= 1) s[0] = fma(ok ? Vvec(ws, full, r)[i] : 0.0, hs[full], s[0]);
+  if (nv - full >= 2) s[1] = fma(ok ? Vvec(ws, full + 1, r)[i] : 0.0, hs[full + 1], s[1]);
+  return (s[0] + s[1]) + s[2];
+}
+
+// Pass 2 for NV = nv <= 15 vectors, reading V_r from memory once: per row, w' = w - V_r h1
+// (proj_row), then the dots of V_r and w' with w' (the row's V entries were just read:
+// cache hits), NV + 1 accumulators in registers over the block's rows.
+template <int NV>
+__device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r,
                                             const double *__restrict__ hs, double *w,
                                             long long lo, long long hi, double *part,
                                             double (*red)[kJC]) {
-  double acc[NACC] = {};
-  for (long long i = lo + threadIdx.x; i < hi; i += 2 * kRT) {
-    double p0, p1;
-    proj_rows(ws, r, nv, hs, i, hi, p0, p1);
-    const bool v1 = i + kRT < hi;
-    const double x0 = w[i] - p0;
-    const double x1 = v1 ? w[i + kRT] - p1 : 0.0;
-    w[i] = x0;
-    if (v1) w[i + kRT] = x1;
+  constexpr int NA = (NV + 1 + kJC - 1) / kJC * kJC;
+  double acc[NA] = {};
+  for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
+    const double x = w[i] - proj_row(ws, r, NV, hs, i, true);
+    w[i] = x;
 #pragma unroll
-    for (int j = 0; j < NACC; ++j) {
-      if (j < nv) {
-        const double *v = Vvec(ws, j, r);
-        const double b0 = v[i], b1 = v1 ? v[i + kRT] : 0.0;
-        acc[j] = fma(b1, x1, fma(b0, x0, acc[j]));
-      } else if (j == nv) {
-        acc[j] = fma(x1, x1, fma(x0, x0, acc[j]));
-      }
-    }
+    for (int j = 0; j < NV; ++j) acc[j] = fma(Vvec(ws, j, r)[i], x, acc[j]);
+    acc[NV] = fma(x, x, acc[NV]);
   }
 #pragma unroll
-  for (int c = 0; c < NACC / kJC; ++c) {
-    if (c * kJC > nv) break;
+  for (int c = 0; c < NA / kJC; ++c) {
     double a[kJC];
 #pragma unroll
     for (int q = 0; q < kJC; ++q) a[q] = acc[c * kJC + q];
-    block_store_partials(a, min(kJC, nv + 1 - c * kJC), c * kJC, part, gridDim.x, red);
+    block_store_partials(a, min(kJC, NV + 1 - c * kJC), c * kJC, part, gridDim.x, red);
   }
 }
 
@@ -409,15 +451,16 @@ __global__ void __launch_bounds__(kRT, 2) cgs_pass2_kernel(KrylovWs ws, double *
     __syncthreads();  // hs of the previous right-hand side is no longer read
     for (int j = threadIdx.x; j < nv; j += kRT) hs[j] = h1[j];
     __syncthreads();
-    if (nv + 1 <= 8) {
-      pass2_fused<8>(ws, r, nv, hs, wr, lo, hi, part, red);
-    } else if (nv + 1 <= 16) {
-      pass2_fused<16>(ws, r, nv, hs, wr, lo, hi, part, red);
-    } else {
-      subtract_proj(ws, r, nv, hs, wr, lo, hi, wr);
-      for (int j0 = 0; j0 <= nv; j0 += kJC)
-        chunk_dots(ws, r, j0, min(kJC, nv + 1 - j0), wr, lo, hi, part, red, nv);
+#define IGA_P2(NVV) \
+  case NVV: pass2_fused<NVV>(ws, r, hs, wr, lo, hi, part, red); break;
+    switch (nv) {
+      IGA_P2(1) IGA_P2(2) IGA_P2(3) IGA_P2(4) IGA_P2(5) IGA_P2(6) IGA_P2(7) IGA_P2(8) IGA_P2(9) IGA_P2(10) IGA_P2(11) IGA_P2(12) IGA_P2(13) IGA_P2(14) IGA_P2(15)
+      default:
+        subtract_proj(ws, r, nv, hs, wr, lo, hi, wr);
+        for (int j0 = 0; j0 <= nv; j0 += kJC)
+          chunk_dots(ws, r, j0, min(kJC, nv + 1 - j0), wr, lo, hi, part, red, nv);
     }
+#undef IGA_P2
     if (!arrive_last(ws.counter + r)) continue;
     double *y = ws.y + r * (ws.max_iter + 2);
     last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, y);

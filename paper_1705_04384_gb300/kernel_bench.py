@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--max-iter", type=int, default=200,
+                    help="Krylov workspace of --op solve (steps)")
     a = ap.parse_args()
     if a.op == "fp64peak":
         # the FP64 ceiling (iga_fp64_probe): best of a.reps timed launches per probe kind
@@ -46,7 +48,7 @@ def main():
         elif a.op == "operator":
             P.apply_operator(b, out=out)
         else:
-            P.solve(b, tol=1e-8, max_iter=200, out=out)
+            P.solve(b, tol=1e-8, max_iter=a.max_iter, out=out)
 
     for _ in range(a.warmup):
         call()

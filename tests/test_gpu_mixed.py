@@ -122,3 +122,42 @@ def test_device_error_word_reports_timeout_and_handle_stays_usable():
         x1, i1 = P.solve(b, tol=1e-8, max_iter=100)
         assert i1["status"] == 0 and i1["iters"] == i0["iters"]
         assert torch.equal(x1, x0)
+
+
+PERSISTENT_CHECK = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1705_04384_gb300.api import Problem
+from tests.oracle_ref import ref
+worst = 0.0
+for prec, tol in (("tf32", 1e-2), ("bf16", 6e-2)):
+    for d, ne, p, R in ((2, 40, 3, 1), (2, 95, 5, 4), (3, 9, 3, 1), (3, 20, 4, 3)):
+        Rf = ref(d, ne, p, assemble=False)
+        with Problem(d, ne, p, precision=prec) as P:
+            P.prepare(R, 10)
+            g = np.random.default_rng(ne)
+            for _ in range(2):
+                b = g.standard_normal(P.N)
+                s = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+                want = Rf.fd(b)
+                e = np.linalg.norm(s - want) / np.linalg.norm(want)
+                assert e <= tol, (prec, d, ne, p, R, e)
+                worst = max(worst, e / tol)
+print("ok", worst)
+"""
+
+
+def test_persistent_tensor_core_kernel_matches_oracle(tmp_path):
+    """The persistent (tile-loop) tensor-core mode product, forced as the only autotuner
+    candidate (IGA_TC_PERSISTENT=2, read once per process, hence a child process), against
+    the oracle's FD at the tolerances above, with 1 and several right-hand sides."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "persistent.py"
+    script.write_text(PERSISTENT_CHECK)
+    env = dict(os.environ, IGA_TC_PERSISTENT="2", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr

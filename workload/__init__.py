@@ -36,6 +36,11 @@ CONFIGS = {
     # a constant wind (5, 5, 5); f = 1 with the same perturbation
     "3d_wind_ne64": dict(d=3, n_elem=64, ps=[3, 4, 5], r0=1.0, r1=2.0,
                          wind=(5.0, 5.0, 5.0), rhs="constant", sigma=1e-3, seed=0),
+    # Sec. 2.3's weighted-quadrature Galerkin discretization on Sec. 5's revolved ring (the
+    # setting of the paper's WQ tables); f = 1, its WQ load vector perturbed as above
+    "3d_wq_revolved_ne64": dict(d=3, n_elem=64, ps=[3, 4, 5], r0=1.0, r1=2.0,
+                                geometry="revolved", scheme="wq", rhs="wq_constant",
+                                sigma=1e-3, seed=0),
 }
 
 
