@@ -534,6 +534,10 @@ def run_ours(args):
         out[f]["speedup_vs_fp64_tts_warm"] = (main["tts_warm_ms_per_step"] /
                                               out[f]["tts_warm_ms_per_step"])
 
+    # the GMRES solutions of the p = oracle_p problems, before the BiCGStab line reuses the
+    # FP64 problems' solution buffers
+    x4 = {f: q4[f]["x"].double().cpu().numpy() for f in forms}
+
     # Sec. 5's solver on the same problems: BiCGStab + FP64 FD, counted in halves
     bicg_out = None
     if not args.no_bicgstab:
@@ -543,7 +547,6 @@ def run_ours(args):
                     "iters": bs["iters"], "relres_true": bs["relres_true"],
                     "p50_ms": bs["p50_ms"], "tts_warm_ms_per_step": bs["tts_warm_ms_per_step"]}
 
-    x4 = {f: q4[f]["x"].double().cpu().numpy() for f in forms}
     for f in forms:
         for q in probs[f]:
             q["P"].close()

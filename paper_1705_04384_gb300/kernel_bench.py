@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--max-iter", type=int, default=200,
                     help="Krylov workspace of --op solve (steps)")
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="right-hand sides of --op solve (solved in lockstep, iga_solve_multi)")
     a = ap.parse_args()
     if a.op == "fp64peak":
         # the FP64 ceiling (iga_fp64_probe): best of a.reps timed launches per probe kind
@@ -40,6 +42,9 @@ def main():
     g = torch.Generator(device="cpu").manual_seed(0)
     b = torch.randn(P.N, dtype=torch.float64, generator=g).cuda()
     out = torch.empty_like(b)
+    if a.op == "solve" and a.nrhs > 1:
+        P.prepare(a.nrhs, a.max_iter)
+        B = torch.randn(a.nrhs, P.N, dtype=torch.float64, generator=g).cuda()
     s = torch.cuda.current_stream()
 
     def call():
@@ -47,6 +52,8 @@ def main():
             P.precond_apply(b, out=out)
         elif a.op == "operator":
             P.apply_operator(b, out=out)
+        elif a.nrhs > 1:
+            P.solve_multi(B, tol=1e-8, max_iter=a.max_iter)
         else:
             P.solve(b, tol=1e-8, max_iter=a.max_iter, out=out)
 
@@ -62,6 +69,7 @@ def main():
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e3)
     print(json.dumps({"op": a.op, "d": a.d, "ne": a.ne, "p": a.p, "n": P.n, "N": P.N,
+                      "nrhs": a.nrhs,
                       "precision": a.precision, "us_mean": float(np.mean(times)),
                       "us_min": float(np.min(times)), "reps": a.reps}))
     P.close()
