@@ -462,11 +462,18 @@ def run_ours(args):
     # FP64 form: the folded FD mode product (6 launches per FD apply)
     t_launch = time_calls(lambda: P4.precond_apply(q4["fp64"]["rhs"], out=buf), 10) / (2 * d)
     fl = fold_flops_per_launch(n4, d)
+    fd_kind = P4.fd_kernel(1)
+    if fd_kind == "fold_fma":
+        fd_prof = ("fd_fold_fma_3d_ne128.md", ("kernels_fd64_fma.cu",),
+                   "fd_fold_fma_kernel (folded FD mode product, FP64 FMAs)")
+    else:
+        fd_prof = ("fd_fold_mma_3d_ne128.md", ("kernels_fd64.cu",),
+                   "fd_fold_mma_kernel (folded FD mode product, FP64 mma.sync m8n8k4)")
     main["roofline"] = {
         "bound": "alu", "achieved": fl / t_launch / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
         "frac": fl / t_launch / 1e9 / fp64_peak,
-        "traffic": committed_traffic("fd_fold_mma_3d_ne128.md", ("kernels_fd64.cu",)),
-        "kernel": "fd_fold_mma_kernel (folded FD mode product, FP64 mma.sync m8n8k4)",
+        "traffic": committed_traffic(fd_prof[0], fd_prof[1]),
+        "kernel": fd_prof[2],
         "per_launch_us": t_launch * 1e6, "flops_per_launch": fl,
         "dense_equivalent_flops_per_launch": 2.0 * n4 ** (d + 1),
         "peak_note": f"of measured: FP64 ceiling of this GPU measured in this run by "

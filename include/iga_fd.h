@@ -250,6 +250,21 @@ iga_status iga_solve_host(iga_handle h, const double *rhs_host, double *x_host,
  * and one Arnoldi step); builds the graph if no solve has run yet.           */
 iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration);
 
+/* Which kernel runs the mode products of this handle's FD solve for nrhs right-hand sides
+ * (eq. FD2D / FD3D): *kind = IGA_FD_KERNEL_FOLD_MMA (folded products, FP64 mma.sync),
+ * IGA_FD_KERNEL_FOLD_FMA (folded products, FP64 FMAs), IGA_FD_KERNEL_DENSE_MMA (pencils
+ * without reflection parity, FP64 mma.sync) or IGA_FD_KERNEL_TENSOR_CORE (tcgen05, the
+ * TF32 / BF16 precision forms).  The FP64 choice depends on the size (more rows favour the
+ * FMA kernel); IGA_FD64=fma|mma in the environment forces one.  Errors:
+ * IGA_ERR_INVALID_ARG for a null handle or kind, nrhs < 1, or an unpreconditioned handle. */
+typedef enum {
+  IGA_FD_KERNEL_FOLD_MMA = 0,
+  IGA_FD_KERNEL_FOLD_FMA = 1,
+  IGA_FD_KERNEL_DENSE_MMA = 2,
+  IGA_FD_KERNEL_TENSOR_CORE = 3
+} iga_fd_kernel_kind;
+iga_status iga_fd_kernel(iga_handle h, int nrhs, int *kind);
+
 /* s = P^{-1} b by the FP64 FD method, eq. (FD2D) / (FD3D), for callers that cannot
  * allocate device memory when they apply the preconditioner (a fixed memory budget
  * reserved up front, an allocator-free real-time loop, or a host whose own allocator owns

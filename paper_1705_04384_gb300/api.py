@@ -123,6 +123,13 @@ class Problem:
         """Allocate the solve workspace and capture the solve graph ahead of time."""
         check(self.lib.iga_prepare(self.h, int(nrhs), int(max_iter)), "iga_prepare")
 
+    def fd_kernel(self, nrhs=1):
+        """Name of the kernel that runs this handle's FD mode products for nrhs
+        right-hand sides: fold_mma, fold_fma, dense_mma or tensor_core."""
+        k = ctypes.c_int()
+        check(self.lib.iga_fd_kernel(self.h, int(nrhs), ctypes.byref(k)), "iga_fd_kernel")
+        return ("fold_mma", "fold_fma", "dense_mma", "tensor_core")[k.value]
+
     def launch_counts(self):
         """(fixed, per_iteration): kernel launches of one solve = fixed + per_iteration * iters."""
         f, it = ctypes.c_int(), ctypes.c_int()

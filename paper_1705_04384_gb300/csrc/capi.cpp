@@ -314,6 +314,21 @@ iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration) {
   });
 }
 
+iga_status iga_fd_kernel(iga_handle h, int nrhs, int *kind) {
+  return guarded([&]() -> iga_status {
+    if (!h || !kind || nrhs < 1) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle or kind, or nrhs < 1"};
+    const iga::Ctx &c = h->c;
+    if (c.prec == IGA_PREC_NONE)
+      throw iga::Error{IGA_ERR_INVALID_ARG, "unpreconditioned handle"};
+    if (c.prec != IGA_PREC_FP64) *kind = IGA_FD_KERNEL_TENSOR_CORE;
+    else if (!c.fold_ok) *kind = IGA_FD_KERNEL_DENSE_MMA;
+    else
+      *kind = iga::use_fold_fma((long long)nrhs * (c.N / c.n), c.n) ? IGA_FD_KERNEL_FOLD_FMA
+                                                                   : IGA_FD_KERNEL_FOLD_MMA;
+    return IGA_OK;
+  });
+}
+
 iga_status iga_solve_bicgstab(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0,
                               double tol, int max_iter, int *half_steps, double *res_hist_host,
                               double *true_relres) {

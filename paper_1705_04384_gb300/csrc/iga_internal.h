@@ -177,6 +177,7 @@ struct Factor1D {
   bool folded = false;
   int ne = 0;
   DevBuf<double> d_Bf, d_Bi, d_lam_fold;
+  DevBuf<double> d_BfT, d_BiT;  // their transposes (n x n, n x ne), for the FMA kernel
   // FD pencil (K + shift B', M): shift = w_l, the wind of the direction (Sec. 3.2)
   double shift = 0.0;
 
@@ -200,6 +201,14 @@ struct FdScale;
 template <class Tout>
 void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
                            int M, int n, int ne, const FdScale *scale, cudaStream_t s, int nrhs);
+// The folded products on FP64 FMAs (kernels_fd64_fma.cu): BT is d_BfT (dir 0) or d_BiT
+// (dir 1); dinv (forward only, may be null) is the fused diagonal.
+void launch_gemm_fp64_fold_fma(int dir, IdxPtr<const double> A, const double *BT,
+                               IdxPtr<double> out, int M, int n, int ne, const double *dinv,
+                               cudaStream_t s, int nrhs);
+// Whether the folded FP64 products of M rows of length n run on the FMA kernel (else on
+// mma.sync); IGA_FD64=fma|mma forces one.
+bool use_fold_fma(long long M, int n);
 template <class Tout>
 void launch_gemm_fp64_dense_mma(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out,
                                 int M, int n, const FdScale *scale, cudaStream_t s, int nrhs);
@@ -223,6 +232,7 @@ void span_basis(const std::vector<double> &t, int p, int mu, double x, double ou
 std::shared_mutex &device_mutex();
 void ensure_kernels_loaded();
 void preload_kernels_fd64();
+void preload_kernels_fd64_fma();
 void preload_kernels_fd_tc();
 void preload_kernels_geom_op();
 void preload_kernels_krylov();

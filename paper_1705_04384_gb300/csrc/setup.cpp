@@ -143,8 +143,9 @@ struct SolverHandle {
 // largest singular value of a dense row-major n x n matrix by power iteration on A^T A
 double norm2_est(const std::vector<double> &A, int n) {
   std::vector<double> x(n, 1.0 / std::sqrt((double)n)), y(n), z(n);
-  double s = 0.0;
-  for (int it = 0; it < 60; ++it) {
+  double s = 0.0, s_prev = -1.0;
+  for (int it = 0; it < 60 && std::fabs(s - s_prev) > 1e-12 * s; ++it) {
+    s_prev = s;
     for (int i = 0; i < n; ++i) {
       double a = 0.0;
       for (int j = 0; j < n; ++j) a += A[(size_t)i * n + j] * x[j];
@@ -326,27 +327,17 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
       Mc[i + (size_t)n * j] = mval(i, t);
       Kc[i + (size_t)n * j] = kval(i, t);
     }
-  SolverHandle sh;
-  CUSOLVER_TRY(cusolverDnCreate(&sh.h));
-  CUSOLVER_TRY(cusolverDnSetStream(sh.h, stream));
-  CUSOLVER_TRY(cusolverDnCreateParams(&sh.prm));
+  // Every CUDA and cuSOLVER call of this function -- handle creation and destruction
+  // (which may load library code), allocations, frees, solves -- runs with the device lock
+  // held shared; the O(n^2 W) host work between them runs unlocked.
   std::vector<double> lam_u, VR;
-  eig_all(sh, Kc, Mc, n, lam_u, VR, stream);
-  DevBuf<double> dM, dX;
-  DevBuf<int64_t> dipiv;
-  DevBuf<int> dinfo;
-  dM.alloc((size_t)n * n);
-  dX.alloc((size_t)n * n);
-  dipiv.alloc(n);
-  dinfo.alloc(1);
-  auto check_info = [&](const char *what) {
-    int info = 0;
-    IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    IGA_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (info != 0)
-      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
-  };
-  size_t dws = 0, hws = 0;
+  std::shared_lock<std::shared_mutex> dlk(device_mutex());
+  auto sh = std::make_unique<SolverHandle>();
+  CUSOLVER_TRY(cusolverDnCreate(&sh->h));
+  CUSOLVER_TRY(cusolverDnSetStream(sh->h, stream));
+  CUSOLVER_TRY(cusolverDnCreateParams(&sh->prm));
+  eig_all(*sh, Kc, Mc, n, lam_u, VR, stream);
+  dlk.unlock();
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam_u[a] < lam_u[b]; });
@@ -370,24 +361,46 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
       for (int j = 0; j < n; ++j) MUc[i + (size_t)n * j] += mv * f.U[(size_t)k * n + j];
     }
   for (int i = 0; i < n; ++i) Ic[i + (size_t)n * i] = 1.0;
+  std::vector<double> Xc((size_t)n * n);
+  dlk.lock();
+  DevBuf<double> dM, dX;
+  DevBuf<int64_t> dipiv;
+  DevBuf<int> dinfo;
+  dM.alloc((size_t)n * n);
+  dX.alloc((size_t)n * n);
+  dipiv.alloc(n);
+  dinfo.alloc(1);
+  auto check_info = [&](const char *what) {
+    int info = 0;
+    IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (info != 0)
+      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
+  };
+  size_t dws = 0, hws = 0;
   IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, MUc.data(), MUc.size() * 8, cudaMemcpyHostToDevice, stream));
   IGA_CUDA_TRY(cudaMemcpyAsync(dX.ptr, Ic.data(), Ic.size() * 8, cudaMemcpyHostToDevice, stream));
-  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
+  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh->h, sh->prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
                                            &dws, &hws));
   {
     DevBuf<char> dbuf;
     dbuf.alloc(std::max<size_t>(dws, 1));
     std::vector<char> hbuf(std::max<size_t>(hws, 1));
-    CUSOLVER_TRY(cusolverDnXgetrf(sh.h, sh.prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
+    CUSOLVER_TRY(cusolverDnXgetrf(sh->h, sh->prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
                                   dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
     check_info("getrf(MU)");
   }
-  CUSOLVER_TRY(cusolverDnXgetrs(sh.h, sh.prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
+  CUSOLVER_TRY(cusolverDnXgetrs(sh->h, sh->prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
                                 CUDA_R_64F, dX.ptr, n, dinfo.ptr));
   check_info("getrs(MU, I)");
-  std::vector<double> Xc((size_t)n * n);
   IGA_CUDA_TRY(cudaMemcpyAsync(Xc.data(), dX.ptr, Xc.size() * 8, cudaMemcpyDeviceToHost, stream));
   IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  dM.release();
+  dX.release();
+  dipiv.release();
+  dinfo.release();
+  sh.reset();
+  dlk.unlock();
   f.Vt.resize((size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) f.Vt[(size_t)i * n + j] = Xc[i + (size_t)n * j];
@@ -458,8 +471,15 @@ static void build_folded(Factor1D &f, cudaStream_t s) {
   for (int a = 0; a < ne; ++a)
     for (int k = 0; k < n; ++k)
       if (k < ne || a < h) Bi[(size_t)a * n + k] = f.U[(size_t)a * n + perm[k]];
+  std::vector<double> BfT((size_t)n * n), BiT((size_t)n * ne);
+  for (int c = 0; c < n; ++c)
+    for (int q = 0; q < n; ++q) BfT[(size_t)q * n + c] = Bf[(size_t)c * n + q];
+  for (int a = 0; a < ne; ++a)
+    for (int k = 0; k < n; ++k) BiT[(size_t)k * ne + a] = Bi[(size_t)a * n + k];
   upload(f.d_Bf, Bf, s);
   upload(f.d_Bi, Bi, s);
+  upload(f.d_BfT, BfT, s);
+  upload(f.d_BiT, BiT, s);
   upload(f.d_lam_fold, lamf, s);
   f.ne = ne;
   f.folded = true;
@@ -518,6 +538,7 @@ int pdl_mask() {
   return mask;
 }
 
+
 void ensure_kernels_loaded() {
   static bool loaded[64] = {};
   int dev = 0;
@@ -525,6 +546,7 @@ void ensure_kernels_loaded() {
   std::unique_lock<std::shared_mutex> lk(device_mutex());
   if (dev < 0 || dev >= 64 || loaded[dev]) return;
   preload_kernels_fd64();
+  preload_kernels_fd64_fma();
   preload_kernels_fd_tc();
   preload_kernels_geom_op();
   preload_kernels_krylov();
@@ -559,10 +581,7 @@ std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, dou
   f->scheme = scheme;
   build_basis_1d(*f);
   if (scheme == 1) build_wq_1d(*f);
-  {
-    std::shared_lock<std::shared_mutex> dlk(device_mutex());
-    eigen_factors(*f, stream);
-  }
+  eigen_factors(*f, stream);
   upload_factor(*f, stream);
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);

@@ -13,6 +13,8 @@
 
 #include "context.h"
 
+#include <type_traits>
+
 namespace iga {
 
 Ctx::~Ctx() {
@@ -239,6 +241,15 @@ static void fd_chain_fp64(const Ctx &c, IdxPtr<const double> in, IdxPtr<Tout> ou
       const bool fwd = g < c.d, last = g == 2 * c.d - 1;
       const double *B = fwd ? f.d_Bf.ptr : f.d_Bi.ptr;
       const FdScale *scp = (g == c.d - 1) ? &sc : nullptr;
+      if constexpr (std::is_same_v<Tout, double>) {
+        if (use_fold_fma(M, n)) {
+          launch_gemm_fp64_fold_fma(fwd ? 0 : 1, src, fwd ? f.d_BfT.ptr : f.d_BiT.ptr,
+                                    last ? out : P(bufs[g & 1]), M, n, f.ne,
+                                    scp ? c.dinv.ptr : nullptr, s, R);
+          src = Pc(bufs[g & 1]);
+          continue;
+        }
+      }
       if (last) {
         launch_gemm_fp64_fold<Tout>(1, src, B, out, M, n, f.ne, nullptr, s, R);
       } else {

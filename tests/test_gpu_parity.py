@@ -272,3 +272,69 @@ def test_full_size_3d_revolved(ne, p):
     assert info["status"] == 0 and info["relres_true"] <= 1e-8 * 1.05
     r = b[idx] - rows @ x
     assert np.max(np.abs(r)) <= 1.05e-8 * np.linalg.norm(b)
+
+
+FMA_CHECK = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1705_04384_gb300.api import Problem
+from tests.oracle_ref import ref
+worst = 0.0
+# n odd and even, tiny n, n past one 32-column run, 3D
+for d, ne, p in ((2, 3, 2), (2, 14, 4), (2, 40, 3), (2, 130, 2), (2, 97, 5), (3, 3, 3),
+                 (3, 8, 4), (3, 13, 6), (3, 20, 3)):
+    R = ref(d, ne, p, assemble=False)
+    with Problem(d, ne, p, precision="fp64") as P:
+        for seed in (7, 8):
+            b = np.random.default_rng(seed).standard_normal(R.N)
+            got = P.precond_apply(torch.from_numpy(b).cuda()).cpu().numpy()
+            want = R.fd(b)
+            e = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert e <= 1e-11, (d, ne, p, e)
+            worst = max(worst, e / 1e-11)
+# three right-hand sides in lockstep, GMRES iterate at fixed k against the oracle's
+for d, ne, p, k in ((2, 24, 3, 6), (3, 9, 4, 5)):
+    R = ref(d, ne, p)
+    B = np.stack([R.manufactured_rhs(1e-3, s) for s in range(3)])
+    with Problem(d, ne, p, precision="fp64") as P:
+        X, info = P.solve_multi(torch.from_numpy(B).cuda(), tol=0.0, max_iter=k)
+        X = X.cpu().numpy()
+    for r in range(3):
+        o = R.gmres(B[r], tol=0.0, max_iter=k)
+        e = np.linalg.norm(X[r] - o["x"]) / np.linalg.norm(o["x"])
+        assert info["iters"][r] == k and e <= 1e-10, (d, ne, p, r, e)
+        worst = max(worst, e / 1e-10)
+print("ok", worst)
+"""
+
+
+@pytest.mark.parametrize("kernel", ["fma", "mma"])
+def test_fd64_kernels_match_oracle(kernel, tmp_path):
+    """Both kernels of the folded FP64 mode products, forced through IGA_FD64 (read once
+    per process, hence a child process), against the oracle's FD (1e-11, as above) and
+    GMRES iterates (1e-10) with one and three right-hand sides."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fd64.py"
+    script.write_text(FMA_CHECK)
+    env = dict(os.environ, IGA_FD64=kernel, PYTHONPATH=root)
+    r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def test_fd_kernel_choice():
+    """iga_fd_kernel names the kernel the FD solve runs: the folded products on mma.sync for
+    few rows, on FMAs for many (unless IGA_FD64 forces one), dense products for a wind,
+    tensor cores for the precision forms."""
+    from paper_1705_04384_gb300.api import Problem
+    forced = os.environ.get("IGA_FD64")
+    with _problem(3, 8, 3) as P:
+        assert P.fd_kernel(1) == ("fold_fma" if forced == "fma" else "fold_mma")
+    with _problem(2, 1024, 3) as P:
+        assert P.fd_kernel(1) == ("fold_mma" if forced == "mma" else "fold_fma")
+    with Problem(2, 16, 3, wind=(2.0, 1.0), precision="fp64") as P:
+        assert P.fd_kernel(1) == "dense_mma"
+    with _problem(2, 16, 3, precision="tf32") as P:
+        assert P.fd_kernel(2) == "tensor_core"
