@@ -287,29 +287,17 @@ __device__ __forceinline__ void chunk_dots(const KrylovWs &ws, int r, int j0, in
   }
 }
 
-// (V_r h)[i] and (V_r h)[i + kRT] for one row pair (rows past hi read as zero): kPG
-// vectors per group, the next group's entries loaded before this group's FMAs, kPG
-// independent FMA chains per row; the last nv mod kPG vectors follow with their exact count.
-// h is in shared memory.
+// u[i] - (V_r h)[i] and the same for row i + kRT, as one FMA chain per row that starts at u
+// (rows past hi read as zero): on GB300 a warp-wide FP64 FMA holds a sub-partition's FP64
+// unit for ~64 cycles, so one chain per row with four warps per sub-partition keeps the
+// unit busy, and the chain needs no adds to combine partial sums (split accumulators
+// cost 2 FP64 adds per row).  kPG vectors' entries are loaded ahead of their FMAs.
 constexpr int kPG = 3;
-template <int G>
-__device__ __forceinline__ void proj_group(const KrylovWs &ws, int r, int j,
-                                           const double *__restrict__ hs, long long i, bool v0,
-                                           bool v1, double (&s0)[kPG], double (&s1)[kPG]) {
-#pragma unroll
-  for (int q = 0; q < G; ++q) {
-    const double *v = Vvec(ws, j + q, r);
-    const double b0 = v0 ? v[i] : 0.0, b1 = v1 ? v[i + kRT] : 0.0;
-    s0[q] = fma(b0, hs[j + q], s0[q]);
-    s1[q] = fma(b1, hs[j + q], s1[q]);
-  }
-}
-
-__device__ __forceinline__ void proj_rows(const KrylovWs &ws, int r, int nv,
-                                          const double *__restrict__ hs, long long i,
-                                          long long hi, double &p0, double &p1) {
+__device__ __forceinline__ void sub_proj_rows(const KrylovWs &ws, int r, int nv,
+                                              const double *__restrict__ hs, long long i,
+                                              long long hi, double &x0, double &x1) {
   const bool v0 = i < hi, v1 = i + kRT < hi;
-  double s0[kPG] = {}, s1[kPG] = {}, c0[kPG], c1[kPG];
+  double c0[kPG], c1[kPG];
   const int full = nv - nv % kPG;
   auto load = [&](int j, double (&b0)[kPG], double (&b1)[kPG]) {
 #pragma unroll
@@ -325,8 +313,8 @@ __device__ __forceinline__ void proj_rows(const KrylovWs &ws, int r, int nv,
     if (j + kPG < full) load(j + kPG, n0, n1);
 #pragma unroll
     for (int q = 0; q < kPG; ++q) {
-      s0[q] = fma(c0[q], hs[j + q], s0[q]);
-      s1[q] = fma(c1[q], hs[j + q], s1[q]);
+      x0 = fma(-c0[q], hs[j + q], x0);
+      x1 = fma(-c1[q], hs[j + q], x1);
     }
 #pragma unroll
     for (int q = 0; q < kPG; ++q) {
@@ -334,10 +322,11 @@ __device__ __forceinline__ void proj_rows(const KrylovWs &ws, int r, int nv,
       c1[q] = n1[q];
     }
   }
-  if (nv - full == 1) proj_group<1>(ws, r, full, hs, i, v0, v1, s0, s1);
-  else if (nv - full == 2) proj_group<2>(ws, r, full, hs, i, v0, v1, s0, s1);
-  p0 = (s0[0] + s0[1]) + s0[2];
-  p1 = (s1[0] + s1[1]) + s1[2];
+  for (int j = full; j < nv; ++j) {  // nv mod kPG <= 2 vectors
+    const double *v = Vvec(ws, j, r);
+    x0 = fma(-(v0 ? v[i] : 0.0), hs[j], x0);
+    x1 = fma(-(v1 ? v[i + kRT] : 0.0), hs[j], x1);
+  }
 }
 
 // dst[i] = (u_r[i] - sum_j V_r[j][i] h[j]) (* scale with kScale) for this block's rows.
@@ -348,45 +337,22 @@ __device__ __forceinline__ void subtract_proj(const KrylovWs &ws, int r, int nv,
                                               long long lo, long long hi, double *dst,
                                               double scale = 1.0) {
   for (long long i = lo + threadIdx.x; i < hi; i += 2 * kRT) {
-    double p0, p1;
-    proj_rows(ws, r, nv, hs, i, hi, p0, p1);
-    double x0 = u[i] - p0;
+    double x0 = u[i], x1 = i + kRT < hi ? u[i + kRT] : 0.0;
+    sub_proj_rows(ws, r, nv, hs, i, hi, x0, x1);
     if (kScale) x0 *= scale;
     dst[i] = x0;
     if (i + kRT < hi) {
-      double x1 = u[i + kRT] - p1;
       if (kScale) x1 *= scale;
       dst[i + kRT] = x1;
     }
   }
 }
 
-// (V_r h)[i] for one row (zero past hi), as proj_rows for a single row.
-__device__ __forceinline__ double proj_row(const KrylovWs &ws, int r, int nv,
-                                           const double *__restrict__ hs, long long i, bool ok) {
-  double s[kPG] = {}, c[kPG];
-  const int full = nv - nv % kPG;
-  auto load = [&](int j, double (&b)[kPG]) {
-#pragma unroll
-    for (int q = 0; q < kPG; ++q) b[q] = ok ? Vvec(ws, j + q, r)[i] : 0.0;
-  };
-  if (full > 0) load(0, c);
-  for (int j = 0; j < full; j += kPG) {
-    double n[kPG];
-    if (j + kPG < full) load(j + kPG, n);
-#pragma unroll
-    for (int q = 0; q < kPG; ++q) s[q] = fma(c[q], hs[j + q], s[q]);
-#pragma unroll
-    for (int q = 0; q < kPG; ++q) c[q] = n[q];
-  }
-  if (nv - full >= 1) s[0] = fma(ok ? Vvec(ws, full, r)[i] : 0.0, hs[full], s[0]);
-  if (nv - full >= 2) s[1] = fma(ok ? Vvec(ws, full + 1, r)[i] : 0.0, hs[full + 1], s[1]);
-  return (s[0] + s[1]) + s[2];
-}
-
-// Pass 2 for NV = nv <= 15 vectors, reading V_r from memory once: per row, w' = w - V_r h1
-// (proj_row), then the dots of V_r and w' with w' (the row's V entries were just read:
-// cache hits), NV + 1 accumulators in registers over the block's rows.
+// Pass 2 for NV = nv <= 15 vectors, reading V_r from memory once: per row, the NV entries
+// of V_r are loaded, w' = w - V_r h1 as one FMA chain, then the dots of V_r and w' with w'
+// from the same registers, NV + 1 accumulators over the block's rows.  The other warps of
+// the sub-partition cover the loads' latency (each row is 2 NV + 1 warp FMAs, ~64 cycles
+// of the FP64 unit apiece).
 template <int NV>
 __device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r,
                                             const double *__restrict__ hs, double *w,
@@ -394,11 +360,18 @@ __device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r,
                                             double (*red)[kJC]) {
   constexpr int NA = (NV + 1 + kJC - 1) / kJC * kJC;
   double acc[NA] = {};
+  const long long vs = (long long)ws.R * ws.N;  // stride between V_r[j] and V_r[j + 1]
+  const double *__restrict__ v0 = Vvec(ws, 0, r);
   for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
-    const double x = w[i] - proj_row(ws, r, NV, hs, i, true);
+    double b[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) b[j] = v0[i + j * vs];
+    double x = w[i];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) x = fma(-b[j], hs[j], x);
     w[i] = x;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) acc[j] = fma(Vvec(ws, j, r)[i], x, acc[j]);
+    for (int j = 0; j < NV; ++j) acc[j] = fma(b[j], x, acc[j]);
     acc[NV] = fma(x, x, acc[NV]);
   }
 #pragma unroll
@@ -407,6 +380,33 @@ __device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r,
 #pragma unroll
     for (int q = 0; q < kJC; ++q) a[q] = acc[c * kJC + q];
     block_store_partials(a, min(kJC, NV + 1 - c * kJC), c * kJC, part, gridDim.x, red);
+  }
+}
+
+// Pass 1 for NV = nv <= 15 vectors: the dots of V_r with w over the block's rows in one
+// sweep (w read once), NV accumulators in registers.
+template <int NV>
+__device__ __forceinline__ void pass1_fused(const KrylovWs &ws, int r,
+                                            const double *__restrict__ w, long long lo,
+                                            long long hi, double *part, double (*red)[kJC]) {
+  constexpr int NA = (NV + kJC - 1) / kJC * kJC;
+  double acc[NA] = {};
+  const long long vs = (long long)ws.R * ws.N;
+  const double *__restrict__ v0 = Vvec(ws, 0, r);
+  for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
+    double b[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) b[j] = v0[i + j * vs];
+    const double u = w[i];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = fma(b[j], u, acc[j]);
+  }
+#pragma unroll
+  for (int c = 0; c < NA / kJC; ++c) {
+    double a[kJC];
+#pragma unroll
+    for (int q = 0; q < kJC; ++q) a[q] = acc[c * kJC + q];
+    block_store_partials(a, min(kJC, NV - c * kJC), c * kJC, part, gridDim.x, red);
   }
 }
 
@@ -421,8 +421,15 @@ __global__ void __launch_bounds__(kRT, 2) cgs_pass1_kernel(KrylovWs ws, const do
     if (ws.rs[r].done) continue;
     const double *wr = w + (long long)r * ws.N;
     double *part = ws.partials + r * ws.pstride;
-    for (int j0 = 0; j0 < nv; j0 += kJC)
-      chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
+#define IGA_P1(NVV) \
+  case NVV: pass1_fused<NVV>(ws, r, wr, lo, hi, part, red); break;
+    switch (nv) {
+      IGA_P1(1) IGA_P1(2) IGA_P1(3) IGA_P1(4) IGA_P1(5) IGA_P1(6) IGA_P1(7) IGA_P1(8) IGA_P1(9) IGA_P1(10) IGA_P1(11) IGA_P1(12) IGA_P1(13) IGA_P1(14) IGA_P1(15)
+      default:
+        for (int j0 = 0; j0 < nv; j0 += kJC)
+          chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
+    }
+#undef IGA_P1
     if (!arrive_last(ws.counter + r)) continue;
     last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 0, nullptr);
     __syncthreads();
