@@ -265,6 +265,13 @@ typedef enum {
 } iga_fd_kernel_kind;
 iga_status iga_fd_kernel(iga_handle h, int nrhs, int *kind);
 
+/* Algorithmic FLOPs of one iga_apply_operator on one vector, counted from the handle's
+ * pass plan: 2 per stored band entry of every banded mode product (sum factorization of
+ * eq. collocation, or of eq. WQapprox: expansion onto the quadrature grid and contraction
+ * by the WQ rules), plus 2 per contracted collocation term and 1 per quadrature point of a
+ * Q-weighted WQ term.  Errors: IGA_ERR_INVALID_ARG for a null handle or flops.            */
+iga_status iga_operator_flops(iga_handle h, double *flops);
+
 /* s = P^{-1} b by the FP64 FD method, eq. (FD2D) / (FD3D), for callers that cannot
  * allocate device memory when they apply the preconditioner (a fixed memory budget
  * reserved up front, an allocator-free real-time loop, or a host whose own allocator owns

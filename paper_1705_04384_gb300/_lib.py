@@ -57,6 +57,7 @@ PROTOTYPES = {
     "iga_test_set_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "iga_launch_counts": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p]),
     "iga_fd_kernel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int_p]),
+    "iga_operator_flops": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "iga_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "iga_set_grid_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "iga_solve_bicgstab": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,

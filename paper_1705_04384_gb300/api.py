@@ -130,6 +130,12 @@ class Problem:
         check(self.lib.iga_fd_kernel(self.h, int(nrhs), ctypes.byref(k)), "iga_fd_kernel")
         return ("fold_mma", "fold_fma", "dense_mma", "tensor_core")[k.value]
 
+    def operator_flops(self):
+        """Algorithmic FLOPs of one operator application (iga_operator_flops)."""
+        f = ctypes.c_double()
+        check(self.lib.iga_operator_flops(self.h, ctypes.byref(f)), "iga_operator_flops")
+        return f.value
+
     def launch_counts(self):
         """(fixed, per_iteration): kernel launches of one solve = fixed + per_iteration * iters."""
         f, it = ctypes.c_int(), ctypes.c_int()

@@ -329,6 +329,14 @@ iga_status iga_fd_kernel(iga_handle h, int nrhs, int *kind) {
   });
 }
 
+iga_status iga_operator_flops(iga_handle h, double *flops) {
+  return guarded([&]() -> iga_status {
+    if (!h || !flops) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle or flops"};
+    *flops = h->c.operator_flops();
+    return IGA_OK;
+  });
+}
+
 iga_status iga_solve_bicgstab(iga_handle h, const double *rhs_dev, double *x_dev, int use_x0,
                               double tol, int max_iter, int *half_steps, double *res_hist_host,
                               double *true_relres) {

@@ -142,6 +142,7 @@ struct Ctx {
               cudaStream_t s);
   void wq_load_vector(const double *g, double *f, cudaStream_t s);
   void quadrature_points(double *xyz) const;
+  double operator_flops() const;
   void ensure_capacity(int R);
   template <class Tin>
   void apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t s);

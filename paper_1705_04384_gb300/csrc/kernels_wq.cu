@@ -9,7 +9,10 @@
 // functions).  One launch applies several such banded products along one direction:
 // term t reads input in[t], applies the band rows of the output coordinate, optionally
 // multiplies the input by a pointwise factor first (the Q_ab field on the quadrature
-// grid, fused into the first contraction), and adds into output out_of[t].
+// grid, fused into the first contraction), and adds into output out_of[t]; the terms of
+// one output are consecutive, so each output is one running sum (a per-output accumulator
+// array indexed by a runtime output number compiled to predicated FP64 adds for every slot,
+// which take FP64 issue slots even when predicated off).
 #include "fp_widen.h"
 #include "iga_internal.h"
 
@@ -37,9 +40,8 @@ __global__ void __launch_bounds__(256)
     const unsigned rest = fdiv(o, divL), low = o - rest * L;
     const unsigned high = fdiv(rest, divD), c = rest - high * divD.d;
     const long long base = (long long)low + (long long)L * Din * high;
-    double acc[kWqMaxOut];
-#pragma unroll
-    for (int q = 0; q < kWqMaxOut; ++q) acc[q] = 0.0;
+    // terms come sorted by output: one running sum, stored when the output changes
+    double acc = 0.0;
 #pragma unroll
     for (int t = 0; t < kWqMaxTerms; ++t) {
       if (t >= a.nterm) break;
@@ -56,14 +58,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll 4
         for (int u = 0; u < w; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
       }
-      const int oq = a.out_of[t];
-#pragma unroll
-      for (int q = 0; q < kWqMaxOut; ++q)
-        if (q == oq) acc[q] += s;
+      acc += s;
+      if (t + 1 == a.nterm || a.out_of[t + 1] != a.out_of[t]) {
+        a.out[a.out_of[t]][r * out_per_rhs + o] = acc;
+        acc = 0.0;
+      }
     }
-#pragma unroll
-    for (int q = 0; q < kWqMaxOut; ++q)
-      if (q < a.nout) a.out[q][r * out_per_rhs + o] = acc[q];
   }
 }
 
@@ -72,6 +72,13 @@ void launch_wq_pass(const WqPassArgs<Tin> &a, int dir, const int *ext_in, const 
                     int R, cudaStream_t s) {
   if (a.nterm < 1 || a.nterm > kWqMaxTerms || a.nout < 1 || a.nout > kWqMaxOut)
     throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: bad term or output count"};
+  // the kernel sums consecutive terms of one output: outputs 0 .. nout-1 in order, each
+  // with at least one term
+  for (int t = 0; t < a.nterm; ++t)
+    if (a.out_of[t] != (t ? a.out_of[t - 1] + (a.out_of[t] != a.out_of[t - 1]) : 0))
+      throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: terms not grouped by output"};
+  if (a.out_of[a.nterm - 1] != a.nout - 1)
+    throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: output without a term"};
   long long L = 1, H = 1;
   for (int l = 0; l < dir; ++l) L *= ext_in[l];
   for (int l = dir + 1; l < 3; ++l) H *= ext_in[l];

@@ -218,6 +218,24 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t 
   launch_contract_pass<double>(ins, plan.terms, plan.nterm, out, n, n, n3, band, s, R);
 }
 
+// Algorithmic FLOPs of one application of the operator to one vector, from the pass
+// plan: 2 per stored band entry of every banded product, 2 per contracted collocation term
+// (its coefficient), 1 per quadrature point of a Q-weighted WQ term.
+double Ctx::operator_flops() const {
+  double fl = 0.0;
+  if (scheme == 1) {
+    for (const WqPass &P : wq_op) {
+      const double out = (double)P.ext_out[0] * P.ext_out[1] * P.ext_out[2];
+      const double in = (double)P.ext_in[0] * P.ext_in[1] * P.ext_in[2];
+      const int w = P.kind == 0 ? fac->W : fac->WW;
+      for (int t = 0; t < P.nterm; ++t) fl += 2.0 * w * out + (P.coef[t] >= 0 ? in : 0.0);
+    }
+    return fl;
+  }
+  const int passes = plan.nA + (d == 3 ? plan.nB : 0) + plan.nterm;
+  return (double)N * (2.0 * fac->W * passes + 2.0 * plan.nterm);
+}
+
 template void Ctx::apply_operator<double>(IdxPtr<const double>, double *, int, cudaStream_t);
 template void Ctx::apply_operator<float>(IdxPtr<const float>, double *, int, cudaStream_t);
 

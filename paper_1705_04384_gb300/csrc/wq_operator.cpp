@@ -160,6 +160,17 @@ void Ctx::build_wq_plan() {
         P.out_slot[q] = dir == d - 1 ? -1 : new_slot(P.ext_out);
         next[q].slot = P.out_slot[q];
       }
+      // the pass kernel sums the consecutive terms of one output: group them (stable)
+      int perm[kWqMaxTerms];
+      for (int t = 0; t < P.nterm; ++t) perm[t] = t;
+      std::stable_sort(perm, perm + P.nterm, [&](int x, int y) { return P.out_of[x] < P.out_of[y]; });
+      const WqPass U = P;
+      for (int t = 0; t < P.nterm; ++t) {
+        P.in_slot[t] = U.in_slot[perm[t]];
+        P.sel[t] = U.sel[perm[t]];
+        P.coef[t] = U.coef[perm[t]];
+        P.out_of[t] = U.out_of[perm[t]];
+      }
       chain.push_back(P);
       its = next;
     }

@@ -92,6 +92,7 @@ def test_every_handle_entry_point_rejects_a_null_handle(lib):
         ("iga_solve_collect", (null, null, null, null, null)),
         ("iga_launch_counts", (null, None, None)),
         ("iga_fd_kernel", (null, 1, None)),
+        ("iga_operator_flops", (null, None)),
         ("iga_prepare", (null, 1, 10)),
         ("iga_solve_bicgstab", (null, null, null, 0, 1e-8, 10, None, null, None)),
         ("iga_test_set_device_error", (null, 1)),

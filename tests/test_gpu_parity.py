@@ -338,3 +338,21 @@ def test_fd_kernel_choice():
         assert P.fd_kernel(1) == "dense_mma"
     with _problem(2, 16, 3, precision="tf32") as P:
         assert P.fd_kernel(2) == "tensor_core"
+
+
+def test_operator_flop_count():
+    """iga_operator_flops counts the plan's banded products: the 3D extruded annulus keeps
+    4 of 9 fields (2 + 3 + 4 band passes of 2W FLOPs per DOF, 2 per contracted term), the
+    2D one 3 of 5 (2 passes along the second direction, 3 contracted terms); a WQ plan on
+    the quadrature grid costs more per DOF than the collocation plan of the same mesh."""
+    import bench
+    from paper_1705_04384_gb300.api import Problem
+    for p in (3, 4):
+        with _problem(3, 8, p) as P:
+            assert P.operator_flops() == bench.operator_flops_per_dof(p + 1, 3) * P.N
+    with _problem(2, 12, 3) as P:
+        assert P.operator_flops() == P.N * (2 * 4 * (2 + 3) + 2 * 3)
+    with Problem(3, 6, 3, geometry="revolved", precision="fp64", scheme="wq") as P:
+        fl_wq = P.operator_flops()
+    with Problem(3, 6, 3, geometry="revolved", precision="fp64") as P:
+        assert fl_wq > 4 * P.operator_flops() > 0
