@@ -48,6 +48,11 @@ struct WqPass {
   int coef[kWqMaxTerms] = {};
   int out_of[kWqMaxTerms] = {};
   int out_slot[kWqMaxOut] = {};
+  // fan-out pass: term t writes its band sum times field fcoef[t][k] to slot fslot[t][k]
+  int fan = 0;
+  int nfan[kWqMaxTerms] = {};
+  int fcoef[kWqMaxTerms][kWqMaxFan] = {};
+  int fslot[kWqMaxTerms][kWqMaxFan] = {};
 };
 
 struct SolveGraph {

@@ -317,7 +317,7 @@ void launch_gemm_fp64(IdxPtr<const double> A, const double *Bt, IdxPtr<Tout> out
 // reads in[t] (nullptr: the pass input vin), applies band rows start[c] .. + width - 1 of
 // the output coordinate c (values band + c * width), optionally times the pointwise
 // field coef (on the input grid), and adds into output out_of[t].
-constexpr int kWqMaxTerms = 9, kWqMaxOut = 9;
+constexpr int kWqMaxTerms = 9, kWqMaxOut = 9, kWqMaxFan = 3;
 template <class Tin> struct WqPassArgs {
   IdxPtr<const Tin> vin;
   const Tin *in[kWqMaxTerms];
@@ -328,6 +328,12 @@ template <class Tin> struct WqPassArgs {
   int out_of[kWqMaxTerms];
   double *out[kWqMaxOut];
   int nterm, nout;
+  // fan-out pass (fan = 1): term t's band sum s is written, times the pointwise field
+  // fcoef[t][k] on the output grid, to fout[t][k] for k < nfan[t] (out / out_of unused)
+  int fan;
+  int nfan[kWqMaxTerms];
+  const double *fcoef[kWqMaxTerms][kWqMaxFan];
+  double *fout[kWqMaxTerms][kWqMaxFan];
 };
 template <class Tin>
 void launch_wq_pass(const WqPassArgs<Tin> &a, int dir, const int *ext_in, const int *ext_out,

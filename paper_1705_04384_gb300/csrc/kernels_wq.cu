@@ -9,10 +9,14 @@
 // functions).  One launch applies several such banded products along one direction:
 // term t reads input in[t], applies the band rows of the output coordinate, optionally
 // multiplies the input by a pointwise factor first (the Q_ab field on the quadrature
-// grid, fused into the first contraction), and adds into output out_of[t]; the terms of
+// grid, for the load vector's first contraction), and adds into output out_of[t]; the terms of
 // one output are consecutive, so each output is one running sum (a per-output accumulator
 // array indexed by a runtime output number compiled to predicated FP64 adds for every slot,
-// which take FP64 issue slots even when predicated off).
+// which take FP64 issue slots even when predicated off).  The operator's last expansion
+// pass fans out instead: each derivative of u on the quadrature grid is summed once and
+// written once per Q_ab that multiplies it (Q on the output grid), so the contraction
+// taps are plain FMAs (multiplying Q in at every contraction tap cost ~WW n / nq times the
+// multiplies).
 #include "fp_widen.h"
 #include "iga_internal.h"
 
@@ -36,6 +40,30 @@ __global__ void __launch_bounds__(256)
   pdl_entry();
   const int r = blockIdx.y;
   const Tin *vin = a.vin.get();
+  if (a.fan) {  // expansion with the Q factors applied on the output grid
+    for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < Nout;
+         o += gridDim.x * blockDim.x) {
+      const unsigned rest = fdiv(o, divL), low = o - rest * L;
+      const unsigned high = fdiv(rest, divD), c = rest - high * divD.d;
+      const long long base = (long long)low + (long long)L * Din * high;
+#pragma unroll
+      for (int t = 0; t < kWqMaxTerms; ++t) {
+        if (t >= a.nterm) break;
+        const int st = __ldg(a.start[t] + c), w = a.width[t];
+        const double *bd = a.band[t] + (long long)c * w;
+        const Tin *src = (a.in[t] ? a.in[t] : vin) + r * in_per_rhs + base + (long long)L * st;
+        double s = 0.0;
+#pragma unroll 4
+        for (int u = 0; u < w; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
+#pragma unroll
+        for (int k = 0; k < kWqMaxFan; ++k) {
+          if (k >= a.nfan[t]) break;
+          a.fout[t][k][r * out_per_rhs + o] = __ldg(a.fcoef[t][k] + o) * s;
+        }
+      }
+    }
+    return;
+  }
   for (unsigned o = blockIdx.x * blockDim.x + threadIdx.x; o < Nout; o += gridDim.x * blockDim.x) {
     const unsigned rest = fdiv(o, divL), low = o - rest * L;
     const unsigned high = fdiv(rest, divD), c = rest - high * divD.d;
@@ -70,14 +98,21 @@ __global__ void __launch_bounds__(256)
 template <class Tin>
 void launch_wq_pass(const WqPassArgs<Tin> &a, int dir, const int *ext_in, const int *ext_out,
                     int R, cudaStream_t s) {
-  if (a.nterm < 1 || a.nterm > kWqMaxTerms || a.nout < 1 || a.nout > kWqMaxOut)
+  if (a.fan) {
+    if (a.nterm < 1 || a.nterm > kWqMaxTerms)
+      throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: bad term count"};
+    for (int t = 0; t < a.nterm; ++t)
+      if (a.nfan[t] < 1 || a.nfan[t] > kWqMaxFan || a.coef[t])
+        throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: bad fan-out"};
+  } else if (a.nterm < 1 || a.nterm > kWqMaxTerms || a.nout < 1 || a.nout > kWqMaxOut) {
     throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: bad term or output count"};
+  }
   // the kernel sums consecutive terms of one output: outputs 0 .. nout-1 in order, each
   // with at least one term
-  for (int t = 0; t < a.nterm; ++t)
+  for (int t = 0; t < a.nterm && !a.fan; ++t)
     if (a.out_of[t] != (t ? a.out_of[t - 1] + (a.out_of[t] != a.out_of[t - 1]) : 0))
       throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: terms not grouped by output"};
-  if (a.out_of[a.nterm - 1] != a.nout - 1)
+  if (!a.fan && a.out_of[a.nterm - 1] != a.nout - 1)
     throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: output without a term"};
   long long L = 1, H = 1;
   for (int l = 0; l < dir; ++l) L *= ext_in[l];

@@ -220,7 +220,8 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t 
 
 // Algorithmic FLOPs of one application of the operator to one vector, from the pass
 // plan: 2 per stored band entry of every banded product, 2 per contracted collocation term
-// (its coefficient), 1 per quadrature point of a Q-weighted WQ term.
+// (its coefficient), 1 per quadrature point of a Q-weighted WQ term (the multiplication by
+// Q_ab, on the expansion's output grid).
 double Ctx::operator_flops() const {
   double fl = 0.0;
   if (scheme == 1) {
@@ -228,7 +229,8 @@ double Ctx::operator_flops() const {
       const double out = (double)P.ext_out[0] * P.ext_out[1] * P.ext_out[2];
       const double in = (double)P.ext_in[0] * P.ext_in[1] * P.ext_in[2];
       const int w = P.kind == 0 ? fac->W : fac->WW;
-      for (int t = 0; t < P.nterm; ++t) fl += 2.0 * w * out + (P.coef[t] >= 0 ? in : 0.0);
+      for (int t = 0; t < P.nterm; ++t)
+        fl += 2.0 * w * out + (P.coef[t] >= 0 ? in : 0.0) + (P.fan ? P.nfan[t] * out : 0.0);
     }
     return fl;
   }

@@ -83,10 +83,14 @@ void Ctx::build_wq_plan() {
     for (int l = k; l < d; ++l) code |= (l == beta ? 1 : 0) << l;
     return code;
   };
+  // the last pass (direction 0) fans out: d_beta u on the quadrature grid is summed once and
+  // written as Q_{a,beta} d_beta u for every active a (slot fan_slot[a][beta])
+  int fan_slot[3][3];
   for (int dir = d - 1; dir >= 0; --dir) {
     WqPass P;
     P.dir = dir;
     P.kind = 0;
+    P.fan = dir == 0 ? 1 : 0;
     std::memcpy(P.ext_in, ext, sizeof(ext));
     ext[dir] = nq;
     std::memcpy(P.ext_out, ext, sizeof(ext));
@@ -94,23 +98,34 @@ void Ctx::build_wq_plan() {
     for (int beta : betas) {
       const int code = suffix(beta, dir);
       if (next.count(code)) continue;
-      const int q = P.nout++;
-      next[code] = q;
-      P.in_slot[P.nterm] = cur.at(suffix(beta, dir + 1));
-      P.sel[P.nterm] = beta == dir ? 1 : 0;
-      P.coef[P.nterm] = -1;
-      P.out_of[P.nterm] = q;
-      P.nterm++;
+      const int t = P.nterm++;
+      P.in_slot[t] = cur.at(suffix(beta, dir + 1));
+      P.sel[t] = beta == dir ? 1 : 0;
+      P.coef[t] = -1;
+      if (P.fan) {
+        next[code] = -1;
+        for (int a = 0; a < d; ++a) {
+          if (!wq_active[wq_field(d, a, beta)]) continue;
+          const int k = P.nfan[t]++;
+          P.fcoef[t][k] = wq_field(d, a, beta);
+          P.fslot[t][k] = fan_slot[a][beta] = new_slot(P.ext_out);
+        }
+      } else {
+        const int q = P.nout++;
+        next[code] = q;
+        P.out_of[t] = q;
+      }
     }
-    for (auto &kv : next) {
-      const int q = kv.second;
-      P.out_slot[q] = new_slot(P.ext_out);
-      kv.second = P.out_slot[q];
-    }
+    if (!P.fan)
+      for (auto &kv : next) {
+        const int q = kv.second;
+        P.out_slot[q] = new_slot(P.ext_out);
+        kv.second = P.out_slot[q];
+      }
     cur = next;
     wq_op.push_back(P);
   }
-  // Y_beta = cur[suffix(beta, 0)] on the quadrature grid
+  // Q_ab d_b u on the quadrature grid: slot fan_slot[a][b]
 
   // ---- contraction: directions 0 .. d-1; an item after contracting directions 0 .. k-1 is
   // identified by its remaining rules (r_k .. r_{d-1}), r_l = 2 a_l + b_l, in base-4 digits
@@ -123,9 +138,8 @@ void Ctx::build_wq_plan() {
     int slot, code, field;
   };
   std::vector<Item> items;
-  for (auto &t : terms)
-    items.push_back({cur.at(suffix(t.second, 0)), rules(t.first, t.second),
-                     wq_field(d, t.first, t.second)});
+  for (auto &t : terms)  // Q is already applied: no coefficient in the contraction
+    items.push_back({fan_slot[t.first][t.second], rules(t.first, t.second), -1});
   auto contract_chain = [&](std::vector<Item> its, std::vector<WqPass> &chain) {
     int e[3] = {1, 1, 1};
     for (int l = 0; l < d; ++l) e[l] = nq;
@@ -205,6 +219,14 @@ void Ctx::run_wq(const std::vector<WqPass> &chain, IdxPtr<const Tin> in, double 
     A.nout = P.nout;
     for (int q = 0; q < P.nout; ++q)
       A.out[q] = P.out_slot[q] < 0 ? out : wq_scratch.ptr + R * off[P.out_slot[q]];
+    A.fan = P.fan;
+    for (int t = 0; t < P.nterm && P.fan; ++t) {
+      A.nfan[t] = P.nfan[t];
+      for (int k = 0; k < P.nfan[t]; ++k) {
+        A.fcoef[t][k] = wq_fields.ptr + P.fcoef[t][k] * ldq;
+        A.fout[t][k] = wq_scratch.ptr + R * off[P.fslot[t][k]];
+      }
+    }
   };
   for (size_t k = 0; k < chain.size(); ++k) {
     const WqPass &P = chain[k];
