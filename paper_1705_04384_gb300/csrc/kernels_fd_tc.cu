@@ -169,6 +169,66 @@ struct TcEpi {
   int *err;
 };
 
+// Epilogue of one 128 x n_tile tile for the 32 rows (TMEM lanes) of one warp: tcgen05.ld of
+// 16 columns at a time, optional FD diagonal, conversion, stores in the rotated layout.
+// Row = a + n (m + nmid r) (a: fastest component, m: middle, r: right-hand side); the output
+// index a + ld_out (m + nmid col + nmid N r) keeps r slowest.  The diagonal's entries of the
+// next 16 columns are loaded before this chunk's stores: loaded next to each store they
+// waited behind it, a memory latency per column (a persistent CTA's second product, the one
+// with the diagonal, took three times as long as its first).  Called by all 32 lanes (the
+// TMEM load is warp-collective).
+__device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c0, int N,
+                                              int n_tile, const TcEpi &epi) {
+  long long obase = 0;
+  const float *dinv_row = nullptr;  // the FD diagonal in DOF order: a + n (m + nmid col)
+  if (row < M) {
+    const int a = row % epi.n, rest = row / epi.n;
+    const int m = rest % epi.nmid, rr = rest / epi.nmid;
+    obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
+    if (epi.dinv) dinv_row = epi.dinv + a + (long long)epi.n * m;
+  }
+  const long long cstride = (long long)epi.ld_out * epi.nmid;
+  const long long dstride = (long long)epi.n * epi.nmid;
+  const long long off = epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0;
+  auto load_dv = [&](int cc, float (&dv)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int col = c0 + cc + j;
+      dv[j] = (dinv_row && col < N) ? __ldg(dinv_row + dstride * col) : 1.0f;
+    }
+  };
+  float dv[16];
+  load_dv(0, dv);
+  for (int cc = 0; cc < n_tile; cc += 16) {
+    float dn[16];
+    if (cc + 16 < n_tile) load_dv(cc + 16, dn);
+    uint32_t v[16];
+    tmem_ld16(tl + (uint32_t)cc, v);
+    if (row < M) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c0 + cc + j;
+        if (col < N) {
+          float x = __uint_as_float(v[j]);
+          if (dinv_row) x *= dv[j];
+          const long long o = off + obase + cstride * col;
+          if (epi.kind == kOutF32) {
+            ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
+          } else if (epi.kind == kOutBF16) {
+            ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
+          } else {
+            ((double *)epi.out)[o] = (double)x;
+          }
+        }
+      }
+    }
+    if (cc + 16 < n_tile) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) dv[j] = dn[j];
+    }
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -257,43 +317,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // the accumulator is incomplete (the error word is already set): store nothing
   } else {
     tc_fence_after();
-    // row = a + n (m + nmid r): a = fastest component, m = middle, r = right-hand side;
-    // output index a + ld_out (m + nmid col + nmid N r) keeps r slowest
     const int row = m0 + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    long long obase = 0;
-    const float *dinv_row = nullptr;  // the FD diagonal in DOF order: a + n (m + nmid col)
-    if (row < M) {
-      const int a = row % epi.n, rest = row / epi.n;
-      const int m = rest % epi.nmid, rr = rest / epi.nmid;
-      obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
-      if (epi.dinv) dinv_row = epi.dinv + a + (long long)epi.n * m;
-    }
-    const long long cstride = (long long)epi.ld_out * epi.nmid;
-    const long long dstride = (long long)epi.n * epi.nmid;
-    const long long off = epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0;
-    for (int cc = 0; cc < n_tile; cc += 16) {
-      uint32_t v[16];
-      tmem_ld16(tl + (uint32_t)cc, v);
-      if (row < M) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = c0 + cc + j;
-          if (col < N) {
-            float x = __uint_as_float(v[j]);
-            if (dinv_row) x *= __ldg(dinv_row + dstride * col);
-            const long long o = off + obase + cstride * col;
-            if (epi.kind == kOutF32) {
-              ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
-            } else if (epi.kind == kOutBF16) {
-              ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
-            } else {
-              ((double *)epi.out)[o] = (double)x;
-            }
-          }
-        }
-      }
-    }
+    tc_store_rows(tmem + ((uint32_t)(warp * 32) << 16), row, M, c0, N, n_tile, epi);
   }
   tc_fence_before();
   __syncthreads();
@@ -324,45 +349,6 @@ constexpr size_t kTcpRingBytes = 200 * 1024;  // ring budget per CTA (stages x s
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Epilogue of one 128 x n_tile tile for the 32 rows (TMEM lanes) of one warp: tcgen05.ld of
-// 16 columns at a time, optional FD diagonal, conversion, stores in the rotated layout.
-__device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c0, int N,
-                                              int n_tile, const TcEpi &epi) {
-  long long obase = 0;
-  const float *dinv_row = nullptr;
-  if (row < M) {
-    const int a = row % epi.n, rest = row / epi.n;
-    const int m = rest % epi.nmid, rr = rest / epi.nmid;
-    obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
-    if (epi.dinv) dinv_row = epi.dinv + a + (long long)epi.n * m;
-  }
-  const long long cstride = (long long)epi.ld_out * epi.nmid;
-  const long long dstride = (long long)epi.n * epi.nmid;
-  const long long off = epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0;
-  for (int cc = 0; cc < n_tile; cc += 16) {
-    uint32_t v[16];
-    tmem_ld16(tl + (uint32_t)cc, v);
-    if (row < M) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = c0 + cc + j;
-        if (col < N) {
-          float x = __uint_as_float(v[j]);
-          if (dinv_row) x *= __ldg(dinv_row + dstride * col);
-          const long long o = off + obase + cstride * col;
-          if (epi.kind == kOutF32) {
-            ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
-          } else if (epi.kind == kOutBF16) {
-            ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
-          } else {
-            ((double *)epi.out)[o] = (double)x;
-          }
-        }
-      }
-    }
-  }
 }
 
 template <int KIND>
@@ -591,9 +577,9 @@ static bool persistent_candidate(int R_max) {
 }
 
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
-// candidate column tile -- the whole padded width, or 2, 3, 4 ... narrower tiles that
-// put more CTAs on the GPU at the cost of re-reading the row tile -- and keep the
-// fastest.  The choice is cached per (device, d, n, precision, R_max) so that every
+// candidate column tile -- the padded width split into the fewest parts of at most 256
+// columns and up to 5 more (narrower tiles put more CTAs on the GPU at the cost of
+// re-reading the row tile), and 256, 128, 64 for n > 256 -- and keep the fastest.  The choice is cached per (device, d, n, precision, R_max) so that every
 // problem of one shape runs the same kernels.
 static void autotune(TcFd &t, cudaStream_t s) {
   static std::mutex mu;
@@ -610,13 +596,30 @@ static void autotune(TcFd &t, cudaStream_t s) {
     }
   }
   std::vector<int> widths;
-  if (t.n <= 256) {
-    for (int parts = 1; parts <= 6; ++parts) {
-      const int nt = ((t.n + parts - 1) / parts + 15) / 16 * 16;
-      if (std::find(widths.begin(), widths.end(), nt) == widths.end()) widths.push_back(nt);
-    }
+  // IGA_TC_TILE=<multiple of 16, at most 256 and n rounded up to 16>: the only column tile
+  // (pins the configuration, e.g. for a profiler run, under which the timings that rank the
+  // candidates are distorted)
+  const char *tile_env = std::getenv("IGA_TC_TILE");
+  const int forced_tile = tile_env ? std::atoi(tile_env) : 0;
+  if (forced_tile >= 16 && forced_tile <= 256 && forced_tile % 16 == 0 &&
+      forced_tile <= (t.n + 15) / 16 * 16) {
+    widths = {forced_tile};
   } else {
-    widths = {256, 128, 64};
+    // the padded width split into p0 .. p0 + 5 balanced parts (p0: the fewest parts of at most
+    // 256 columns), each rounded up to 16: no nearly empty last tile (n = 1025 in 256-column
+    // tiles left a fifth tile of one column, a full MMA width of work), and tile counts that
+    // fill whole waves of the persistent grid
+    const int p0 = (t.n + 255) / 256;
+    for (int parts = p0; parts <= p0 + 5; ++parts) {
+      const int nt = ((t.n + parts - 1) / parts + 15) / 16 * 16;
+      if (nt <= 256 && std::find(widths.begin(), widths.end(), nt) == widths.end())
+        widths.push_back(nt);
+    }
+    // and, for wide problems, the powers of two (2D n = 1025 with one right-hand side runs
+    // fastest in 64-column tiles: 77 against 84 us per FD apply for the best balanced width)
+    if (t.n > 256)
+      for (int nt : {256, 128, 64})
+        if (std::find(widths.begin(), widths.end(), nt) == widths.end()) widths.push_back(nt);
   }
   // (column tile, persistent kernel)
   std::vector<std::pair<int, int>> cand;

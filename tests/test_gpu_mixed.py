@@ -131,7 +131,8 @@ from paper_1705_04384_gb300.api import Problem
 from tests.oracle_ref import ref
 worst = 0.0
 for prec, tol in (("tf32", 1e-2), ("bf16", 6e-2)):
-    for d, ne, p, R in ((2, 40, 3, 1), (2, 95, 5, 4), (3, 9, 3, 1), (3, 20, 4, 3)):
+    for d, ne, p, R in ((2, 40, 3, 1), (2, 95, 5, 4), (2, 300, 3, 2), (3, 9, 3, 1),
+                        (3, 20, 4, 3)):
         Rf = ref(d, ne, p, assemble=False)
         with Problem(d, ne, p, precision=prec) as P:
             P.prepare(R, 10)
