@@ -230,6 +230,9 @@ void span_basis(const std::vector<double> &t, int p, int mu, double x, double ou
 // capture is in progress.  Every kernel of this library is loaded once per device before
 // the first problem is set up, so none of it is loaded during a capture.
 std::shared_mutex &device_mutex();
+// IGA_VERBOSE=2 prints the duration of each setup phase to stderr (0 when unset)
+int verbose_level();
+double wall_seconds();
 void ensure_kernels_loaded();
 void preload_kernels_fd64();
 void preload_kernels_fd64_fma();

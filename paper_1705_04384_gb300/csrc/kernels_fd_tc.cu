@@ -629,7 +629,9 @@ static void autotune(TcFd &t, cudaStream_t s) {
     for (int nt : widths) cand.push_back({nt, 1});
   std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
+    const double tw = wall_seconds();
     std::unique_lock<std::shared_mutex> dlk(device_mutex());
+    const double tl = wall_seconds();
     cudaEvent_t e0, e1;
     IGA_CUDA_TRY(cudaEventCreate(&e0));
     IGA_CUDA_TRY(cudaEventCreate(&e1));
@@ -659,8 +661,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
         best_ms = ms;
         best = cd;
       }
-      const char *verbose = std::getenv("IGA_VERBOSE");
-      if (verbose && verbose[0] == '1')
+      if (verbose_level() >= 1)
         std::fprintf(stderr,
                      "iga autotune d=%d n=%d prec=%d R=%d n_tile=%d%s: %.1f us/apply\n", t.d,
                      t.n, t.prec, t.R_max, cd.first, cd.second ? " persistent" : "",
@@ -669,6 +670,10 @@ static void autotune(TcFd &t, cudaStream_t s) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     IGA_CUDA_TRY(cudaMemsetAsync(t.err.ptr, 0, sizeof(int), s));
+    if (verbose_level() >= 2)
+      std::fprintf(stderr, "iga autotune d=%d n=%d R=%d: lock wait %.1f ms, %zu candidates "
+                   "timed in %.1f ms\n", t.d, t.n, t.R_max, 1e3 * (tl - tw), cand.size(),
+                   1e3 * (wall_seconds() - tl));
   }
   set_tile(t, best.first, best.second);
   std::lock_guard<std::mutex> lk(mu);

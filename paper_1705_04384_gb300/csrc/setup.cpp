@@ -9,6 +9,8 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -526,6 +528,19 @@ std::shared_mutex &device_mutex() {
   return mu;
 }
 
+int verbose_level() {
+  static const int v = [] {
+    const char *e = std::getenv("IGA_VERBOSE");
+    return e ? std::atoi(e) : 0;
+  }();
+  return v;
+}
+
+double wall_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
 int pdl_mask() {
   // measured on GB300 (3D n = 65 solves): programmatic dependent launch pays off for
   // the FD mode products (FP64 and tensor-core chains), is neutral for the operator
@@ -579,10 +594,17 @@ std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, dou
   f->p = p;
   f->shift = shift;
   f->scheme = scheme;
+  const double t0 = wall_seconds();
   build_basis_1d(*f);
   if (scheme == 1) build_wq_1d(*f);
+  const double t1 = wall_seconds();
   eigen_factors(*f, stream);
+  const double t2 = wall_seconds();
   upload_factor(*f, stream);
+  if (verbose_level() >= 2)
+    std::fprintf(stderr, "iga setup n_elem=%d p=%d: 1D basis %.1f ms, eigen-factors %.1f ms, "
+                 "upload %.1f ms\n", n_elem, p, 1e3 * (t1 - t0), 1e3 * (t2 - t1),
+                 1e3 * (wall_seconds() - t2));
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
   if (it != cache.end()) {

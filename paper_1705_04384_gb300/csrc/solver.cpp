@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
@@ -55,6 +56,7 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   prec = prec_;
   stream = s_;
   scheme = scheme_;
+  const double t0 = wall_seconds();
   ensure_kernels_loaded();
   bool has_wind = false;
   for (int l = 0; l < d; ++l) has_wind = has_wind || geom.wind[l] != 0.0;
@@ -78,11 +80,13 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   IGA_CUDA_TRY(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
   IGA_CUDA_TRY(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
 
+  const double t1 = wall_seconds();
   if (scheme == 1) {
     setup_wq();
   } else {
     setup_collocation_fields();
   }
+  const double t2 = wall_seconds();
   if (prec == IGA_PREC_FP64) {
     // the FP64 chain uses the folded eigen-order when one factor set with parity serves
     // every direction, else each direction's own eigenvalues
@@ -96,8 +100,13 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
     dinv32.alloc(N);
     launch_fd_diag_inverse(fac->d_lam.ptr, n, d, nullptr, dinv32.ptr, stream);
   }
+  const double t3 = wall_seconds();
   ensure_capacity(1);
   IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (verbose_level() >= 2)
+    std::fprintf(stderr, "iga setup d=%d n=%d p=%d prec=%d: factors %.1f ms, fields %.1f ms, "
+                 "diagonal %.1f ms, buffers and tensor-core context %.1f ms\n", d, n, p, prec,
+                 1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2), 1e3 * (wall_seconds() - t3));
 }
 
 // Geometry coefficient fields of the collocation operator and its pass plan.
@@ -440,7 +449,9 @@ SolveGraph &Ctx::graph_for(int R, int use_x0) {
   const auto key = std::make_pair(R, use_x0);
   auto it = graphs.find(key);
   if (it != graphs.end()) return it->second;
+  const double tw = wall_seconds();
   std::unique_lock<std::shared_mutex> dlk(device_mutex());
+  const double tl = wall_seconds();
   ws.R = R;
   SolveGraph sg;
   cudaStream_t s = cap_stream;
@@ -491,6 +502,9 @@ SolveGraph &Ctx::graph_for(int R, int use_x0) {
   sg.launches_fixed = (int)(c1 - c0);
   sg.launches_iter = (int)(g_launch_count - c1);
   IGA_CUDA_TRY(cudaGraphInstantiate(&sg.exec, sg.graph, 0));
+  if (verbose_level() >= 2)
+    std::fprintf(stderr, "iga solve graph d=%d n=%d R=%d: lock wait %.1f ms, capture and "
+                 "instantiation %.1f ms\n", d, n, R, 1e3 * (tl - tw), 1e3 * (wall_seconds() - tl));
   return graphs[key] = sg;
 }
 
