@@ -90,7 +90,7 @@ void Ctx::bicg_epilogue(cudaStream_t s) {
 SolveGraph &Ctx::bicg_graph_for(int use_x0) {
   auto it = bicg_graphs.find(use_x0);
   if (it != bicg_graphs.end()) return it->second;
-  std::unique_lock<std::shared_mutex> dlk(device_mutex());
+  std::unique_lock<DeviceLock> dlk(device_mutex());
   SolveGraph sg;
   cudaStream_t s = cap_stream;
   IGA_CUDA_TRY(cudaGraphCreate(&sg.graph, 0));

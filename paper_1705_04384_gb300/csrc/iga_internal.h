@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/iga_fd.h"
+#include "device_lock.h"
 
 namespace iga {
 
@@ -229,7 +230,7 @@ void span_basis(const std::vector<double> &t, int p, int mu, double x, double ou
 // hold it shared, so eigensolves of different shapes run concurrently but never while a
 // capture is in progress.  Every kernel of this library is loaded once per device before
 // the first problem is set up, so none of it is loaded during a capture.
-std::shared_mutex &device_mutex();
+DeviceLock &device_mutex();
 // IGA_VERBOSE=2 prints the duration of each setup phase to stderr (0 when unset)
 int verbose_level();
 double wall_seconds();

@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -630,7 +631,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
   std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
     const double tw = wall_seconds();
-    std::unique_lock<std::shared_mutex> dlk(device_mutex());
+    std::unique_lock<DeviceLock> dlk(device_mutex());
     const double tl = wall_seconds();
     cudaEvent_t e0, e1;
     IGA_CUDA_TRY(cudaEventCreate(&e0));
@@ -749,11 +750,13 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     // to the kernel, not to this problem, so a smaller per-problem value would
     // invalidate launches already captured by other problems.
     {
-      static bool smem_set[64] = {};
+      static std::atomic<bool> smem_set[64] = {};
       int dev = 0;
       IGA_CUDA_TRY(cudaGetDevice(&dev));
-      std::unique_lock<std::shared_mutex> lk(device_mutex());
-      if (dev >= 0 && dev < 64 && !smem_set[dev]) {
+      const bool done = dev >= 0 && dev < 64 && smem_set[dev].load(std::memory_order_acquire);
+      std::unique_lock<DeviceLock> lk(device_mutex(), std::defer_lock);
+      if (!done) lk.lock();  // once per device; later setups take no lock here
+      if (!done && dev >= 0 && dev < 64 && !smem_set[dev].load(std::memory_order_relaxed)) {
         const int max_smem = 1024 + kStages * (kTileM * 128 + 256 * 128);
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
@@ -768,7 +771,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             max_smem_p));
         }
-        smem_set[dev] = true;
+        smem_set[dev].store(true, std::memory_order_release);
       }
     }
     autotune(*t, s);

@@ -9,6 +9,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cmath>
@@ -333,7 +334,7 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   // (which may load library code), allocations, frees, solves -- runs with the device lock
   // held shared; the O(n^2 W) host work between them runs unlocked.
   std::vector<double> lam_u, VR;
-  std::shared_lock<std::shared_mutex> dlk(device_mutex());
+  std::shared_lock<DeviceLock> dlk(device_mutex());
   auto sh = std::make_unique<SolverHandle>();
   CUSOLVER_TRY(cusolverDnCreate(&sh->h));
   CUSOLVER_TRY(cusolverDnSetStream(sh->h, stream));
@@ -523,8 +524,8 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ device-wide lock
-std::shared_mutex &device_mutex() {
-  static std::shared_mutex mu;
+DeviceLock &device_mutex() {
+  static DeviceLock mu;
   return mu;
 }
 
@@ -555,11 +556,12 @@ int pdl_mask() {
 
 
 void ensure_kernels_loaded() {
-  static bool loaded[64] = {};
+  static std::atomic<bool> loaded[64] = {};
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
-  std::unique_lock<std::shared_mutex> lk(device_mutex());
-  if (dev < 0 || dev >= 64 || loaded[dev]) return;
+  if (dev >= 0 && dev < 64 && loaded[dev].load(std::memory_order_acquire)) return;
+  std::unique_lock<DeviceLock> lk(device_mutex());
+  if (dev < 0 || dev >= 64 || loaded[dev].load(std::memory_order_relaxed)) return;
   preload_kernels_fd64();
   preload_kernels_fd64_fma();
   preload_kernels_fd_tc();
@@ -567,7 +569,7 @@ void ensure_kernels_loaded() {
   preload_kernels_krylov();
   preload_kernels_bicgstab();
   preload_kernels_wq();
-  loaded[dev] = true;
+  loaded[dev].store(true, std::memory_order_release);
 }
 
 // ------------------------------------------------------------------ factor cache

@@ -450,7 +450,7 @@ SolveGraph &Ctx::graph_for(int R, int use_x0) {
   auto it = graphs.find(key);
   if (it != graphs.end()) return it->second;
   const double tw = wall_seconds();
-  std::unique_lock<std::shared_mutex> dlk(device_mutex());
+  std::unique_lock<DeviceLock> dlk(device_mutex());
   const double tl = wall_seconds();
   ws.R = R;
   SolveGraph sg;
