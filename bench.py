@@ -472,6 +472,12 @@ def run_ours(args):
     if fd_kind == "fold_fma":
         fd_prof = ("fd_fold_fma_3d_ne128.md", ("kernels_fd64_fma.cu",),
                    "fd_fold_fma_kernel (folded FD mode product, FP64 FMAs)")
+    elif fd_kind == "dense_mma":
+        # pencils without reflection parity (a wind): dense products, 2 n^{d+1} FLOPs each
+        fl = 2.0 * n4 ** (d + 1)
+        fd_prof = ("fd_fold_mma_3d_ne128.md", ("kernels_fd64.cu",),
+                   "fd_fold_mma_kernel, dense mode (FD mode product without parity, FP64 "
+                   "mma.sync m8n8k4)")
     else:
         fd_prof = ("fd_fold_mma_3d_ne128.md", ("kernels_fd64.cu",),
                    "fd_fold_mma_kernel (folded FD mode product, FP64 mma.sync m8n8k4)")

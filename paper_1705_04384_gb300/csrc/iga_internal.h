@@ -225,10 +225,10 @@ void span_basis(const std::vector<double> &t, int p, int mu, double x, double ou
 
 // Operations that touch device-wide state share one process-wide reader-writer lock, so
 // that setups on several host threads never disturb another thread's stream capture:
-// captures of solve graphs, kernel attribute changes and the tensor-core autotuner hold
-// it exclusively; the cuSOLVER eigensolves (which may load library code on first use)
-// hold it shared, so eigensolves of different shapes run concurrently but never while a
-// capture is in progress.  Every kernel of this library is loaded once per device before
+// captures of solve graphs and kernel attribute changes hold it exclusively; the cuSOLVER
+// eigensolves (which may load library code on first use) and the tensor-core autotuner
+// hold it shared, so those of different shapes run concurrently but never while a capture
+// is in progress.  Every kernel of this library is loaded once per device before
 // the first problem is set up, so none of it is loaded during a capture.
 DeviceLock &device_mutex();
 // IGA_VERBOSE=2 prints the duration of each setup phase to stderr (0 when unset)

@@ -630,8 +630,12 @@ static void autotune(TcFd &t, cudaStream_t s) {
     for (int nt : widths) cand.push_back({nt, 1});
   std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
+    // shared: the candidates are this library's preloaded kernels, launched on this problem's
+    // own stream, so the timing runs beside other threads' eigensolves and autotunes (timings
+    // stay exposed to whatever else runs on the GPU, as they always were to other solves), but
+    // never during a graph capture
     const double tw = wall_seconds();
-    std::unique_lock<DeviceLock> dlk(device_mutex());
+    std::shared_lock<DeviceLock> dlk(device_mutex());
     const double tl = wall_seconds();
     cudaEvent_t e0, e1;
     IGA_CUDA_TRY(cudaEventCreate(&e0));

@@ -137,9 +137,43 @@ namespace {
 struct SolverHandle {
   cusolverDnHandle_t h = nullptr;
   cusolverDnParams_t prm = nullptr;
-  ~SolverHandle() {
-    if (prm) cusolverDnDestroyParams(prm);
-    if (h) cusolverDnDestroy(h);
+};
+
+// One cuSOLVER handle per host thread and device, created on the thread's first
+// eigensolve there and kept for the life of the process (never destroyed: destroying one
+// frees device memory with a device-wide synchronisation, and at process exit the context
+// may already be gone).  Created and used with the device lock held shared.
+SolverHandle &thread_solver(cudaStream_t stream) {
+  thread_local SolverHandle hs[64];
+  int dev = 0;
+  IGA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error{IGA_ERR_CUDA, "device index out of range"};
+  SolverHandle &sh = hs[dev];
+  if (!sh.h) {
+    CUSOLVER_TRY(cusolverDnCreate(&sh.h));
+    CUSOLVER_TRY(cusolverDnCreateParams(&sh.prm));
+  }
+  CUSOLVER_TRY(cusolverDnSetStream(sh.h, stream));
+  return sh;
+}
+
+// Stream-ordered temporary device buffer of the eigensolves: cudaMallocAsync / cudaFreeAsync
+// on the setup's own stream, so that freeing it does not synchronise the whole device (a
+// cudaFree waits for every stream's work, the other setup threads' and the running solves').
+template <class T> struct StreamBuf {
+  T *ptr = nullptr;
+  cudaStream_t s;
+  StreamBuf(size_t n, cudaStream_t s_) : s(s_) {
+    if (cudaMallocAsync((void **)&ptr, std::max<size_t>(n, 1) * sizeof(T), s) != cudaSuccess) {
+      ptr = nullptr;
+      (void)cudaGetLastError();
+      throw Error{IGA_ERR_OOM, "cudaMallocAsync of " + std::to_string(n * sizeof(T)) + " bytes failed"};
+    }
+  }
+  StreamBuf(const StreamBuf &) = delete;
+  StreamBuf &operator=(const StreamBuf &) = delete;
+  ~StreamBuf() {
+    if (ptr) cudaFreeAsync(ptr, s);
   }
 };
 
@@ -174,15 +208,10 @@ double norm2_est(const std::vector<double> &A, int n) {
 static void eig_pencil(SolverHandle &sh, const std::vector<double> &Kc,
                        const std::vector<double> &Mc, int m, std::vector<double> &lam,
                        std::vector<double> &U, cudaStream_t stream) {
-  DevBuf<double> dM, dA, dVR, dW;
-  DevBuf<int64_t> dipiv;
-  DevBuf<int> dinfo;
-  dM.alloc((size_t)m * m);
-  dA.alloc((size_t)m * m);
-  dVR.alloc((size_t)m * m);
-  dW.alloc(2 * (size_t)m);
-  dipiv.alloc(m);
-  dinfo.alloc(1);
+  StreamBuf<double> dM((size_t)m * m, stream), dA((size_t)m * m, stream),
+      dVR((size_t)m * m, stream), dW(2 * (size_t)m, stream);
+  StreamBuf<int64_t> dipiv(m, stream);
+  StreamBuf<int> dinfo(1, stream);
   IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, Mc.data(), Mc.size() * 8, cudaMemcpyHostToDevice, stream));
   IGA_CUDA_TRY(cudaMemcpyAsync(dA.ptr, Kc.data(), Kc.size() * 8, cudaMemcpyHostToDevice, stream));
   auto check_info = [&](const char *what) {
@@ -196,8 +225,7 @@ static void eig_pencil(SolverHandle &sh, const std::vector<double> &Kc,
   CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh.h, sh.prm, m, m, CUDA_R_64F, dM.ptr, m, CUDA_R_64F,
                                            &dws, &hws));
   {
-    DevBuf<char> dbuf;
-    dbuf.alloc(std::max<size_t>(dws, 1));
+    StreamBuf<char> dbuf(std::max<size_t>(dws, 1), stream);
     std::vector<char> hbuf(std::max<size_t>(hws, 1));
     CUSOLVER_TRY(cusolverDnXgetrf(sh.h, sh.prm, m, m, CUDA_R_64F, dM.ptr, m, dipiv.ptr, CUDA_R_64F,
                                   dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
@@ -211,8 +239,7 @@ static void eig_pencil(SolverHandle &sh, const std::vector<double> &Kc,
                                           CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr, 1, CUDA_R_64F,
                                           dVR.ptr, m, CUDA_R_64F, &dws, &hws));
   {
-    DevBuf<char> dbuf;
-    dbuf.alloc(std::max<size_t>(dws, 1));
+    StreamBuf<char> dbuf(std::max<size_t>(dws, 1), stream);
     std::vector<char> hbuf(std::max<size_t>(hws, 1));
     CUSOLVER_TRY(cusolverDnXgeev(sh.h, sh.prm, CUSOLVER_EIG_MODE_NOVECTOR, CUSOLVER_EIG_MODE_VECTOR,
                                  m, CUDA_R_64F, dA.ptr, m, CUDA_C_64F, dW.ptr, CUDA_R_64F, nullptr,
@@ -330,15 +357,12 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
       Mc[i + (size_t)n * j] = mval(i, t);
       Kc[i + (size_t)n * j] = kval(i, t);
     }
-  // Every CUDA and cuSOLVER call of this function -- handle creation and destruction
-  // (which may load library code), allocations, frees, solves -- runs with the device lock
-  // held shared; the O(n^2 W) host work between them runs unlocked.
+  // Every CUDA and cuSOLVER call of this function -- the thread's handle creation on its
+  // first use (which may load library code), allocations, frees, solves -- runs with the
+  // device lock held shared; the O(n^2 W) host work between them runs unlocked.
   std::vector<double> lam_u, VR;
   std::shared_lock<DeviceLock> dlk(device_mutex());
-  auto sh = std::make_unique<SolverHandle>();
-  CUSOLVER_TRY(cusolverDnCreate(&sh->h));
-  CUSOLVER_TRY(cusolverDnSetStream(sh->h, stream));
-  CUSOLVER_TRY(cusolverDnCreateParams(&sh->prm));
+  SolverHandle *sh = &thread_solver(stream);
   eig_all(*sh, Kc, Mc, n, lam_u, VR, stream);
   dlk.unlock();
   std::vector<int> order(n);
@@ -366,43 +390,36 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   for (int i = 0; i < n; ++i) Ic[i + (size_t)n * i] = 1.0;
   std::vector<double> Xc((size_t)n * n);
   dlk.lock();
-  DevBuf<double> dM, dX;
-  DevBuf<int64_t> dipiv;
-  DevBuf<int> dinfo;
-  dM.alloc((size_t)n * n);
-  dX.alloc((size_t)n * n);
-  dipiv.alloc(n);
-  dinfo.alloc(1);
-  auto check_info = [&](const char *what) {
-    int info = 0;
-    IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  {  // the buffers are freed (stream-ordered) before the lock is released
+    sh = &thread_solver(stream);
+    StreamBuf<double> dM((size_t)n * n, stream), dX((size_t)n * n, stream);
+    StreamBuf<int64_t> dipiv(n, stream);
+    StreamBuf<int> dinfo(1, stream);
+    auto check_info = [&](const char *what) {
+      int info = 0;
+      IGA_CUDA_TRY(cudaMemcpyAsync(&info, dinfo.ptr, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      IGA_CUDA_TRY(cudaStreamSynchronize(stream));
+      if (info != 0)
+        throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
+    };
+    size_t dws = 0, hws = 0;
+    IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, MUc.data(), MUc.size() * 8, cudaMemcpyHostToDevice, stream));
+    IGA_CUDA_TRY(cudaMemcpyAsync(dX.ptr, Ic.data(), Ic.size() * 8, cudaMemcpyHostToDevice, stream));
+    CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh->h, sh->prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
+                                             &dws, &hws));
+    {
+      StreamBuf<char> dbuf(std::max<size_t>(dws, 1), stream);
+      std::vector<char> hbuf(std::max<size_t>(hws, 1));
+      CUSOLVER_TRY(cusolverDnXgetrf(sh->h, sh->prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
+                                    dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
+      check_info("getrf(MU)");
+    }
+    CUSOLVER_TRY(cusolverDnXgetrs(sh->h, sh->prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
+                                  CUDA_R_64F, dX.ptr, n, dinfo.ptr));
+    check_info("getrs(MU, I)");
+    IGA_CUDA_TRY(cudaMemcpyAsync(Xc.data(), dX.ptr, Xc.size() * 8, cudaMemcpyDeviceToHost, stream));
     IGA_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (info != 0)
-      throw Error{IGA_ERR_NOT_DIAGONALIZABLE, std::string(what) + " info=" + std::to_string(info)};
-  };
-  size_t dws = 0, hws = 0;
-  IGA_CUDA_TRY(cudaMemcpyAsync(dM.ptr, MUc.data(), MUc.size() * 8, cudaMemcpyHostToDevice, stream));
-  IGA_CUDA_TRY(cudaMemcpyAsync(dX.ptr, Ic.data(), Ic.size() * 8, cudaMemcpyHostToDevice, stream));
-  CUSOLVER_TRY(cusolverDnXgetrf_bufferSize(sh->h, sh->prm, n, n, CUDA_R_64F, dM.ptr, n, CUDA_R_64F,
-                                           &dws, &hws));
-  {
-    DevBuf<char> dbuf;
-    dbuf.alloc(std::max<size_t>(dws, 1));
-    std::vector<char> hbuf(std::max<size_t>(hws, 1));
-    CUSOLVER_TRY(cusolverDnXgetrf(sh->h, sh->prm, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr, CUDA_R_64F,
-                                  dbuf.ptr, dws, hbuf.data(), hws, dinfo.ptr));
-    check_info("getrf(MU)");
   }
-  CUSOLVER_TRY(cusolverDnXgetrs(sh->h, sh->prm, CUBLAS_OP_N, n, n, CUDA_R_64F, dM.ptr, n, dipiv.ptr,
-                                CUDA_R_64F, dX.ptr, n, dinfo.ptr));
-  check_info("getrs(MU, I)");
-  IGA_CUDA_TRY(cudaMemcpyAsync(Xc.data(), dX.ptr, Xc.size() * 8, cudaMemcpyDeviceToHost, stream));
-  IGA_CUDA_TRY(cudaStreamSynchronize(stream));
-  dM.release();
-  dX.release();
-  dipiv.release();
-  dinfo.release();
-  sh.reset();
   dlk.unlock();
   f.Vt.resize((size_t)n * n);
   for (int i = 0; i < n; ++i)
