@@ -151,6 +151,10 @@ struct Ctx {
   void ensure_capacity(int R);
   template <class Tin>
   void apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t s);
+  template <class Tin>
+  void operator_passes(IdxPtr<const Tin> in, int R, cudaStream_t s, IdxPtr<const double> (&ins)[6]);
+  template <class Tin>
+  void operator_and_pass1(IdxPtr<const Tin> in, int R, cudaStream_t s);
   void precond(IdxPtr<const double> in, double *out, int R, cudaStream_t s);  // FP64 result
   void ensure_ws(int max_iter, int R);
   void launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaStream_t s);

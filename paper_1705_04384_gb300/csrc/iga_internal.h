@@ -430,6 +430,17 @@ void launch_init_solve(const KrylovWs &ws, const double *b, const double *r0,
 // (the next basis vector), which may run beside the Givens kernel of the same step.
 void launch_cgs2_coeffs(const KrylovWs &ws, double *w, cudaStream_t s);
 void launch_cgs2_vector(const KrylovWs &ws, const double *w, cudaStream_t s);
+// Pass 2 alone, after the operator's last pass fused with pass 1 (launch_cgs_pass1_op).
+void launch_cgs2_pass2(const KrylovWs &ws, double *w, cudaStream_t s);
+template <class Tin> struct ContractArgsT;
+// The operator's final contraction (collocation) fused with CGS2 pass 1: w = the contraction
+// of the direction-0 band products with the geometry fields, and h1 = V^T w, on the
+// reduction passes' row partition.  Bitwise the same w and h1 as contract_pass_kernel
+// followed by cgs_pass1_kernel.
+void launch_cgs_pass1_op(const KrylovWs &ws, const ContractArgsT<double> &a, const BandDev &b,
+                         int n, double *w, cudaStream_t s);
+// IGA_FUSE_P1=0 keeps the operator's contraction and pass 1 as separate launches
+bool fuse_pass1();
 void launch_givens(const KrylovWs &ws, cudaGraphConditionalHandle cond, int has_cond,
                    cudaStream_t s);
 void launch_finish(const KrylovWs &ws, const double *x0, int use_x0, double *x, cudaStream_t s);

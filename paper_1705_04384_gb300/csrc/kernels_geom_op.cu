@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "fp_widen.h"
+#include "contract_point.cuh"
 #include "iga_internal.h"
 
 namespace iga {
@@ -411,13 +412,6 @@ void launch_band_pass_multi(const double *const *ins, int nin, double *const *ou
 // earlier passes) with the band of order[t] along direction 0 and the field coef[t].  The
 // kernel unrolls over the terms so that it indexes its parameters statically (no local
 // copy of the arrays).
-template <class Tin> struct ContractArgsT {
-  const Tin *src[kMaxFields];
-  int order[kMaxFields];
-  const double *coef[kMaxFields];
-  int nterm;
-};
-
 template <class Tin, int W>
 __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a, double *out,
                                                             unsigned N, FastDiv div1,
@@ -426,28 +420,13 @@ __global__ void __launch_bounds__(256) contract_pass_kernel(ContractArgsT<Tin> a
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const int c = (int)(i - fdiv(i, div1) * div1.d);         // coordinate along direction 0
     const unsigned ic = i - fdiv(i, divN1) * divN1.d;         // point index of one rhs
-    const int st = __ldg(b.start + c);
-    const int base = (int)i + (st - c);
-    double acc = 0.0;
-#pragma unroll
-    for (int t = 0; t < kMaxFields; ++t) {
-      if (t >= a.nterm) break;
-      const Tin *src = a.src[t] + base;
-      const int o = a.order[t];
-      const double *B = (o == 0 ? b.band0 : (o == 1 ? b.band1 : b.band2)) + c * W;
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < W; ++q) s = fma(__ldg(B + q), ld_val(src + q), s);
-      acc = fma(__ldg(a.coef[t] + ic), s, acc);
-    }
-    out[i] = acc;
+    out[i] = contract_point<Tin, W>(a, i, ic, c, b);
   }
 }
 
 template <class Tin>
-void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *terms, int nterm,
-                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
-                          int nrhs) {
+ContractArgsT<Tin> make_contract_args(IdxPtr<const Tin> const *ins, const ContractTerm *terms,
+                                      int nterm) {
   if (nterm < 0 || nterm > kMaxFields) throw Error{IGA_ERR_INVALID_ARG, "contraction terms"};
   ContractArgsT<Tin> a{};
   for (int t = 0; t < nterm; ++t) {
@@ -458,6 +437,16 @@ void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *term
     a.coef[t] = terms[t].coef;
   }
   a.nterm = nterm;
+  return a;
+}
+template ContractArgsT<double> make_contract_args<double>(IdxPtr<const double> const *,
+                                                          const ContractTerm *, int);
+
+template <class Tin>
+void launch_contract_pass(IdxPtr<const Tin> const *ins, const ContractTerm *terms, int nterm,
+                          double *out, int n1, int n2, int n3, const BandDev &b, cudaStream_t s,
+                          int nrhs) {
+  const ContractArgsT<Tin> a = make_contract_args<Tin>(ins, terms, nterm);
   const long long N = (long long)n1 * n2 * n3 * nrhs;
   if (N > kMaxIndex32) throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per operator pass"};
   const int threads = 256, blocks = grid_for(N, threads);

@@ -13,7 +13,9 @@
 // same for a right-hand side alone or among others.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
+#include "contract_point.cuh"
 #include "iga_internal.h"
 
 namespace iga {
@@ -437,6 +439,75 @@ __global__ void __launch_bounds__(kRT, 2) cgs_pass1_kernel(KrylovWs ws, const do
   }
 }
 
+// Pass 1 fused with the operator's last pass, for NV = nv <= 15 vectors: per row, w is
+// contracted (contract_point), stored, and dotted with the row's NV entries of V_r; the
+// same FMAs in the same order as contract_pass_kernel followed by pass1_fused.
+template <int W, int NV>
+__device__ __forceinline__ void pass1_op_fused(const KrylovWs &ws, int r,
+                                               const ContractArgsT<double> &a, const BandDev &b,
+                                               const FastDiv &divn, double *wr, long long lo,
+                                               long long hi, double *part, double (*red)[kJC]) {
+  constexpr int NA = (NV + kJC - 1) / kJC * kJC;
+  double acc[NA] = {};
+  const long long vs = (long long)ws.R * ws.N;
+  const double *__restrict__ v0 = Vvec(ws, 0, r);
+  const long long roff = (long long)r * ws.N;
+  for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
+    const int c = (int)((unsigned)i - fdiv((unsigned)i, divn) * divn.d);
+    const double u = contract_point<double, W>(a, roff + i, (unsigned)i, c, b);
+    wr[i] = u;
+    double bb[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) bb[j] = v0[i + j * vs];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = fma(bb[j], u, acc[j]);
+  }
+#pragma unroll
+  for (int c = 0; c < NA / kJC; ++c) {
+    double t[kJC];
+#pragma unroll
+    for (int q = 0; q < kJC; ++q) t[q] = acc[c * kJC + q];
+    block_store_partials(t, min(kJC, NV - c * kJC), c * kJC, part, gridDim.x, red);
+  }
+}
+
+// the operator's last pass (w for this block's rows of right-hand side r) fused with pass 1
+template <int W>
+__global__ void __launch_bounds__(kRT, 2)
+    cgs_pass1_op_kernel(KrylovWs ws, ContractArgsT<double> a, BandDev b, FastDiv divn,
+                        double *w) {
+  pdl_entry();
+  __shared__ double red[kWarps][kJC];
+  const int k = ws.st->k, nv = k + 1;
+  long long lo, hi;
+  row_range(ws.N, lo, hi);
+  for (int r = 0; r < ws.R; ++r) {
+    if (ws.rs[r].done) continue;
+    double *wr = w + (long long)r * ws.N;
+    double *part = ws.partials + r * ws.pstride;
+#define IGA_P1OP(NVV) \
+  case NVV: pass1_op_fused<W, NVV>(ws, r, a, b, divn, wr, lo, hi, part, red); break;
+    switch (nv) {
+      IGA_P1OP(1) IGA_P1OP(2) IGA_P1OP(3) IGA_P1OP(4) IGA_P1OP(5) IGA_P1OP(6) IGA_P1OP(7) IGA_P1OP(8) IGA_P1OP(9) IGA_P1OP(10) IGA_P1OP(11) IGA_P1OP(12) IGA_P1OP(13) IGA_P1OP(14) IGA_P1OP(15)
+      default: {
+        const long long roff = (long long)r * ws.N;
+        for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
+          const int c = (int)((unsigned)i - fdiv((unsigned)i, divn) * divn.d);
+          wr[i] = contract_point<double, W>(a, roff + i, (unsigned)i, c, b);
+        }
+        __syncthreads();  // the block's rows of w are complete (and visible) for the dots
+        for (int j0 = 0; j0 < nv; j0 += kJC)
+          chunk_dots(ws, r, j0, min(kJC, nv - j0), wr, lo, hi, part, red);
+      }
+    }
+#undef IGA_P1OP
+    if (!arrive_last(ws.counter + r)) continue;
+    last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 0, nullptr);
+    __syncthreads();
+    if (threadIdx.x == 0) ws.counter[r] = 0;
+  }
+}
+
 // pass 2: w_r -= V_r h1; h2 = V_r^T w_r -> H_r[0..k,k] += h2, y_r = h2; nu = ||w_r||^2;
 // H_r[k+1,k] = sqrt(nu - ||h2||^2), the norm of w_r - V_r h2 (V_r orthonormal), so
 // that pass 3 needs no reduction of its own.  After the first projection w_r is
@@ -520,6 +591,37 @@ void launch_cgs2_coeffs(const KrylovWs &ws, double *w, cudaStream_t s) {
   launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), (ws.max_iter + 1) * sizeof(double), s,
              ws, w);
   IGA_LAUNCH_CHECK();
+}
+
+void launch_cgs2_pass2(const KrylovWs &ws, double *w, cudaStream_t s) {
+  launch_pdl(kPdlKrylov, cgs_pass2_kernel, dim3(ws.nblk), dim3(kRT),
+             (ws.max_iter + 1) * sizeof(double), s, ws, w);
+  IGA_LAUNCH_CHECK();
+}
+
+void launch_cgs_pass1_op(const KrylovWs &ws, const ContractArgsT<double> &a, const BandDev &b,
+                         int n, double *w, cudaStream_t s) {
+  const FastDiv divn = make_fastdiv((unsigned)n);
+  const dim3 grid(ws.nblk);
+  switch (b.W) {
+#define IGA_P1OP_W(WW)                                                                      \
+  case WW:                                                                                   \
+    launch_pdl(kPdlKrylov, cgs_pass1_op_kernel<WW>, grid, dim3(kRT), 0, s, ws, a, b, divn, w); \
+    break;
+    IGA_P1OP_W(3) IGA_P1OP_W(4) IGA_P1OP_W(5) IGA_P1OP_W(6) IGA_P1OP_W(7)
+#undef IGA_P1OP_W
+    default:
+      throw Error{IGA_ERR_INVALID_ARG, "band width out of range"};
+  }
+  IGA_LAUNCH_CHECK();
+}
+
+bool fuse_pass1() {
+  static const bool on = [] {
+    const char *e = std::getenv("IGA_FUSE_P1");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 void launch_cgs2_vector(const KrylovWs &ws, const double *w, cudaStream_t s) {
@@ -741,6 +843,11 @@ void preload_kernels_krylov() {
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, init_finalize_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, scale_v0_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<3>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<4>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<5>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<6>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<7>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass2_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass3_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, givens_kernel));

@@ -13,6 +13,7 @@
 #include <cstring>
 
 #include "context.h"
+#include "contract_point.cuh"
 
 #include <type_traits>
 
@@ -205,6 +206,16 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t 
     run_wq<Tin>(wq_op, in, out, R, s);
     return;
   }
+  IdxPtr<const double> ins[6];
+  operator_passes<Tin>(in, R, s, ins);
+  launch_contract_pass<double>(ins, plan.terms, plan.nterm, out, n, n, d == 3 ? n : 1, band, s, R);
+}
+
+// The band passes of the collocation operator before its final contraction (which reads
+// ins): along direction d-1, then (3D) all second-direction passes in one launch.
+template <class Tin>
+void Ctx::operator_passes(IdxPtr<const Tin> in, int R, cudaStream_t s,
+                          IdxPtr<const double> (&ins)[6]) {
   double *TA[3], *TB[6];
   const size_t blk = (size_t)R * N;
   for (int q = 0; q < plan.nA; ++q) TA[q] = op_scratch.ptr + q * blk;
@@ -212,7 +223,6 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t 
   const int n3 = d == 3 ? n : 1;
   // first pass along the slowest direction (d-1) reads the input
   launch_band_pass<Tin>(in, TA, plan.ordA, plan.nA, d - 1, n, n, n3, band, s, R);
-  IdxPtr<const double> ins[6];
   if (d == 2) {
     for (int q = 0; q < plan.nA; ++q) ins[q] = plain_ptr<const double>(TA[q]);
   } else {
@@ -224,7 +234,22 @@ void Ctx::apply_operator(IdxPtr<const Tin> in, double *out, int R, cudaStream_t 
                              s, R);
     for (int q = 0; q < plan.nB; ++q) ins[q] = plain_ptr<const double>(TB[q]);
   }
-  launch_contract_pass<double>(ins, plan.terms, plan.nterm, out, n, n, n3, band, s, R);
+}
+
+// w = A z followed by CGS2 pass 1 (h1 = V^T w) of an Arnoldi step: for collocation the
+// operator's last pass and pass 1 run as one kernel (one launch and one read of w fewer).
+template <class Tin>
+void Ctx::operator_and_pass1(IdxPtr<const Tin> in, int R, cudaStream_t s) {
+  if (scheme == 1 || !fuse_pass1()) {
+    apply_operator<Tin>(in, w.ptr, R, s);
+    launch_cgs2_coeffs(ws, w.ptr, s);
+    return;
+  }
+  IdxPtr<const double> ins[6];
+  operator_passes<Tin>(in, R, s, ins);
+  launch_cgs_pass1_op(ws, make_contract_args<double>(ins, plan.terms, plan.nterm), band, n,
+                      w.ptr, s);
+  launch_cgs2_pass2(ws, w.ptr, s);
 }
 
 // Algorithmic FLOPs of one application of the operator to one vector, from the pass
@@ -249,6 +274,8 @@ double Ctx::operator_flops() const {
 
 template void Ctx::apply_operator<double>(IdxPtr<const double>, double *, int, cudaStream_t);
 template void Ctx::apply_operator<float>(IdxPtr<const float>, double *, int, cudaStream_t);
+template void Ctx::operator_and_pass1<double>(IdxPtr<const double>, int, cudaStream_t);
+template void Ctx::operator_and_pass1<float>(IdxPtr<const float>, int, cudaStream_t);
 
 // ------------------------------------------------------------------ FD (FP64)
 template <class Tout>
@@ -404,18 +431,17 @@ void Ctx::launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaSt
   const int *kptr = &ws.st->k;
   IdxPtr<const double> vk{ws.V, kptr, 0, blk};
   if (prec == IGA_PREC_NONE) {
-    apply_operator<double>(vk, w.ptr, R, s);
+    operator_and_pass1<double>(vk, R, s);
   } else if (prec == IGA_PREC_FP64) {
     IdxPtr<double> zk{(double *)ws.Z, kptr, 0, blk};
     fd_chain_fp64<double>(*this, vk, zk, R, s);
-    apply_operator<double>(IdxPtr<const double>{(const double *)ws.Z, kptr, 0, blk}, w.ptr, R, s);
+    operator_and_pass1<double>(IdxPtr<const double>{(const double *)ws.Z, kptr, 0, blk}, R, s);
   } else {
     if (!tc) throw Error{IGA_ERR_CUDA, "tensor-core FD context missing"};
     IdxPtr<float> zk{(float *)ws.Z, kptr, 0, blk};
     tc_fd_apply(*tc, vk, zk, R, s);
-    apply_operator<float>(IdxPtr<const float>{(const float *)ws.Z, kptr, 0, blk}, w.ptr, R, s);
+    operator_and_pass1<float>(IdxPtr<const float>{(const float *)ws.Z, kptr, 0, blk}, R, s);
   }
-  launch_cgs2_coeffs(ws, w.ptr, s);
   // the Givens update of column k needs only passes 1 and 2: it runs on a side stream
   // beside pass 3, and the step ends when both have finished
   IGA_CUDA_TRY(cudaEventRecord(fork_ev, s));

@@ -356,3 +356,56 @@ def test_operator_flop_count():
         fl_wq = P.operator_flops()
     with Problem(3, 6, 3, geometry="revolved", precision="fp64") as P:
         assert fl_wq > 4 * P.operator_flops() > 0
+
+
+FUSE_RUN = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1705_04384_gb300.api import Problem
+out = {}
+g = np.random.default_rng(5)
+for key, (d, ne, p, geo, prec, R, tol, mi) in enumerate((
+        (2, 30, 3, "annulus", "fp64", 1, 1e-8, 200),
+        (3, 10, 4, "revolved", "fp64", 1, 0.0, 22),      # 23 basis vectors: the chunked path
+        (3, 9, 3, "annulus", "fp64", 3, 1e-8, 200),      # right-hand sides finishing apart
+        (3, 12, 3, "annulus", "tf32", 2, 1e-8, 200),
+        (2, 40, 5, "annulus", "none", 1, 0.0, 18))):
+    with Problem(d, ne, p, geometry=geo, precision=prec) as P:
+        B = g.standard_normal((R, P.N))
+        B[0] *= 1e3  # different scales: different step counts
+        if R == 1:
+            x, info = P.solve(torch.from_numpy(B[0]).cuda(), tol=tol, max_iter=mi)
+            out[f"x{key}"] = x.cpu().numpy()
+            out[f"h{key}"] = info["hist"]
+        else:
+            X, info = P.solve_multi(torch.from_numpy(B).cuda(), tol=tol, max_iter=mi)
+            out[f"x{key}"] = X.cpu().numpy()
+            for r in range(R):
+                out[f"h{key}_{r}"] = info["hist"][r]
+np.savez(sys.argv[2], **out)
+print("ok")
+"""
+
+
+def test_fused_operator_pass1_is_bitwise_the_unfused_step(tmp_path):
+    """The Arnoldi step's fused kernel (the operator's last pass with CGS2 pass 1) does the
+    same FP64 operations in the same order as the two kernels it replaces: solutions and
+    residual histories are bitwise equal with IGA_FUSE_P1=0 (read once per process, hence
+    child processes) -- 2D and 3D, more than 15 basis vectors, right-hand sides that stop at
+    different steps, the TF32 form and the unpreconditioned solver."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fuse.py"
+    script.write_text(FUSE_RUN)
+    res = {}
+    for flag in ("1", "0"):
+        f = tmp_path / f"r{flag}.npz"
+        env = dict(os.environ, IGA_FUSE_P1=flag, PYTHONPATH=root)
+        r = subprocess.run([sys.executable, str(script), root, str(f)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+        res[flag] = dict(np.load(f))
+    assert res["1"].keys() == res["0"].keys()
+    for k in res["1"]:
+        assert np.array_equal(res["1"][k], res["0"][k]), k
