@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(kThreads)
 //                                 x_a - x_{n-1-a} (f = ne + a);
 //   inverse (DIR 1):  pe_a = sum_{k < ne} Bi[a][k] y_k,  po_a = sum_{k >= ne} Bi[a][k] y_k,
 //                     z_a = pe_a + po_a, z_{n-1-a} = pe_a - po_a (a < h), z_h = pe_h.
-// Both need n^2 / 2 FMAs per row instead of n^2 (the 1/sqrt(2) of the basis is folded
-// into Bf and Bi at setup).
+// Both need n^2 / 2 FMAs per row instead of n^2.  The fold uses plain sums and differences
+// and Bf, Bi hold the left halves of the rows of V^T and U as they are, so no 1/sqrt(2)
+// normalisation appears anywhere.
 //
 // The products run on the FP64 tensor path (mma.sync m8n8k4 .f64).  On GB300 it has the
 // FP64 rate of the CUDA cores (about 2 FMAs per clock per SM), but one warp instruction
