@@ -165,3 +165,24 @@ def test_wq_full_size_3d_revolved_ne64():
         bn, xn = b.cpu().numpy(), x.cpu().numpy()
         assert info["status"] == 0
         assert np.linalg.norm(bn - R.op(xn)) <= 1.05e-8 * np.linalg.norm(bn)
+
+
+@pytest.mark.parametrize("d,ne,p,geo,prec", [(2, 14, 3, "annulus", "fp64"),
+                                              (3, 5, 4, "revolved", "fp64"),
+                                              (3, 6, 3, "revolved", "tf32")])
+def test_wq_several_rhs_bitwise_alone_and_against_oracle(d, ne, p, geo, prec):
+    """Several right-hand sides in lockstep on a WQ problem: every pass of the matrix-free
+    operator, the fan-out to Q_ab times each derivative included, addresses each right-hand
+    side's slice. Each solution must equal the same right-hand side's solve alone bit for
+    bit, and (FP64) the oracle's GMRES iterate at a fixed step count to 1e-10."""
+    R = ref(d, ne, p, geo)
+    B = np.stack([_rand(R.N, 20 + s) * (10.0 ** s) for s in range(3)])
+    with _problem(d, ne, p, geo, prec) as P:
+        X, info = P.solve_multi(torch.from_numpy(B).cuda(), tol=0.0, max_iter=7)
+        X = X.cpu().numpy()
+        for r in range(3):
+            x1, i1 = P.solve(torch.from_numpy(B[r]).cuda(), tol=0.0, max_iter=7)
+            assert np.array_equal(x1.cpu().numpy(), X[r]), r
+            if prec == "fp64":
+                o = G.gmres(R.A, B[r], M=R.fd, tol=0.0, max_iter=7)
+                assert np.linalg.norm(X[r] - o["x"]) <= 1e-10 * np.linalg.norm(o["x"]), r
