@@ -29,6 +29,7 @@
 #include <tuple>
 
 #include "context.h"
+#include "fp_widen.h"
 
 namespace iga {
 
@@ -218,7 +219,7 @@ __device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c
           } else if (epi.kind == kOutBF16) {
             ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
           } else {
-            ((double *)epi.out)[o] = (double)x;
+            ((double *)epi.out)[o] = widen_f32(x);  // on the integer units (fp_widen.h)
           }
         }
       }

@@ -16,6 +16,7 @@
 #include <cstdlib>
 
 #include "contract_point.cuh"
+#include "fp_widen.h"
 #include "iga_internal.h"
 
 namespace iga {
@@ -760,6 +761,10 @@ __global__ void backsolve_kernel(KrylovWs ws) {
   }
 }
 
+__device__ __forceinline__ double z_val(double v) { return v; }
+// FP32 basis entries (precision form) widened on the integer units (fp_widen.h)
+__device__ __forceinline__ double z_val(float v) { return widen_f32(v); }
+
 template <class TZ>
 __global__ void update_x_kernel(KrylovWs ws, const TZ *__restrict__ Z,
                                 const double *__restrict__ x0, int use_x0,
@@ -773,7 +778,7 @@ __global__ void update_x_kernel(KrylovWs ws, const TZ *__restrict__ Z,
        i += (long long)gridDim.x * blockDim.x) {
     double s = use_x0 ? x0r[i] : 0.0;
     for (int j = 0; j < k; ++j)
-      s = fma(__ldg(y + j), (double)Z[((long long)j * ws.R + r) * ws.N + i], s);
+      s = fma(__ldg(y + j), z_val(Z[((long long)j * ws.R + r) * ws.N + i]), s);
     xr[i] = s;
   }
 }
