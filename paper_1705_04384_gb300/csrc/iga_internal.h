@@ -172,6 +172,7 @@ struct Factor1D {
   DevBuf<__nv_bfloat16> d_Vt16, d_U16;
   int kpad = 0;                 // padded leading dimension for the TC operands
   double cond_U = 0.0;
+  double setup_solver_s = 0.0;  // time in the eigen-factorisation's locked (cuSOLVER) parts
   // Folded form of the FD factors (eigenvectors even or odd under i -> n-1-i): the
   // eigen-index reordered [even | odd], Bf (n x n, forward, block diagonal in the
   // folded basis), Bi (ne x n, inverse, pairs a / n-1-a), eigenvalues in that order.

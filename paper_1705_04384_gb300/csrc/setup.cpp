@@ -181,7 +181,8 @@ template <class T> struct StreamBuf {
 double norm2_est(const std::vector<double> &A, int n) {
   std::vector<double> x(n, 1.0 / std::sqrt((double)n)), y(n), z(n);
   double s = 0.0, s_prev = -1.0;
-  for (int it = 0; it < 60 && std::fabs(s - s_prev) > 1e-12 * s; ++it) {
+  // the estimate feeds only the cond(U) <= 1e3 check (Remark 1): six digits are plenty
+  for (int it = 0; it < 60 && std::fabs(s - s_prev) > 1e-6 * s; ++it) {
     s_prev = s;
     for (int i = 0; i < n; ++i) {
       double a = 0.0;
@@ -361,10 +362,12 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
   // first use (which may load library code), allocations, frees, solves -- runs with the
   // device lock held shared; the O(n^2 W) host work between them runs unlocked.
   std::vector<double> lam_u, VR;
+  const double ts0 = wall_seconds();
   std::shared_lock<DeviceLock> dlk(device_mutex());
   SolverHandle *sh = &thread_solver(stream);
   eig_all(*sh, Kc, Mc, n, lam_u, VR, stream);
   dlk.unlock();
+  f.setup_solver_s = wall_seconds() - ts0;
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam_u[a] < lam_u[b]; });
@@ -389,6 +392,7 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
     }
   for (int i = 0; i < n; ++i) Ic[i + (size_t)n * i] = 1.0;
   std::vector<double> Xc((size_t)n * n);
+  const double ts1 = wall_seconds();
   dlk.lock();
   {  // the buffers are freed (stream-ordered) before the lock is released
     sh = &thread_solver(stream);
@@ -421,6 +425,7 @@ static void eigen_factors(Factor1D &f, cudaStream_t stream) {
     IGA_CUDA_TRY(cudaStreamSynchronize(stream));
   }
   dlk.unlock();
+  f.setup_solver_s += wall_seconds() - ts1;
   f.Vt.resize((size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) f.Vt[(size_t)i * n + j] = Xc[i + (size_t)n * j];
@@ -621,8 +626,9 @@ std::shared_ptr<Factor1D> get_factor(int n_elem, int p, cudaStream_t stream, dou
   const double t2 = wall_seconds();
   upload_factor(*f, stream);
   if (verbose_level() >= 2)
-    std::fprintf(stderr, "iga setup n_elem=%d p=%d: 1D basis %.1f ms, eigen-factors %.1f ms, "
-                 "upload %.1f ms\n", n_elem, p, 1e3 * (t1 - t0), 1e3 * (t2 - t1),
+    std::fprintf(stderr, "iga setup n_elem=%d p=%d: 1D basis %.1f ms, eigen-factors %.1f ms "
+                 "(cuSOLVER with the lock wait %.1f ms), upload %.1f ms\n", n_elem, p,
+                 1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * f->setup_solver_s,
                  1e3 * (wall_seconds() - t2));
   std::lock_guard<std::mutex> lk(mu);
   auto it = cache.find(key);
