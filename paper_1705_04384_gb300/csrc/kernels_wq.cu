@@ -30,10 +30,42 @@ template <> __device__ __forceinline__ double wq_ld<float>(const float *p) {
   return widen_f32(__ldg(p));
 }
 
+// sum_u band[u] src[u L] over the term's band width: WD > 0 the width as a template
+// argument (every term of a pass has the same width), fully unrolled; WD = 0 any width.
+template <int WD, class Tin>
+__device__ __forceinline__ double band_dot(const double *__restrict__ bd, const Tin *src,
+                                           unsigned L, int w) {
+  double s = 0.0;
+  if constexpr (WD > 0) {
+#pragma unroll
+    for (int u = 0; u < WD; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
+  } else {
+#pragma unroll 4
+    for (int u = 0; u < w; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
+  }
+  return s;
+}
+template <int WD, class Tin>
+__device__ __forceinline__ double band_dot_coef(const double *__restrict__ bd, const Tin *src,
+                                                const double *__restrict__ cf, unsigned L,
+                                                int w) {
+  double s = 0.0;
+  if constexpr (WD > 0) {
+#pragma unroll
+    for (int u = 0; u < WD; ++u)
+      s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L) * __ldg(cf + (long long)u * L), s);
+  } else {
+#pragma unroll 4
+    for (int u = 0; u < w; ++u)
+      s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L) * __ldg(cf + (long long)u * L), s);
+  }
+  return s;
+}
+
 // Output point o of one right-hand side = low + L (c + Dout high): low indexes the
 // directions faster than the pass, c the pass direction, high the slower ones; the
 // input rows of c are start[c] .. start[c] + width - 1 along the pass direction.
-template <class Tin>
+template <class Tin, int WD>
 __global__ void __launch_bounds__(256)
     wq_pass_kernel(WqPassArgs<Tin> a, unsigned Nout, unsigned L, unsigned Din, FastDiv divL,
                    FastDiv divD, long long in_per_rhs, long long out_per_rhs) {
@@ -49,12 +81,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int t = 0; t < kWqMaxTerms; ++t) {
         if (t >= a.nterm) break;
-        const int st = __ldg(a.start[t] + c), w = a.width[t];
+        const int st = __ldg(a.start[t] + c), w = WD > 0 ? WD : a.width[t];
         const double *bd = a.band[t] + (long long)c * w;
         const Tin *src = (a.in[t] ? a.in[t] : vin) + r * in_per_rhs + base + (long long)L * st;
-        double s = 0.0;
-#pragma unroll 4
-        for (int u = 0; u < w; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
+        const double s = band_dot<WD>(bd, src, L, w);
 #pragma unroll
         for (int k = 0; k < kWqMaxFan; ++k) {
           if (k >= a.nfan[t]) break;
@@ -73,19 +103,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int t = 0; t < kWqMaxTerms; ++t) {
       if (t >= a.nterm) break;
-      const int st = __ldg(a.start[t] + c), w = a.width[t];
+      const int st = __ldg(a.start[t] + c), w = WD > 0 ? WD : a.width[t];
       const double *bd = a.band[t] + (long long)c * w;
       const Tin *src = (a.in[t] ? a.in[t] : vin) + r * in_per_rhs + base + (long long)L * st;
       const double *cf = a.coef[t] ? a.coef[t] + base + (long long)L * st : nullptr;
-      double s = 0.0;
-      if (cf) {
-#pragma unroll 4
-        for (int u = 0; u < w; ++u)
-          s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L) * __ldg(cf + (long long)u * L), s);
-      } else {
-#pragma unroll 4
-        for (int u = 0; u < w; ++u) s = fma(__ldg(bd + u), wq_ld(src + (long long)u * L), s);
-      }
+      const double s = cf ? band_dot_coef<WD>(bd, src, cf, L, w) : band_dot<WD>(bd, src, L, w);
       acc += s;
       if (t + 1 == a.nterm || a.out_of[t + 1] != a.out_of[t]) {
         a.out[a.out_of[t]][r * out_per_rhs + o] = acc;
@@ -121,11 +143,28 @@ void launch_wq_pass(const WqPassArgs<Tin> &a, int dir, const int *ext_in, const 
   const long long Nout = L * Dout * H, Nin = L * Din * H;
   if (Nout * R > kMaxIndex32 || Nin * R > kMaxIndex32)
     throw Error{IGA_ERR_INVALID_ARG, "more than 2^31 - 1 values per weighted-quadrature pass"};
+  for (int t = 1; t < a.nterm; ++t)
+    if (a.width[t] != a.width[0])
+      throw Error{IGA_ERR_INVALID_ARG, "weighted-quadrature pass: terms of unequal width"};
   const int threads = 256;
   const int blocks = (int)std::min<long long>((Nout + threads - 1) / threads, 152LL * 16);
-  launch_pdl(kPdlOperator, wq_pass_kernel<Tin>, dim3(blocks, R), dim3(threads), 0, s, a,
-             (unsigned)Nout, (unsigned)L, (unsigned)Din, make_fastdiv((unsigned)L),
-             make_fastdiv((unsigned)Dout), Nin, Nout);
+  const dim3 grid(blocks, R), block(threads);
+  const FastDiv divL = make_fastdiv((unsigned)L), divD = make_fastdiv((unsigned)Dout);
+  // the basis widths p + 1 and the rule widths of p = 2 .. 6 on at least 10 elements
+  // (3p + 2) as template arguments; any other width runs the generic loop
+  switch (a.width[0]) {
+#define IGA_WQ_W(WW)                                                                        \
+  case WW:                                                                                   \
+    launch_pdl(kPdlOperator, wq_pass_kernel<Tin, WW>, grid, block, 0, s, a, (unsigned)Nout,   \
+               (unsigned)L, (unsigned)Din, divL, divD, Nin, Nout);                            \
+    break;
+    IGA_WQ_W(3) IGA_WQ_W(4) IGA_WQ_W(5) IGA_WQ_W(6) IGA_WQ_W(7) IGA_WQ_W(8) IGA_WQ_W(11)
+    IGA_WQ_W(14) IGA_WQ_W(17) IGA_WQ_W(20)
+#undef IGA_WQ_W
+    default:
+      launch_pdl(kPdlOperator, wq_pass_kernel<Tin, 0>, grid, block, 0, s, a, (unsigned)Nout,
+                 (unsigned)L, (unsigned)Din, divL, divD, Nin, Nout);
+  }
   IGA_LAUNCH_CHECK();
 }
 
@@ -136,8 +175,12 @@ template void launch_wq_pass<float>(const WqPassArgs<float> &, int, const int *,
 
 void preload_kernels_wq() {
   cudaFuncAttributes at;
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&at, wq_pass_kernel<double>));
-  IGA_CUDA_TRY(cudaFuncGetAttributes(&at, wq_pass_kernel<float>));
+#define IGA_WQ_PRE(WW)                                                       \
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&at, wq_pass_kernel<double, WW>));       \
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&at, wq_pass_kernel<float, WW>));
+  IGA_WQ_PRE(0) IGA_WQ_PRE(3) IGA_WQ_PRE(4) IGA_WQ_PRE(5) IGA_WQ_PRE(6) IGA_WQ_PRE(7)
+  IGA_WQ_PRE(8) IGA_WQ_PRE(11) IGA_WQ_PRE(14) IGA_WQ_PRE(17) IGA_WQ_PRE(20)
+#undef IGA_WQ_PRE
 }
 
 }  // namespace iga

@@ -24,6 +24,9 @@ def main():
     ap.add_argument("--ne", type=int, default=64)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--geometry", default="annulus")
+    ap.add_argument("--scheme", default="collocation", choices=["collocation", "wq"],
+                    help="discretization: collocation (Sec. 2.2) or weighted-quadrature "
+                         "Galerkin (Sec. 2.3)")
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -38,7 +41,7 @@ def main():
         print(json.dumps({"op": "fp64peak", "gflops_dmma": r["dmma"], "gflops_fma": r["fma"],
                           "gflops_peak": r["peak"], "trials": a.reps}))
         return
-    P = Problem(a.d, a.ne, a.p, geometry=a.geometry, precision=a.precision)
+    P = Problem(a.d, a.ne, a.p, geometry=a.geometry, precision=a.precision, scheme=a.scheme)
     g = torch.Generator(device="cpu").manual_seed(0)
     b = torch.randn(P.N, dtype=torch.float64, generator=g).cuda()
     out = torch.empty_like(b)
@@ -68,7 +71,8 @@ def main():
         e1.record(s)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) * 1e3)
-    print(json.dumps({"op": a.op, "d": a.d, "ne": a.ne, "p": a.p, "n": P.n, "N": P.N,
+    print(json.dumps({"op": a.op, "scheme": a.scheme, "d": a.d, "ne": a.ne, "p": a.p, "n": P.n,
+                      "N": P.N,
                       "nrhs": a.nrhs,
                       "precision": a.precision, "us_mean": float(np.mean(times)),
                       "us_min": float(np.min(times)), "reps": a.reps}))
