@@ -81,13 +81,13 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="FP64 form only")
     ap.add_argument("--no-bicgstab", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="skip the 3d_annulus_ne64 (config 2) secondary line")
+                    help="skip the 3d_annulus_ne64 secondary line (3D annulus, 64 elements)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-form key of the default line")
     ap.add_argument("--workload", default="3d_ne128",
                     choices=["3d_ne128", "3d_ne64", "3d_revolved_ne64", "3d_wind_ne64",
                              "3d_wq_revolved_ne64", "batched", "served"],
-                    help="3d_ne128 (default bench line), 3d_ne64 (config 2), 3d_revolved_ne64 "
+                    help="3d_ne128 (default bench line), 3d_ne64 (64 elements), 3d_revolved_ne64 "
                          "(Sec. 5's revolved ring), 3d_wind_ne64 (Sec. 3.2 convection-diffusion), "
                          "batched (256 2D problems x 8 rhs), served (Poisson request stream)")
     ap.add_argument("--precision", default="tf32", help="preconditioner precision for the "
@@ -239,7 +239,7 @@ def operator_flops_per_dof(W_band, d=3):
 def oracle_problem(name, p):
     """The oracle's view of one problem of a named 3D workload: spaces, matrix-free A_C
     (the definition of eq. collocation applied through the Kronecker identity: the CSR
-    matrix of config 3 has about 8e8 non-zeros), the FD preconditioner and the rhs; for the
+    matrix of the 128-element 3D annulus has about 8e8 non-zeros), the FD preconditioner and the rhs; for the
     WQ workload the matrix-free A_wq (eq. WQapprox), the FD of P_wq and the WQ load."""
     from oracle import collocation as C, fd as F, geometry as Geo
     c = W.CONFIGS[name]
@@ -484,7 +484,7 @@ def run_ours(args):
     main["roofline"] = {
         "bound": "alu", "achieved": fl / t_launch / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
         "frac": fl / t_launch / 1e9 / fp64_peak,
-        # the committed counters are of the config-3 problem (n = 130): other sizes have none
+        # the committed counters are of the 128-element 3D annulus (n = 130): other sizes have none
         "traffic": (committed_traffic(fd_prof[0], fd_prof[1])
                     if WORKLOAD == "3d_annulus_ne128" and n4 == 130 else None),
         "kernel": fd_prof[2],
@@ -574,7 +574,7 @@ def run_ours(args):
             q["P"].close()
     probs = None
 
-    # config 2 (3d_annulus_ne64, FP64 and TF32), a secondary key
+    # the 64-element 3D annulus (3d_annulus_ne64, FP64 and TF32), a secondary key
     secondary = None
     if not args.no_secondary:
         secondary = run_secondary(args, dev, stream, flush)
@@ -620,7 +620,7 @@ def run_ours(args):
             "clocks": clk, "fp64_peak_gflops": fp64,
             "rel_err_vs_oracle": oracle_err,
             "mixed": out.get("tf32"), "bf16": out.get("bf16"), "bicgstab": bicg_out,
-            "config2_3d_annulus_ne64": secondary, "batched": batched}
+            "secondary_3d_annulus_ne64": secondary, "batched": batched}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -629,7 +629,7 @@ def run_ours(args):
 
 
 def run_secondary(args, dev, stream, flush, name="3d_annulus_ne64"):
-    """Config 2 (3D, 64 elements, p = 3, 4, 5): FP64 and TF32 forms, a few steps."""
+    """The 3D annulus with 64 elements (p = 3, 4, 5): FP64 and TF32 forms, a few steps."""
     import torch
     from paper_1705_04384_gb300.api import Problem
     c = W.CONFIGS[name]
