@@ -81,12 +81,17 @@ typedef struct {
 /* Precision of the preconditioner apply (Sec. 4 FD).  FP64: plain GMRES with an
  * FP64 FD.  TF32 / BF16: FD mode products on the tcgen05 tensor cores with FP32
  * accumulation inside flexible GMRES; operator, orthogonalization, least squares
- * and eigen-factors stay FP64.  NONE: no preconditioner (P = I).                    */
+ * and eigen-factors stay FP64.  TF32X3: the same with error-compensated TF32 -- every
+ * operand is split into a TF32 part and the TF32 rounding of its remainder, and each
+ * product sums hi*hi + hi*lo + lo*hi in FP32 (three MMAs per step), which brings the FD
+ * close to FP32 accuracy (and the flexible GMRES close to the FP64 form's step count) for
+ * about the cost of the latency-bound TF32 products.  NONE: no preconditioner (P = I). */
 typedef enum {
   IGA_PREC_FP64 = 0,
   IGA_PREC_TF32 = 1,
   IGA_PREC_BF16 = 2,
-  IGA_PREC_NONE = 3
+  IGA_PREC_NONE = 3,
+  IGA_PREC_TF32X3 = 4
 } iga_precision;
 
 /* Discretization scheme of iga_setup_scheme.

@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import Geometry, check
 
 GEOM = {"identity": 0, "annulus": 1, "revolved": 2}
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3, "tf32x3": 4}
 FACTOR = {"tau": 0, "M": 1, "B1": 2, "K": 3, "lambda": 4, "U": 5, "Vt": 6}
 GRID = {"latency": 0, "throughput": 1}
 SCHEME = {"collocation": 0, "wq": 1}

@@ -52,7 +52,7 @@ iga_status iga_setup_scheme(int d, int n_elem, int p, const iga_geometry *geom, 
     if (p < 2 || p > iga::kMaxDeg) throw iga::Error{IGA_ERR_INVALID_ARG, "p must be in 2..6"};
     if (n_elem < 3 || n_elem > 4096)
       throw iga::Error{IGA_ERR_INVALID_ARG, "n_elem must be in 3..4096"};
-    if (precision < IGA_PREC_FP64 || precision > IGA_PREC_NONE)
+    if (precision < IGA_PREC_FP64 || precision > IGA_PREC_TF32X3)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad precision"};
     if (scheme != IGA_SCHEME_COLLOCATION && scheme != IGA_SCHEME_WQ_GALERKIN)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad discretization scheme"};

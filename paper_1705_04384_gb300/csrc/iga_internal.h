@@ -169,6 +169,7 @@ struct Factor1D {
   DevBuf<double> d_lam;
   DevBuf<double> d_Vt, d_U;     // FP64 FD operands (row-major, ld = n)
   DevBuf<float> d_Vt32, d_U32;  // TF32 FD operands (row-major, ld = kpad)
+  DevBuf<float> d_Vt32lo, d_U32lo;  // TF32 roundings of their remainders (the TF32X3 form)
   DevBuf<__nv_bfloat16> d_Vt16, d_U16;
   int kpad = 0;                 // padded leading dimension for the TC operands
   double cond_U = 0.0;
@@ -208,6 +209,10 @@ void launch_gemm_fp64_fold(int dir, IdxPtr<const double> A, const double *Bt, Id
 void launch_gemm_fp64_fold_fma(int dir, IdxPtr<const double> A, const double *BT,
                                IdxPtr<double> out, int M, int n, int ne, const double *dinv,
                                cudaStream_t s, int nrhs);
+// The precision forms whose FD runs on the tensor cores (TF32, BF16, error-compensated TF32).
+inline bool tensor_core_prec(int prec) {
+  return prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16 || prec == IGA_PREC_TF32X3;
+}
 // Whether the folded FP64 products of M rows of length n run on the FMA kernel (else on
 // mma.sync); IGA_FD64=fma|mma forces one.
 bool use_fold_fma(long long M, int n);

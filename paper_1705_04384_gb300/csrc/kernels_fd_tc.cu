@@ -1,5 +1,9 @@
 // FD solve (eq. FD2D / FD3D) with the mode products on the 5th-generation tensor
 // cores (tcgen05): TF32 or BF16 operands, FP32 accumulation in tensor memory.
+// Error-compensated TF32 (the TF32X3 precision): every operand x is held as two TF32
+// tensors, hi = tf32(x) and lo = tf32(x - hi), and each product accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (the lo * lo term, 2^-22 relative, is dropped): three
+// MMAs per K-step on twice the staged bytes, for products close to FP32 accuracy.
 //
 // Each mode product is the GEMM D[M x N] = A[M x K] * B[K x N] of the layout-rotating
 // scheme used by the FP64 path (A: activation rows with the contracted index
@@ -115,10 +119,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// KIND 0: TF32, 1: BF16, 2: split TF32 (each instruction a TF32 MMA)
 template <int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
                                           uint32_t accum) {
-  if constexpr (KIND == 0) {
+  if constexpr (KIND != 1) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
@@ -164,6 +169,7 @@ struct TcEpi {
   long long ostride;
   int kind;         // kOutF32 / kOutBF16 / kOutF64
   int tf32_round;   // round FP32 outputs to TF32 (operands of the next TF32 product)
+  float *out_lo;    // split TF32 operands: TF32 rounding of the remainder (nullptr: none)
   int n;            // extent of the fastest component of a row index
   int ld_out;       // stride of that component in the output
   int nmid;         // rows per right-hand side / n  (n^{d-2})
@@ -178,7 +184,9 @@ struct TcEpi {
 // next 16 columns are loaded before this chunk's stores: loaded next to each store they
 // waited behind it, a memory latency per column (a persistent CTA's second product, the one
 // with the diagonal, took three times as long as its first).  Called by all 32 lanes (the
-// TMEM load is warp-collective).
+// TMEM load is warp-collective).  SPLIT: an FP32 output that feeds the next split-TF32
+// product is stored as hi = tf32(x) at out and tf32(x - hi) at out_lo when out_lo is set.
+template <bool SPLIT = false>
 __device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c0, int N,
                                               int n_tile, const TcEpi &epi) {
   long long obase = 0;
@@ -215,7 +223,9 @@ __device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c
           if (dinv_row) x *= dv[j];
           const long long o = off + obase + cstride * col;
           if (epi.kind == kOutF32) {
-            ((float *)epi.out)[o] = epi.tf32_round ? round_tf32(x) : x;
+            const float hi = epi.tf32_round ? round_tf32(x) : x;
+            ((float *)epi.out)[o] = hi;
+            if (SPLIT && epi.out_lo) epi.out_lo[o] = round_tf32(x - hi);
           } else if (epi.kind == kOutBF16) {
             ((__nv_bfloat16 *)epi.out)[o] = __float2bfloat16_rn(x);
           } else {
@@ -231,10 +241,21 @@ __device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c
   }
 }
 
+// Ring depth of the one-tile kernel: kStages, or kStagesSplit for the split TF32 kind (four
+// tiles per stage: at n_tile = 256 two stages take 192 KB, the four-stage budget of the others).
+constexpr int kStagesSplit = 2;
+template <int KIND>
+__host__ __device__ constexpr int tc_ring_stages() {
+  return KIND == 2 ? kStagesSplit : kStages;
+}
+
+// mapA2 / mapB2: the lo parts of A and B for KIND 2 (not read by the other kinds).
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   int M, int N, int K, int n_tile, int tmem_cols, uint32_t idesc, TcEpi epi) {
+                   const __grid_constant__ CUtensorMap mapA2,
+                   const __grid_constant__ CUtensorMap mapB2, int M, int N, int K, int n_tile,
+                   int tmem_cols, uint32_t idesc, TcEpi epi) {
   pdl_entry();  // before any global access, TMEM allocation included
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kStages];
@@ -245,14 +266,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t a_bytes = kTileM * 128, b_bytes = (uint32_t)n_tile * 128;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kTileM, c0 = blockIdx.y * n_tile;
-  constexpr int kbox = KIND == 0 ? 32 : 64;  // elements per 128-byte row
-  constexpr int kmma = KIND == 0 ? 8 : 16;   // K per instruction (32 bytes)
+  constexpr int kbox = KIND == 1 ? 64 : 32;  // elements per 128-byte row
+  constexpr int kmma = KIND == 1 ? 16 : 8;   // K per instruction (32 bytes)
+  constexpr bool split = KIND == 2;
   const int nchunks = (K + kbox - 1) / kbox;
-  // the ring has min(kStages, nchunks) stages: a short contraction (K = n, two or three
+  // the ring has min(stages, nchunks) stages: a short contraction (K = n, two or three
   // 128-byte chunks at the usual n) takes less shared memory, so more CTAs share an SM
-  const int nstage = min(kStages, nchunks);
+  const int nstage = min(tc_ring_stages<KIND>(), nchunks);
   uint8_t *sA = smem;
   uint8_t *sB = smem + nstage * a_bytes;
+  // split kind: the lo tiles follow (every tile stays 1024-byte aligned: n_tile % 16 == 0)
+  uint8_t *sA2 = sB + nstage * b_bytes;
+  uint8_t *sB2 = sA2 + nstage * a_bytes;
+  constexpr uint32_t kTiles = split ? 2u : 1u;
 
   __shared__ int mma_failed;
   if (threadIdx.x == 0) {
@@ -278,9 +304,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         atomicExch(epi.err, 1);
         break;
       }
-      mbar_expect_tx(&full_bar[s], a_bytes + b_bytes);
+      mbar_expect_tx(&full_bar[s], kTiles * (a_bytes + b_bytes));
       tma_load_2d(sA + s * a_bytes, &mapA, &full_bar[s], c * kbox, m0);
       tma_load_2d(sB + s * b_bytes, &mapB, &full_bar[s], c * kbox, c0);
+      if constexpr (split) {
+        tma_load_2d(sA2 + s * a_bytes, &mapA2, &full_bar[s], c * kbox, m0);
+        tma_load_2d(sB2 + s * b_bytes, &mapB2, &full_bar[s], c * kbox, c0);
+      }
       ++issued;
     }
     // no copy may still be landing in shared memory when the CTA exits: wait (bounded)
@@ -299,9 +329,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int rem = K - c * kbox;
       const int ksteps = min(kbox / kmma, (rem + kmma - 1) / kmma);
       const uint32_t a0 = smem_u32(sA + s * a_bytes), b0 = smem_u32(sB + s * b_bytes);
-      for (int j = 0; j < ksteps; ++j)
+      const uint32_t a2 = smem_u32(sA2 + s * a_bytes), b2 = smem_u32(sB2 + s * b_bytes);
+      for (int j = 0; j < ksteps; ++j) {
+        // the correction terms first, the leading term last (all into one accumulator)
+        if constexpr (split) {
+          mma_issue<KIND>(tmem, sw128_desc(a0 + 32u * j), sw128_desc(b2 + 32u * j), idesc,
+                          (c > 0 || j > 0) ? 1u : 0u);
+          mma_issue<KIND>(tmem, sw128_desc(a2 + 32u * j), sw128_desc(b0 + 32u * j), idesc, 1u);
+        }
         mma_issue<KIND>(tmem, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc,
-                        (c > 0 || j > 0) ? 1u : 0u);
+                        (split || c > 0 || j > 0) ? 1u : 0u);
+      }
       mma_commit(&empty_bar[s]);
     }
     // committed on every path: done_bar completes once every MMA issued above has, so
@@ -320,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else {
     tc_fence_after();
     const int row = m0 + warp * 32 + lane;
-    tc_store_rows(tmem + ((uint32_t)(warp * 32) << 16), row, M, c0, N, n_tile, epi);
+    tc_store_rows<split>(tmem + ((uint32_t)(warp * 32) << 16), row, M, c0, N, n_tile, epi);
   }
   tc_fence_before();
   __syncthreads();
@@ -482,16 +520,20 @@ __global__ void __launch_bounds__(kTcpThreads, 1)
 }
 
 // FP64 vector (unpadded) -> TF32-rounded FP32 / BF16 tensor with padded fastest index.
+// out_lo (TF32 only; nullptr: none): tf32((float)x - hi), the split form's lo part.
 template <class T>
-__global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, unsigned N,
-                            FastDiv divn, int ld) {
+__global__ void pack_kernel(IdxPtr<const double> inp, T *__restrict__ out, float *__restrict__ out_lo,
+                            unsigned N, FastDiv divn, int ld) {
   pdl_entry();
   const double *in = inp.get();
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const unsigned q = fdiv(i, divn);
     const long long o = (long long)(i - q * divn.d) + (long long)ld * q;
     if constexpr (sizeof(T) == 4) {
-      out[o] = round_tf32((float)in[i]);
+      const float xf = (float)in[i];
+      const float hi = round_tf32(xf);
+      out[o] = hi;
+      if (out_lo) out_lo[o] = round_tf32(xf - hi);  // xf - hi is exact
     } else {
       out[o] = __float2bfloat16_rn((float)in[i]);
     }
@@ -508,17 +550,25 @@ struct TcFd {
   int persistent = 0, p_nstage = 0, p_cps = 0;
   size_t p_smem = 0;
   uint32_t idesc = 0;
+  bool split = false;  // error-compensated TF32: every operand as hi and lo TF32 tensors
   DevBuf<uint8_t> P0, Ta, Tb;
+  DevBuf<uint8_t> P0lo, Talo, Tblo;  // split only
   DevBuf<int> err;
   CUtensorMap mapP0{}, mapTa{}, mapTb{}, mapVt{}, mapU{};
+  CUtensorMap mapP0lo{}, mapTalo{}, mapTblo{}, mapVtlo{}, mapUlo{};  // split only
   const float *dinv32 = nullptr;
   const void *vt_dev = nullptr, *u_dev = nullptr;
+  const void *vt_lo_dev = nullptr, *u_lo_dev = nullptr;  // split only
+};
+
+// A GEMM operand: its tensor map and, for the split kind, the map of its lo part.
+struct TcOp {
+  const CUtensorMap *hi, *lo;
 };
 
 static void make_map(CUtensorMap &m, const void *base, int elem_bf16, long long n_inner,
                      long long rows, long long ld, int box_rows);
-static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi, int R,
-                 cudaStream_t s);
+static void gemm(TcFd &t, TcOp A, TcOp B, const TcEpi &epi, int R, cudaStream_t s);
 
 static int num_sms_tc() {
   int dev = 0, nsm = 0;
@@ -534,19 +584,25 @@ static int num_sms_tc() {
 // accumulators of tmem_cols columns each, 512 columns per SM) allow.
 static void set_tile(TcFd &t, int n_tile, int persistent = 0) {
   const bool bf = t.prec == IGA_PREC_BF16;
+  if (t.split && persistent) throw Error{IGA_ERR_UNSUPPORTED, "split TF32 runs on the one-tile kernel"};
   t.n_tile = n_tile;
   t.persistent = persistent;
   t.n_ntiles = (t.n + n_tile - 1) / n_tile;
   t.tmem_cols = 32;
   while (t.tmem_cols < n_tile) t.tmem_cols *= 2;
-  const int kbox = bf ? 64 : 32, nstage = std::min(kStages, (t.n + kbox - 1) / kbox);
-  t.smem = 1024 + (size_t)nstage * (kTileM * 128 + (size_t)n_tile * 128);
+  const int kbox = bf ? 64 : 32;
+  const int nstage = std::min(t.split ? kStagesSplit : kStages, (t.n + kbox - 1) / kbox);
+  t.smem = 1024 + (size_t)nstage * (t.split ? 2 : 1) * (kTileM * 128 + (size_t)n_tile * 128);
   // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
   const uint32_t fmt = bf ? 1u : 2u;
   t.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n_tile >> 3) << 17) |
             ((uint32_t)(kTileM >> 4) << 24);
   make_map(t.mapVt, t.vt_dev, bf, t.n, t.n, t.kpad, n_tile);
   make_map(t.mapU, t.u_dev, bf, t.n, t.n, t.kpad, n_tile);
+  if (t.split) {
+    make_map(t.mapVtlo, t.vt_lo_dev, 0, t.n, t.n, t.kpad, n_tile);
+    make_map(t.mapUlo, t.u_lo_dev, 0, t.n, t.n, t.kpad, n_tile);
+  }
   if (persistent) {
     const size_t stage = (size_t)kTileM * 128 + (size_t)n_tile * 128;
     t.p_nstage = (int)std::max<size_t>(2, std::min<size_t>(kTcpMaxStages, kTcpRingBytes / stage));
@@ -573,9 +629,10 @@ static int persistent_mode() {
   if (!e || !e[0]) return -1;
   return (e[0] == '1' || e[0] == '2') ? e[0] - '0' : 0;
 }
-static bool persistent_candidate(int R_max) {
+static bool persistent_candidate(const TcFd &t) {
+  if (t.split) return false;  // the persistent kernel has no split kind
   const int m = persistent_mode();
-  return m > 0 || (m < 0 && R_max >= 4);
+  return m > 0 || (m < 0 && t.R_max >= 4);
 }
 
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
@@ -625,9 +682,9 @@ static void autotune(TcFd &t, cudaStream_t s) {
   }
   // (column tile, persistent kernel)
   std::vector<std::pair<int, int>> cand;
-  if (persistent_mode() != 2)
+  if (persistent_mode() != 2 || t.split)
     for (int nt : widths) cand.push_back({nt, 0});
-  if (persistent_candidate(t.R_max))
+  if (persistent_candidate(t))
     for (int nt : widths) cand.push_back({nt, 1});
   std::pair<int, int> best = cand[0];
   if (cand.size() > 1) {
@@ -646,6 +703,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
       set_tile(t, cd.first, cd.second);
       TcEpi e{};
       e.kind = t.prec == IGA_PREC_BF16 ? kOutBF16 : kOutF32;
+      e.tf32_round = t.split ? 1 : 0;
       e.n = t.n;
       e.ld_out = t.kpad;
       e.nmid = t.M / t.n;
@@ -653,7 +711,10 @@ static void autotune(TcFd &t, cudaStream_t s) {
       auto chain_once = [&]() {
         for (int g = 0; g < 2 * t.d; ++g) {
           e.out = (g & 1) ? t.Tb.ptr : t.Ta.ptr;
-          gemm(t, (g & 1) ? t.mapTa : t.mapP0, g < t.d ? t.mapVt : t.mapU, e, t.R_max, s);
+          if (t.split) e.out_lo = (float *)((g & 1) ? t.Tblo.ptr : t.Talo.ptr);
+          const TcOp A = (g & 1) ? TcOp{&t.mapTa, &t.mapTalo} : TcOp{&t.mapP0, &t.mapP0lo};
+          const TcOp B = g < t.d ? TcOp{&t.mapVt, &t.mapVtlo} : TcOp{&t.mapU, &t.mapUlo};
+          gemm(t, A, B, e, t.R_max, s);
         }
       };
       chain_once();
@@ -730,6 +791,7 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     t->n = n;
     t->prec = precision;
     const bool bf = precision == IGA_PREC_BF16;
+    t->split = precision == IGA_PREC_TF32X3;
     t->esize = bf ? 2 : 4;
     t->kpad = f.kpad;
     long long M = 1;
@@ -738,18 +800,25 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
     t->R_max = R_max;
     t->vt_dev = bf ? (const void *)f.d_Vt16.ptr : (const void *)f.d_Vt32.ptr;
     t->u_dev = bf ? (const void *)f.d_U16.ptr : (const void *)f.d_U32.ptr;
+    t->vt_lo_dev = f.d_Vt32lo.ptr;
+    t->u_lo_dev = f.d_U32lo.ptr;
     const size_t bytes = (size_t)R_max * M * t->kpad * t->esize;
-    t->P0.alloc(bytes);
-    t->Ta.alloc(bytes);
-    t->Tb.alloc(bytes);
-    IGA_CUDA_TRY(cudaMemsetAsync(t->P0.ptr, 0, bytes, s));
-    IGA_CUDA_TRY(cudaMemsetAsync(t->Ta.ptr, 0, bytes, s));
-    IGA_CUDA_TRY(cudaMemsetAsync(t->Tb.ptr, 0, bytes, s));
+    // the padding columns are never written: zero them once (the maps read them as K)
+    for (DevBuf<uint8_t> *b : {&t->P0, &t->Ta, &t->Tb, &t->P0lo, &t->Talo, &t->Tblo}) {
+      if (!t->split && (b == &t->P0lo || b == &t->Talo || b == &t->Tblo)) continue;
+      b->alloc(bytes);
+      IGA_CUDA_TRY(cudaMemsetAsync(b->ptr, 0, bytes, s));
+    }
     t->err.alloc(1);
     IGA_CUDA_TRY(cudaMemsetAsync(t->err.ptr, 0, sizeof(int), s));
     make_map(t->mapP0, t->P0.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
     make_map(t->mapTa, t->Ta.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
     make_map(t->mapTb, t->Tb.ptr, bf, n, (long long)R_max * M, t->kpad, kTileM);
+    if (t->split) {
+      make_map(t->mapP0lo, t->P0lo.ptr, 0, n, (long long)R_max * M, t->kpad, kTileM);
+      make_map(t->mapTalo, t->Talo.ptr, 0, n, (long long)R_max * M, t->kpad, kTileM);
+      make_map(t->mapTblo, t->Tblo.ptr, 0, n, (long long)R_max * M, t->kpad, kTileM);
+    }
     t->dinv32 = dinv32;
     // One limit per device, the largest any tile shape needs: the attribute belongs
     // to the kernel, not to this problem, so a smaller per-problem value would
@@ -766,6 +835,9 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<0>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        static_assert(kStagesSplit * 2 <= kStages, "split ring within the one-tile budget");
+        IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<2>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
         {
           const int max_smem_p = (int)(1024 + kTcpRingBytes);
@@ -790,9 +862,9 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
 
 void destroy_tc_fd(TcFd *fd) { delete fd; }
 
-static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEpi &epi, int R,
-                 cudaStream_t s) {
+static void gemm(TcFd &t, TcOp Aop, TcOp Bop, const TcEpi &epi, int R, cudaStream_t s) {
   const int M = R * t.M;
+  const CUtensorMap &A = *Aop.hi, &B = *Bop.hi;
   if (t.persistent) {
     const long long ntiles = (long long)((M + kTileM - 1) / kTileM) * t.n_ntiles;
     const dim3 pgrid((unsigned)std::min<long long>(ntiles, (long long)num_sms_tc() * t.p_cps));
@@ -806,12 +878,15 @@ static void gemm(TcFd &t, const CUtensorMap &A, const CUtensorMap &B, const TcEp
     return;
   }
   dim3 grid((M + kTileM - 1) / kTileM, t.n_ntiles);
-  if (t.prec == IGA_PREC_BF16)
-    launch_pdl(kPdlTensorCore, tc_gemm_kernel<1>, grid, dim3(kTcThreads), t.smem, s, A, B, M,
-               t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
+  if (t.split)
+    launch_pdl(kPdlTensorCore, tc_gemm_kernel<2>, grid, dim3(kTcThreads), t.smem, s, A, B,
+               *Aop.lo, *Bop.lo, M, t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
+  else if (t.prec == IGA_PREC_BF16)
+    launch_pdl(kPdlTensorCore, tc_gemm_kernel<1>, grid, dim3(kTcThreads), t.smem, s, A, B, A, B,
+               M, t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
   else
-    launch_pdl(kPdlTensorCore, tc_gemm_kernel<0>, grid, dim3(kTcThreads), t.smem, s, A, B, M,
-               t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
+    launch_pdl(kPdlTensorCore, tc_gemm_kernel<0>, grid, dim3(kTcThreads), t.smem, s, A, B, A, B,
+               M, t.n, t.n, t.n_tile, t.tmem_cols, t.idesc, epi);
   IGA_LAUNCH_CHECK();
 }
 
@@ -827,10 +902,11 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, int 
   const FastDiv divn = make_fastdiv((unsigned)t.n);
   if (bf)
     launch_pdl(kPdlTensorCore, pack_kernel<__nv_bfloat16>, dim3(blocks), dim3(256), 0, s, in,
-               (__nv_bfloat16 *)t.P0.ptr, (unsigned)N, divn, t.kpad);
+               (__nv_bfloat16 *)t.P0.ptr, (float *)nullptr, (unsigned)N, divn, t.kpad);
   else
     launch_pdl(kPdlTensorCore, pack_kernel<float>, dim3(blocks), dim3(256), 0, s, in,
-               (float *)t.P0.ptr, (unsigned)N, divn, t.kpad);
+               (float *)t.P0.ptr, t.split ? (float *)t.P0lo.ptr : (float *)nullptr, (unsigned)N,
+               divn, t.kpad);
   IGA_LAUNCH_CHECK();
   TcEpi mid{};
   mid.kind = bf ? kOutBF16 : kOutF32;
@@ -839,29 +915,29 @@ static void chain(TcFd &t, IdxPtr<const double> in, const TcEpi &final_epi, int 
   mid.ld_out = t.kpad;
   mid.nmid = t.M / t.n;
   mid.err = t.err.ptr;
-  auto to = [&](DevBuf<uint8_t> &buf) {
+  auto to = [&](int which) {
     TcEpi e = mid;
-    e.out = buf.ptr;
+    e.out = which ? t.Tb.ptr : t.Ta.ptr;
+    if (t.split) e.out_lo = (float *)(which ? t.Tblo.ptr : t.Talo.ptr);
     return e;
   };
-  const CUtensorMap *cur = &t.mapP0;
-  DevBuf<uint8_t> *bufs[2] = {&t.Ta, &t.Tb};
-  const CUtensorMap *maps[2] = {&t.mapTa, &t.mapTb};
+  TcOp cur{&t.mapP0, &t.mapP0lo};
+  const TcOp maps[2] = {{&t.mapTa, &t.mapTalo}, {&t.mapTb, &t.mapTblo}};
   int which = 0;
   const int total = 2 * t.d;
   for (int g = 0; g < total; ++g) {
     const bool fwd = g < t.d;
-    const CUtensorMap &B = fwd ? t.mapVt : t.mapU;
+    const TcOp B = fwd ? TcOp{&t.mapVt, &t.mapVtlo} : TcOp{&t.mapU, &t.mapUlo};
     TcEpi e;
     if (g == total - 1) {
       e = final_epi;
     } else {
-      e = to(*bufs[which]);
+      e = to(which);
     }
     if (g == t.d - 1) {
       e.dinv = t.dinv32;
     }
-    gemm(t, *cur, B, e, R, s);
+    gemm(t, cur, B, e, R, s);
     if (g != total - 1) {
       cur = maps[which];
       which ^= 1;
@@ -902,6 +978,7 @@ void preload_kernels_fd_tc() {
   cudaFuncAttributes a;
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<0>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<1>));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_kernel<2>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<0>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, tc_gemm_persistent_kernel<1>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, pack_kernel<float>));

@@ -521,17 +521,26 @@ static void upload_factor(Factor1D &f, cudaStream_t s) {
   const int n = f.n;
   f.kpad = (n + 7) / 8 * 8;
   std::vector<float> vt32((size_t)n * f.kpad, 0.f), u32((size_t)n * f.kpad, 0.f);
+  std::vector<float> vt32lo((size_t)n * f.kpad, 0.f), u32lo((size_t)n * f.kpad, 0.f);
   std::vector<__nv_bfloat16> vt16((size_t)n * f.kpad, __float2bfloat16(0.f)),
       u16((size_t)n * f.kpad, __float2bfloat16(0.f));
+  // TF32 part and the TF32 rounding of the remainder (error-compensated TF32 form)
+  auto split = [](double v, float &hi, float &lo) {
+    hi = to_tf32((float)v);
+    lo = to_tf32((float)(v - (double)hi));
+  };
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) {
-      vt32[(size_t)i * f.kpad + j] = to_tf32((float)f.Vt[(size_t)i * n + j]);
-      u32[(size_t)i * f.kpad + j] = to_tf32((float)f.U[(size_t)i * n + j]);
-      vt16[(size_t)i * f.kpad + j] = __float2bfloat16((float)f.Vt[(size_t)i * n + j]);
-      u16[(size_t)i * f.kpad + j] = __float2bfloat16((float)f.U[(size_t)i * n + j]);
+      const size_t o = (size_t)i * f.kpad + j;
+      split(f.Vt[(size_t)i * n + j], vt32[o], vt32lo[o]);
+      split(f.U[(size_t)i * n + j], u32[o], u32lo[o]);
+      vt16[o] = __float2bfloat16((float)f.Vt[(size_t)i * n + j]);
+      u16[o] = __float2bfloat16((float)f.U[(size_t)i * n + j]);
     }
   upload(f.d_Vt32, vt32, s);
   upload(f.d_U32, u32, s);
+  upload(f.d_Vt32lo, vt32lo, s);
+  upload(f.d_U32lo, u32lo, s);
   upload(f.d_Vt16, vt16, s);
   upload(f.d_U16, u16, s);
   if (f.scheme == 1) {

@@ -64,7 +64,7 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   if (has_wind && scheme == 1)
     throw Error{IGA_ERR_INVALID_ARG, "the weighted-quadrature scheme takes no wind"};
   fac = get_factor(n_elem, p, stream, 0.0, scheme);
-  if (has_wind && (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16))
+  if (has_wind && tensor_core_prec(prec))
     throw Error{IGA_ERR_INVALID_ARG, "a wind requires precision FP64 or NONE"};
   // per-direction FD factors: the pencil (K + w_l B', M) of Sec. 3.2 (w_l = 0: Poisson)
   for (int l = 0; l < 3; ++l)
@@ -97,7 +97,7 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
     else
       launch_fd_diag_inverse3(facd[0]->d_lam.ptr, facd[1]->d_lam.ptr, facd[2]->d_lam.ptr, n, d,
                               dinv.ptr, nullptr, stream);
-  } else if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) {
+  } else if (tensor_core_prec(prec)) {
     dinv32.alloc(N);
     launch_fd_diag_inverse(fac->d_lam.ptr, n, d, nullptr, dinv32.ptr, stream);
   }
@@ -191,7 +191,7 @@ void Ctx::ensure_capacity(int R) {
   x0.alloc((size_t)R * N);
   w.alloc((size_t)R * N);
   r.alloc((size_t)R * N);
-  if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) {
+  if (tensor_core_prec(prec)) {
     tc.reset();
     R_max = 0;  // until the new tensor-core context exists
     tc.reset(make_tc_fd(d, n, prec, *fac, stream, R, dinv32.ptr));
@@ -364,7 +364,7 @@ void Ctx::ensure_ws(int max_iter, int R) {
   V.alloc((size_t)(mi + 1) * vecs);
   IGA_CUDA_TRY(cudaMemsetAsync(V.ptr, 0, (size_t)(mi + 1) * vecs * 8, stream));
   if (prec == IGA_PREC_FP64) Zd.alloc((size_t)mi * vecs);
-  if (prec == IGA_PREC_TF32 || prec == IGA_PREC_BF16) Zf.alloc((size_t)mi * vecs);
+  if (tensor_core_prec(prec)) Zf.alloc((size_t)mi * vecs);
   const long long hstride = (long long)(mi + 1) * mi;
   H.alloc((size_t)Rc * hstride);
   cs.alloc((size_t)Rc * (mi + 1));

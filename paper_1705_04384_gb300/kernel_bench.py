@@ -49,6 +49,7 @@ def main():
         P.prepare(a.nrhs, a.max_iter)
         B = torch.randn(a.nrhs, P.N, dtype=torch.float64, generator=g).cuda()
     s = torch.cuda.current_stream()
+    last = {}
 
     def call():
         if a.op == "fd":
@@ -56,9 +57,9 @@ def main():
         elif a.op == "operator":
             P.apply_operator(b, out=out)
         elif a.nrhs > 1:
-            P.solve_multi(B, tol=1e-8, max_iter=a.max_iter)
+            last["info"] = P.solve_multi(B, tol=1e-8, max_iter=a.max_iter)[1]
         else:
-            P.solve(b, tol=1e-8, max_iter=a.max_iter, out=out)
+            last["info"] = P.solve(b, tol=1e-8, max_iter=a.max_iter, out=out)[1]
 
     for _ in range(a.warmup):
         call()
@@ -75,7 +76,9 @@ def main():
                       "N": P.N,
                       "nrhs": a.nrhs,
                       "precision": a.precision, "us_mean": float(np.mean(times)),
-                      "us_min": float(np.min(times)), "reps": a.reps}))
+                      "us_min": float(np.min(times)), "reps": a.reps,
+                      "iters": (np.asarray(last["info"]["iters"]).tolist()
+                                if "info" in last else None)}))
     P.close()
 
 

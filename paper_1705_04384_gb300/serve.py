@@ -29,13 +29,15 @@ import torch
 from .api import Problem
 
 # bytes per DOF of a handle: fields, operator and FD scratch, vectors, and per Krylov
-# vector V (FP64) plus Z (FP32 for TF32/BF16, FP64 otherwise)
+# vector V (FP64) plus Z (FP32 for TF32/BF16/TF32X3, FP64 otherwise); the error-compensated
+# TF32 form holds its three FD scratch tensors twice (hi and lo parts)
 _FIXED_PER_DOF = {2: 8 * (5 + 3 + 2 + 5) + 3 * 4, 3: 8 * (9 + 9 + 2 + 5) + 3 * 4}
 
 
 def handle_bytes(d, N, max_iter, precision):
-    z = 4 if precision in ("tf32", "bf16") else (0 if precision == "none" else 8)
-    return int(N * (_FIXED_PER_DOF[d] + (max_iter + 1) * 8 + max_iter * z)) + (1 << 20)
+    z = 4 if precision in ("tf32", "bf16", "tf32x3") else (0 if precision == "none" else 8)
+    split = 3 * 4 if precision == "tf32x3" else 0
+    return int(N * (_FIXED_PER_DOF[d] + split + (max_iter + 1) * 8 + max_iter * z)) + (1 << 20)
 
 
 class Request:

@@ -65,6 +65,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     bad = Geometry(1, 2.0, 1.0)
     assert lib.iga_setup(2, 32, 3, ctypes.byref(bad), 0, None, ctypes.byref(h)) == 1
     assert lib.iga_setup(2, 32, 3, ctypes.byref(g), 7, None, ctypes.byref(h)) == 1
+    assert lib.iga_setup(2, 32, 3, ctypes.byref(g), 5, None, ctypes.byref(h)) == 1
+    assert lib.iga_setup(2, 32, 3, ctypes.byref(g), -1, None, ctypes.byref(h)) == 1
     assert lib.iga_setup(2, 32, 3, None, 0, None, ctypes.byref(h)) == 1
     assert lib.iga_dims(None, None, None) == 1
     assert lib.iga_solve(None, None, None, 0, 1e-8, 10, None, None, None) == 1
