@@ -241,12 +241,25 @@ __device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c
   }
 }
 
-// Ring depth of the one-tile kernel: kStages, or kStagesSplit for the split TF32 kind (four
-// tiles per stage: at n_tile = 256 two stages take 192 KB, the four-stage budget of the others).
-constexpr int kStagesSplit = 2;
-template <int KIND>
-__host__ __device__ constexpr int tc_ring_stages() {
-  return KIND == 2 ? kStagesSplit : kStages;
+// Ring depth of the one-tile kernel: min(kStages, K chunks).  The split TF32 kind stages four
+// tiles per chunk; its depth is chosen on the host (the autotuner times 2 stages and as many
+// as kSplitRingBytes hold: a deeper ring hides more TMA latency, a shallower one lets two
+// CTAs share an SM) and reaches the kernel through the dynamic shared-memory size, of which
+// the ring takes all but the 1024 alignment bytes.  The budget leaves room for the static
+// shared memory within the 227 KB a CTA may have.
+constexpr int kSplitRingBytes = 225 * 1024;
+__host__ __device__ constexpr int tc_stage_bytes(bool split, int n_tile) {
+  return (split ? 2 : 1) * (kTileM * 128 + n_tile * 128);
+}
+__host__ __device__ constexpr int tc_split_max_stages(int nchunks, int n_tile) {
+  const int s = nchunks < kStages ? nchunks : kStages;
+  const int fit = kSplitRingBytes / tc_stage_bytes(true, n_tile);
+  return s < fit ? s : fit;
+}
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+  uint32_t r;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
 }
 
 // mapA2 / mapB2: the lo parts of A and B for KIND 2 (not read by the other kinds).
@@ -272,7 +285,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nchunks = (K + kbox - 1) / kbox;
   // the ring has min(stages, nchunks) stages: a short contraction (K = n, two or three
   // 128-byte chunks at the usual n) takes less shared memory, so more CTAs share an SM
-  const int nstage = min(tc_ring_stages<KIND>(), nchunks);
+  int nstage = min(kStages, nchunks);
+  if constexpr (split)
+    nstage = min(nstage, (int)((dynamic_smem_bytes() - 1024u) / (2u * (a_bytes + b_bytes))));
   uint8_t *sA = smem;
   uint8_t *sB = smem + nstage * a_bytes;
   // split kind: the lo tiles follow (every tile stays 1024-byte aligned: n_tile % 16 == 0)
@@ -548,6 +563,7 @@ struct TcFd {
   size_t smem = 0;
   // persistent kernel (tc_gemm_persistent_kernel): ring depth, shared memory, CTAs per SM
   int persistent = 0, p_nstage = 0, p_cps = 0;
+  int ring = 0;  // stages of the one-tile kernel's ring
   size_t p_smem = 0;
   uint32_t idesc = 0;
   bool split = false;  // error-compensated TF32: every operand as hi and lo TF32 tensors
@@ -582,7 +598,8 @@ static int num_sms_tc() {
 // persistent: the tile loop of tc_gemm_persistent_kernel, with the deepest ring that fits
 // kTcpRingBytes and as many CTAs per SM as shared memory and tensor memory (two
 // accumulators of tmem_cols columns each, 512 columns per SM) allow.
-static void set_tile(TcFd &t, int n_tile, int persistent = 0) {
+// ring: stages of the split kind's ring (0: the most that fit); ignored by the other kinds.
+static void set_tile(TcFd &t, int n_tile, int persistent = 0, int ring = 0) {
   const bool bf = t.prec == IGA_PREC_BF16;
   if (t.split && persistent) throw Error{IGA_ERR_UNSUPPORTED, "split TF32 runs on the one-tile kernel"};
   t.n_tile = n_tile;
@@ -590,9 +607,14 @@ static void set_tile(TcFd &t, int n_tile, int persistent = 0) {
   t.n_ntiles = (t.n + n_tile - 1) / n_tile;
   t.tmem_cols = 32;
   while (t.tmem_cols < n_tile) t.tmem_cols *= 2;
-  const int kbox = bf ? 64 : 32;
-  const int nstage = std::min(t.split ? kStagesSplit : kStages, (t.n + kbox - 1) / kbox);
-  t.smem = 1024 + (size_t)nstage * (t.split ? 2 : 1) * (kTileM * 128 + (size_t)n_tile * 128);
+  const int kbox = bf ? 64 : 32, nchunks = (t.n + kbox - 1) / kbox;
+  int nstage = std::min(kStages, nchunks);
+  if (t.split) {
+    const int most = tc_split_max_stages(nchunks, n_tile);
+    nstage = ring > 0 ? std::min(ring, most) : most;
+  }
+  t.ring = nstage;
+  t.smem = 1024 + (size_t)nstage * tc_stage_bytes(t.split, n_tile);
   // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
   const uint32_t fmt = bf ? 1u : 2u;
   t.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n_tile >> 3) << 17) |
@@ -638,11 +660,16 @@ static bool persistent_candidate(const TcFd &t) {
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
 // candidate column tile -- the padded width split into the fewest parts of at most 256
 // columns and up to 5 more (narrower tiles put more CTAs on the GPU at the cost of
-// re-reading the row tile), and 256, 128, 64 for n > 256 -- and keep the fastest.  The choice is cached per (device, d, n, precision, R_max) so that every
-// problem of one shape runs the same kernels.
+// re-reading the row tile), and 256, 128, 64 for n > 256 -- and keep the fastest; for the
+// split TF32 kind each width with a 2-stage ring and with the deepest that fits.  The choice
+// is cached per (device, d, n, precision, R_max) so that every problem of one shape runs the
+// same kernels.
+struct TcTileChoice {
+  int n_tile, persistent, ring;
+};
 static void autotune(TcFd &t, cudaStream_t s) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> cache;
+  static std::map<std::tuple<int, int, int, int, int>, TcTileChoice> cache;
   int dev = 0;
   IGA_CUDA_TRY(cudaGetDevice(&dev));
   const auto key = std::make_tuple(dev, t.d, t.n, t.prec, t.R_max);
@@ -650,7 +677,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      set_tile(t, it->second.first, it->second.second);
+      set_tile(t, it->second.n_tile, it->second.persistent, it->second.ring);
       return;
     }
   }
@@ -680,13 +707,15 @@ static void autotune(TcFd &t, cudaStream_t s) {
       for (int nt : {256, 128, 64})
         if (std::find(widths.begin(), widths.end(), nt) == widths.end()) widths.push_back(nt);
   }
-  // (column tile, persistent kernel)
-  std::vector<std::pair<int, int>> cand;
+  std::vector<TcTileChoice> cand;
   if (persistent_mode() != 2 || t.split)
-    for (int nt : widths) cand.push_back({nt, 0});
+    for (int nt : widths) {
+      cand.push_back({nt, 0, 0});
+      if (t.split && tc_split_max_stages((t.n + 31) / 32, nt) > 2) cand.push_back({nt, 0, 2});
+    }
   if (persistent_candidate(t))
-    for (int nt : widths) cand.push_back({nt, 1});
-  std::pair<int, int> best = cand[0];
+    for (int nt : widths) cand.push_back({nt, 1, 0});
+  TcTileChoice best = cand[0];
   if (cand.size() > 1) {
     // shared: the candidates are this library's preloaded kernels, launched on this problem's
     // own stream, so the timing runs beside other threads' eigensolves and autotunes (timings
@@ -700,7 +729,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
     IGA_CUDA_TRY(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     for (const auto &cd : cand) {
-      set_tile(t, cd.first, cd.second);
+      set_tile(t, cd.n_tile, cd.persistent, cd.ring);
       TcEpi e{};
       e.kind = t.prec == IGA_PREC_BF16 ? kOutBF16 : kOutF32;
       e.tf32_round = t.split ? 1 : 0;
@@ -730,9 +759,9 @@ static void autotune(TcFd &t, cudaStream_t s) {
       }
       if (verbose_level() >= 1)
         std::fprintf(stderr,
-                     "iga autotune d=%d n=%d prec=%d R=%d n_tile=%d%s: %.1f us/apply\n", t.d,
-                     t.n, t.prec, t.R_max, cd.first, cd.second ? " persistent" : "",
-                     1000.f * ms / 3);
+                     "iga autotune d=%d n=%d prec=%d R=%d n_tile=%d%s ring=%d: %.1f us/apply\n",
+                     t.d, t.n, t.prec, t.R_max, cd.n_tile, cd.persistent ? " persistent" : "",
+                     cd.persistent ? t.p_nstage : t.ring, 1000.f * ms / 3);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -742,7 +771,7 @@ static void autotune(TcFd &t, cudaStream_t s) {
                    "timed in %.1f ms\n", t.d, t.n, t.R_max, 1e3 * (tl - tw), cand.size(),
                    1e3 * (wall_seconds() - tl));
   }
-  set_tile(t, best.first, best.second);
+  set_tile(t, best.n_tile, best.persistent, best.ring);
   std::lock_guard<std::mutex> lk(mu);
   cache[key] = best;
 }
@@ -836,9 +865,11 @@ TcFd *make_tc_fd(int d, int n, int precision, const Factor1D &f, cudaStream_t s,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-        static_assert(kStagesSplit * 2 <= kStages, "split ring within the one-tile budget");
+        static_assert(2 * 2 * (kTileM * 128 + 256 * 128) <= kSplitRingBytes,
+                      "two split stages of the widest tile fit the ring budget");
         IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<2>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          1024 + kSplitRingBytes));
         {
           const int max_smem_p = (int)(1024 + kTcpRingBytes);
           IGA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_persistent_kernel<0>,
