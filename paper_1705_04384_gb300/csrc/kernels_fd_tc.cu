@@ -241,12 +241,12 @@ __device__ __forceinline__ void tc_store_rows(uint32_t tl, int row, int M, int c
   }
 }
 
-// Ring depth of the one-tile kernel: min(kStages, K chunks).  The split TF32 kind stages four
-// tiles per chunk; its depth is chosen on the host (the autotuner times 2 stages and as many
-// as kSplitRingBytes hold: a deeper ring hides more TMA latency, a shallower one lets two
-// CTAs share an SM) and reaches the kernel through the dynamic shared-memory size, of which
-// the ring takes all but the 1024 alignment bytes.  The budget leaves room for the static
-// shared memory within the 227 KB a CTA may have.
+// Ring depth of the one-tile kernel: at most min(kStages, K chunks), and for the split TF32
+// kind (four tiles per chunk) at most what kSplitRingBytes holds.  The depth is chosen on the
+// host -- the autotuner times 2 stages and the most allowed: a deeper ring hides more TMA
+// latency, a shallower one lets more CTAs share an SM -- and reaches the kernel through the
+// dynamic shared-memory size, of which the ring takes all but the 1024 alignment bytes.  The
+// split budget leaves room for the static shared memory within the 227 KB a CTA may have.
 constexpr int kSplitRingBytes = 225 * 1024;
 __host__ __device__ constexpr int tc_stage_bytes(bool split, int n_tile) {
   return (split ? 2 : 1) * (kTileM * 128 + n_tile * 128);
@@ -282,18 +282,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr int kbox = KIND == 1 ? 64 : 32;  // elements per 128-byte row
   constexpr int kmma = KIND == 1 ? 16 : 8;   // K per instruction (32 bytes)
   constexpr bool split = KIND == 2;
+  constexpr uint32_t kTiles = split ? 2u : 1u;  // tiles of A (and of B) per stage
   const int nchunks = (K + kbox - 1) / kbox;
   // the ring has min(stages, nchunks) stages: a short contraction (K = n, two or three
   // 128-byte chunks at the usual n) takes less shared memory, so more CTAs share an SM
-  int nstage = min(kStages, nchunks);
-  if constexpr (split)
-    nstage = min(nstage, (int)((dynamic_smem_bytes() - 1024u) / (2u * (a_bytes + b_bytes))));
+  const int nstage = min(min(kStages, nchunks),
+                         (int)((dynamic_smem_bytes() - 1024u) / (kTiles * (a_bytes + b_bytes))));
   uint8_t *sA = smem;
   uint8_t *sB = smem + nstage * a_bytes;
   // split kind: the lo tiles follow (every tile stays 1024-byte aligned: n_tile % 16 == 0)
   uint8_t *sA2 = sB + nstage * b_bytes;
   uint8_t *sB2 = sA2 + nstage * a_bytes;
-  constexpr uint32_t kTiles = split ? 2u : 1u;
 
   __shared__ int mma_failed;
   if (threadIdx.x == 0) {
@@ -598,7 +597,8 @@ static int num_sms_tc() {
 // persistent: the tile loop of tc_gemm_persistent_kernel, with the deepest ring that fits
 // kTcpRingBytes and as many CTAs per SM as shared memory and tensor memory (two
 // accumulators of tmem_cols columns each, 512 columns per SM) allow.
-// ring: stages of the split kind's ring (0: the most that fit); ignored by the other kinds.
+// ring: stages of the one-tile kernel's ring (0: the most allowed); not used by the persistent
+// kernel, whose ring fills kTcpRingBytes.
 static void set_tile(TcFd &t, int n_tile, int persistent = 0, int ring = 0) {
   const bool bf = t.prec == IGA_PREC_BF16;
   if (t.split && persistent) throw Error{IGA_ERR_UNSUPPORTED, "split TF32 runs on the one-tile kernel"};
@@ -608,11 +608,8 @@ static void set_tile(TcFd &t, int n_tile, int persistent = 0, int ring = 0) {
   t.tmem_cols = 32;
   while (t.tmem_cols < n_tile) t.tmem_cols *= 2;
   const int kbox = bf ? 64 : 32, nchunks = (t.n + kbox - 1) / kbox;
-  int nstage = std::min(kStages, nchunks);
-  if (t.split) {
-    const int most = tc_split_max_stages(nchunks, n_tile);
-    nstage = ring > 0 ? std::min(ring, most) : most;
-  }
+  const int most = t.split ? tc_split_max_stages(nchunks, n_tile) : std::min(kStages, nchunks);
+  const int nstage = ring > 0 ? std::min(ring, most) : most;
   t.ring = nstage;
   t.smem = 1024 + (size_t)nstage * tc_stage_bytes(t.split, n_tile);
   // instruction descriptor: D = F32; A, B = TF32 (2) or BF16 (1); K-major; N >> 3; M >> 4
@@ -660,8 +657,8 @@ static bool persistent_candidate(const TcFd &t) {
 // Autotuner: time the 2d mode products of one FD apply (R_max right-hand sides) for each
 // candidate column tile -- the padded width split into the fewest parts of at most 256
 // columns and up to 5 more (narrower tiles put more CTAs on the GPU at the cost of
-// re-reading the row tile), and 256, 128, 64 for n > 256 -- and keep the fastest; for the
-// split TF32 kind each width with a 2-stage ring and with the deepest that fits.  The choice
+// re-reading the row tile), and 256, 128, 64 for n > 256 -- and keep the fastest; on the
+// one-tile kernel each width with a 2-stage ring and with the deepest allowed.  The choice
 // is cached per (device, d, n, precision, R_max) so that every problem of one shape runs the
 // same kernels.
 struct TcTileChoice {
@@ -711,7 +708,11 @@ static void autotune(TcFd &t, cudaStream_t s) {
   if (persistent_mode() != 2 || t.split)
     for (int nt : widths) {
       cand.push_back({nt, 0, 0});
-      if (t.split && tc_split_max_stages((t.n + 31) / 32, nt) > 2) cand.push_back({nt, 0, 2});
+      const int nchunks = (t.n + (t.prec == IGA_PREC_BF16 ? 63 : 31)) /
+                          (t.prec == IGA_PREC_BF16 ? 64 : 32);
+      const int most =
+          t.split ? tc_split_max_stages(nchunks, nt) : std::min(kStages, nchunks);
+      if (most > 2) cand.push_back({nt, 0, 2});
     }
   if (persistent_candidate(t))
     for (int nt : widths) cand.push_back({nt, 1, 0});
