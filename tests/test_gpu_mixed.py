@@ -108,9 +108,13 @@ def test_mixed_full_size_3d_ne128(prec, p):
     diff = np.linalg.norm(x - x64) / np.linalg.norm(x64)
     print(f"ne128 p={p} {prec}: iters {info['iters']} (fp64 {info64['iters']}), "
           f"relres {info['relres_true']:.2e}, |x - x_fp64|/|x_fp64| = {diff:.2e}")
-    assert diff <= 1e-7  # measured 1.3e-9 .. 1.6e-9
+    assert diff <= 1e-7  # measured 1.3e-9 .. 1.6e-9 (TF32X3: 5e-12)
     # the outer iteration wins back the lost precision with a modest count increase
     assert info["iters"] <= 2 * info64["iters"] + 5
+    if prec == "tf32x3":
+        # a near-FP32 preconditioner: the FP64 form's step count (measured 21 and 21; TF32 25)
+        assert info["iters"] <= info64["iters"] + 1
+        assert diff <= 1e-10
 
 
 def test_device_error_word_reports_timeout_and_handle_stays_usable():
