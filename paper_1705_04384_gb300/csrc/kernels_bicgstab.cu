@@ -64,14 +64,27 @@ __device__ bool barrive_last(unsigned int *counter) {
 }
 
 // In the last block: out[q] = sum_b partial[q * nblk + b] in block order (warp q sums
-// entry q); every thread of the block receives the sums.
+// entry q); every thread of the block receives the sums.  A lane loads its partials
+// (up to kBLdPer per round) before adding them in the same order, one L2 round trip per
+// 32 kBLdPer partials instead of one per 32.
+constexpr int kBLdPer = 10;
 __device__ void bfinal_sums(const double *partial, int cnt, double (&out)[3]) {
   __shared__ double res[3];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < cnt) {
+    const double *pq = partial + (long long)warp * gridDim.x;
+    const int nblk = (int)gridDim.x;
     double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32)
-      s += __ldcg(partial + (long long)warp * gridDim.x + b);
+    for (int b0 = 0; b0 < nblk; b0 += 32 * kBLdPer) {
+      double t[kBLdPer];
+#pragma unroll
+      for (int q = 0; q < kBLdPer; ++q) {
+        const int b = b0 + lane + 32 * q;
+        t[q] = b < nblk ? __ldcg(pq + b) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < kBLdPer; ++q) s += t[q];
+    }
     s = bwarp_sum(s);
     if (lane == 0) res[warp] = s;
   }

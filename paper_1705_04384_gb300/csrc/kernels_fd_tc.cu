@@ -704,9 +704,17 @@ static void autotune(TcFd &t, cudaStream_t s) {
       for (int nt : {256, 128, 64})
         if (std::find(widths.begin(), widths.end(), nt) == widths.end()) widths.push_back(nt);
   }
+  // IGA_TC_RING=<stages>: the one-tile kernel's only ring depth (with IGA_TC_TILE, pins the
+  // whole configuration for a profiler run)
+  const char *ring_env = std::getenv("IGA_TC_RING");
+  const int forced_ring = ring_env ? std::atoi(ring_env) : 0;
   std::vector<TcTileChoice> cand;
   if (persistent_mode() != 2 || t.split)
     for (int nt : widths) {
+      if (forced_ring > 0) {
+        cand.push_back({nt, 0, forced_ring});  // set_tile clamps it to what is allowed
+        continue;
+      }
       cand.push_back({nt, 0, 0});
       const int nchunks = (t.n + (t.prec == IGA_PREC_BF16 ? 63 : 31)) /
                           (t.prec == IGA_PREC_BF16 ? 64 : 32);

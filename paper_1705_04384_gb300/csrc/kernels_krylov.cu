@@ -121,17 +121,39 @@ __device__ __forceinline__ bool arrive_last(unsigned int *counter) {
 }
 
 // Sum partial[j*nblk + b] over b (fixed order) for j < cnt into out[j] (op 0: store,
-// 1: add); optionally also store the sums in out2[j].
+// 1: add); optionally also store the sums in out2[j].  tail (optional): the last row,
+// j = cnt - 1, is stored there instead (op and out2 do not apply to it), so that one call
+// reduces a pass's coefficients and its norm together.
+// A lane loads all of its partials of a row (up to kLdPer per round) before it adds them,
+// in the same order as one add per load: a row costs one L2 round trip per 32 kLdPer
+// partials.  Loaded and added one at a time they cost one round trip per 32, which made
+// the single last block's reduction the largest fixed cost of a pass (~20 us per CGS2
+// pass 2 at 2.2e6 rows with 304 blocks, two reductions in series).
+constexpr int kLdPer = 10;
 __device__ void last_block_reduce(const double *partial, int nblk, int cnt, double *out, int op,
-                                  double *out2) {
+                                  double *out2, double *tail = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j < cnt; j += kWarps) {
+    const double *pj = partial + (long long)j * nblk;
     double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += __ldcg(partial + (long long)j * nblk + b);
+    for (int b0 = 0; b0 < nblk; b0 += 32 * kLdPer) {
+      double t[kLdPer];
+#pragma unroll
+      for (int q = 0; q < kLdPer; ++q) {
+        const int b = b0 + lane + 32 * q;
+        t[q] = b < nblk ? __ldcg(pj + b) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < kLdPer; ++q) s += t[q];
+    }
     s = warp_sum(s);
     if (lane == 0) {
-      if (op == 0) out[j] = s; else out[j] += s;
-      if (out2) out2[j] = s;
+      if (tail && j == cnt - 1) {
+        *tail = s;
+      } else {
+        if (op == 0) out[j] = s; else out[j] += s;
+        if (out2) out2[j] = s;
+      }
     }
   }
 }
@@ -386,6 +408,73 @@ __device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r,
   }
 }
 
+// Pass 2 for 15 < NV = nv <= kStashMax vectors, still reading V_r once: the row's NV
+// entries are too many to keep in registers beside the NV + 1 accumulators, so the chain
+// w' = w - V_r h1 stores each entry it loads into this thread's column of shared memory
+// (stash[j * kRT + thread]) and the dots read them back from there.  The same FMAs in the
+// same order as subtract_proj followed by chunk_dots (the path for more vectors), and the
+// same partials, so both give bitwise the same w', h2 and norm.  Measured at 2.2e6 rows
+// (config 3), 16 vectors: the two-sweep path took 38 us more than 15 vectors in one sweep;
+// this one 12 us more (16..21 vectors: 26-32 us less than the two-sweep path).
+// 24 and more spill registers (NA = 32 accumulators); 22 and 23 measured slower than 16..21
+// (config 3: 23 vectors took 306 us against 226 us on the two-sweep path)
+constexpr int kStashMax = 21;
+template <int NV>
+__device__ __forceinline__ void pass2_stash(const KrylovWs &ws, int r,
+                                            const double *__restrict__ hs, double *w,
+                                            long long lo, long long hi, double *part,
+                                            double (*red)[kJC], double *stash) {
+  constexpr int NA = (NV + 1 + kJC - 1) / kJC * kJC;
+  double acc[NA] = {};
+  const long long vs = (long long)ws.R * ws.N;
+  const double *__restrict__ v0 = Vvec(ws, 0, r);
+  double *st = stash + threadIdx.x;
+  for (long long i = lo + threadIdx.x; i < hi; i += kRT) {
+    double x = w[i];
+    // loads in groups of kJC: the compiler barrier after each group's stash stores keeps
+    // it from hoisting all NV loads above the chain (NV + NA live doubles spilled)
+#pragma unroll
+    for (int j0 = 0; j0 < NV; j0 += kJC) {
+#pragma unroll
+      for (int j = j0; j < j0 + kJC && j < NV; ++j) {
+        const double b = v0[i + j * vs];
+        x = fma(-b, hs[j], x);
+        st[j * kRT] = b;
+      }
+      asm volatile("" ::: "memory");
+    }
+    w[i] = x;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) acc[j] = fma(st[j * kRT], x, acc[j]);
+    acc[NV] = fma(x, x, acc[NV]);
+  }
+#pragma unroll
+  for (int c = 0; c < NA / kJC; ++c) {
+    double a[kJC];
+#pragma unroll
+    for (int q = 0; q < kJC; ++q) a[q] = acc[c * kJC + q];
+    block_store_partials(a, min(kJC, NV + 1 - c * kJC), c * kJC, part, gridDim.x, red);
+  }
+}
+
+// Whether pass 2 takes pass2_stash for 15 < nv <= kStashMax (IGA_P2_STASH=0: the
+// two-sweep path, to check that both give the same bits).
+static bool p2_stash() {
+  static const bool on = [] {
+    const char *e = std::getenv("IGA_P2_STASH");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// Dynamic shared memory of pass 2: the max_iter + 1 coefficients and, when a step can
+// have more than 15 basis vectors, the stash of pass2_stash.
+static bool pass2_has_stash(int max_iter) { return p2_stash() && max_iter + 1 > 15; }
+static size_t pass2_smem(int max_iter, bool stash) {
+  return (size_t)(max_iter + 1) * sizeof(double) +
+         (stash ? (size_t)kStashMax * kRT * sizeof(double) : 0);
+}
+
 // Pass 1 for NV = nv <= 15 vectors: the dots of V_r with w over the block's rows in one
 // sweep (w read once), NV accumulators in registers.
 template <int NV>
@@ -514,10 +603,14 @@ __global__ void __launch_bounds__(kRT, 2)
 // that pass 3 needs no reduction of its own.  After the first projection w_r is
 // orthogonal to V_r to working accuracy, ||h2|| <= ||w_r|| times a small multiple of the
 // unit roundoff, and the difference loses no significant digits.
-__global__ void __launch_bounds__(kRT, 2) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w) {
+// stash: the dynamic shared memory holds pass2_stash's buffer (15 < nv <= kStashMax runs
+// pass2_stash; otherwise more than 15 vectors take the two-sweep path).
+__global__ void __launch_bounds__(kRT, 2) cgs_pass2_kernel(KrylovWs ws, double *__restrict__ w,
+                                                           int stash_on) {
   pdl_entry();
   __shared__ double red[kWarps][kJC];
-  extern __shared__ double hs[];  // max_iter + 1 coefficients
+  extern __shared__ double hs[];  // max_iter + 1 coefficients, then the stash (pass2_smem)
+  double *stash = hs + (ws.max_iter + 1);
   const int k = ws.st->k, nv = k + 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) ws.st->kv = k;
   long long lo, hi;
@@ -532,19 +625,22 @@ __global__ void __launch_bounds__(kRT, 2) cgs_pass2_kernel(KrylovWs ws, double *
     __syncthreads();
 #define IGA_P2(NVV) \
   case NVV: pass2_fused<NVV>(ws, r, hs, wr, lo, hi, part, red); break;
-    switch (nv) {
+#define IGA_P2S(NVV) \
+  case NVV: pass2_stash<NVV>(ws, r, hs, wr, lo, hi, part, red, stash); break;
+    switch (nv > 15 && !stash_on ? 0 : nv) {
       IGA_P2(1) IGA_P2(2) IGA_P2(3) IGA_P2(4) IGA_P2(5) IGA_P2(6) IGA_P2(7) IGA_P2(8) IGA_P2(9) IGA_P2(10) IGA_P2(11) IGA_P2(12) IGA_P2(13) IGA_P2(14) IGA_P2(15)
+      IGA_P2S(16) IGA_P2S(17) IGA_P2S(18) IGA_P2S(19) IGA_P2S(20) IGA_P2S(21)
       default:
         subtract_proj(ws, r, nv, hs, wr, lo, hi, wr);
         for (int j0 = 0; j0 <= nv; j0 += kJC)
           chunk_dots(ws, r, j0, min(kJC, nv + 1 - j0), wr, lo, hi, part, red, nv);
     }
 #undef IGA_P2
+#undef IGA_P2S
     if (!arrive_last(ws.counter + r)) continue;
     double *y = ws.y + r * (ws.max_iter + 2);
-    last_block_reduce(part, gridDim.x, nv, Hcol(ws, r, k), 1, y);
-    last_block_reduce(part + (long long)nv * gridDim.x, gridDim.x, 1, ws.scal + 8 * r + 2, 0,
-                      nullptr);
+    // the nv coefficients h2 and, as row nv, ||w_r||^2
+    last_block_reduce(part, gridDim.x, nv + 1, Hcol(ws, r, k), 1, y, ws.scal + 8 * r + 2);
     __syncthreads();
     if (threadIdx.x < 32) {
       double q = 0.0;
@@ -589,14 +685,16 @@ void launch_cgs2_coeffs(const KrylovWs &ws, double *w, cudaStream_t s) {
   const dim3 grid(ws.nblk);
   launch_pdl(kPdlKrylov, cgs_pass1_kernel, grid, dim3(kRT), 0, s, ws, (const double *)w);
   IGA_LAUNCH_CHECK();
-  launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), (ws.max_iter + 1) * sizeof(double), s,
-             ws, w);
+  const bool st = pass2_has_stash(ws.max_iter);
+  launch_pdl(kPdlKrylov, cgs_pass2_kernel, grid, dim3(kRT), pass2_smem(ws.max_iter, st), s, ws, w,
+             st ? 1 : 0);
   IGA_LAUNCH_CHECK();
 }
 
 void launch_cgs2_pass2(const KrylovWs &ws, double *w, cudaStream_t s) {
-  launch_pdl(kPdlKrylov, cgs_pass2_kernel, dim3(ws.nblk), dim3(kRT),
-             (ws.max_iter + 1) * sizeof(double), s, ws, w);
+  const bool st = pass2_has_stash(ws.max_iter);
+  launch_pdl(kPdlKrylov, cgs_pass2_kernel, dim3(ws.nblk), dim3(kRT), pass2_smem(ws.max_iter, st),
+             s, ws, w, st ? 1 : 0);
   IGA_LAUNCH_CHECK();
 }
 
@@ -854,6 +952,10 @@ void preload_kernels_krylov() {
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<6>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass1_op_kernel<7>));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass2_kernel));
+  // the largest Krylov workspace's coefficients plus the stash (once per device, before any
+  // capture: the attribute belongs to the kernel)
+  IGA_CUDA_TRY(cudaFuncSetAttribute(cgs_pass2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)pass2_smem(kMaxIter, true)));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, cgs_pass3_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, givens_kernel));
   IGA_CUDA_TRY(cudaFuncGetAttributes(&a, backsolve_kernel));

@@ -369,7 +369,8 @@ for key, (d, ne, p, geo, prec, R, tol, mi) in enumerate((
         (3, 10, 4, "revolved", "fp64", 1, 0.0, 22),      # 23 basis vectors: the chunked path
         (3, 9, 3, "annulus", "fp64", 3, 1e-8, 200),      # right-hand sides finishing apart
         (3, 12, 3, "annulus", "tf32", 2, 1e-8, 200),
-        (2, 40, 5, "annulus", "none", 1, 0.0, 18))):
+        (2, 40, 5, "annulus", "none", 1, 0.0, 18),
+        (2, 20, 3, "annulus", "fp64", 2, 0.0, 30))):   # up to 31 vectors: every pass-2 path
     with Problem(d, ne, p, geometry=geo, precision=prec) as P:
         B = g.standard_normal((R, P.N))
         B[0] *= 1e3  # different scales: different step counts
@@ -402,6 +403,29 @@ def test_fused_operator_pass1_is_bitwise_the_unfused_step(tmp_path):
     for flag in ("1", "0"):
         f = tmp_path / f"r{flag}.npz"
         env = dict(os.environ, IGA_FUSE_P1=flag, PYTHONPATH=root)
+        r = subprocess.run([sys.executable, str(script), root, str(f)], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+        res[flag] = dict(np.load(f))
+    assert res["1"].keys() == res["0"].keys()
+    for k in res["1"]:
+        assert np.array_equal(res["1"][k], res["0"][k]), k
+
+
+def test_stashed_pass2_is_bitwise_the_two_sweep_pass2(tmp_path):
+    """CGS2 pass 2 for 16..21 basis vectors keeps the row's entries of V in shared memory
+    instead of reading V twice; it does the same FMAs in the same order and forms the same
+    partials, so solutions and residual histories are bitwise those of the two-sweep path
+    (IGA_P2_STASH=0), for solves that pass through 1..15, 16..21 and 22..31 vectors."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "stash.py"
+    script.write_text(FUSE_RUN)
+    res = {}
+    for flag in ("1", "0"):
+        f = tmp_path / f"s{flag}.npz"
+        env = dict(os.environ, IGA_P2_STASH=flag, PYTHONPATH=root)
         r = subprocess.run([sys.executable, str(script), root, str(f)], env=env,
                            capture_output=True, text=True, timeout=600)
         assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
