@@ -85,13 +85,18 @@ typedef struct {
  * operand is split into a TF32 part and the TF32 rounding of its remainder, and each
  * product sums hi*hi + hi*lo + lo*hi in FP32 (three MMAs per step), which brings the FD
  * close to FP32 accuracy (and the flexible GMRES close to the FP64 form's step count) for
- * about the cost of the latency-bound TF32 products.  NONE: no preconditioner (P = I). */
+ * about the cost of the latency-bound TF32 products.  FP64_TC: the FP64 form (plain GMRES,
+ * FP64 FD to FP64 accuracy) with the FD mode products on the BF16 tensor cores by exact
+ * integer slice products (error-free splitting of Ozaki et al. 2012: 8 digits of 7 bits
+ * per value, exact FP32 sums, recombined in 128-bit integers); n <= 256, no wind.
+ * NONE: no preconditioner (P = I).                                                     */
 typedef enum {
   IGA_PREC_FP64 = 0,
   IGA_PREC_TF32 = 1,
   IGA_PREC_BF16 = 2,
   IGA_PREC_NONE = 3,
-  IGA_PREC_TF32X3 = 4
+  IGA_PREC_TF32X3 = 4,
+  IGA_PREC_FP64_TC = 5
 } iga_precision;
 
 /* Discretization scheme of iga_setup_scheme.
@@ -258,15 +263,17 @@ iga_status iga_launch_counts(iga_handle h, int *fixed, int *per_iteration);
 /* Which kernel runs the mode products of this handle's FD solve for nrhs right-hand sides
  * (eq. FD2D / FD3D): *kind = IGA_FD_KERNEL_FOLD_MMA (folded products, FP64 mma.sync),
  * IGA_FD_KERNEL_FOLD_FMA (folded products, FP64 FMAs), IGA_FD_KERNEL_DENSE_MMA (pencils
- * without reflection parity, FP64 mma.sync) or IGA_FD_KERNEL_TENSOR_CORE (tcgen05, the
- * TF32 / BF16 precision forms).  The FP64 choice depends on the size (more rows favour the
+ * without reflection parity, FP64 mma.sync), IGA_FD_KERNEL_TENSOR_CORE (tcgen05, the
+ * TF32 / BF16 / TF32X3 precision forms) or IGA_FD_KERNEL_FP64_SLICES (tcgen05 BF16 slice
+ * products, the FP64_TC form).  The FP64 choice depends on the size (more rows favour the
  * FMA kernel); IGA_FD64=fma|mma in the environment forces one.  Errors:
  * IGA_ERR_INVALID_ARG for a null handle or kind, nrhs < 1, or an unpreconditioned handle. */
 typedef enum {
   IGA_FD_KERNEL_FOLD_MMA = 0,
   IGA_FD_KERNEL_FOLD_FMA = 1,
   IGA_FD_KERNEL_DENSE_MMA = 2,
-  IGA_FD_KERNEL_TENSOR_CORE = 3
+  IGA_FD_KERNEL_TENSOR_CORE = 3,
+  IGA_FD_KERNEL_FP64_SLICES = 4
 } iga_fd_kernel_kind;
 iga_status iga_fd_kernel(iga_handle h, int nrhs, int *kind);
 
@@ -347,7 +354,10 @@ iga_status iga_prepare(iga_handle h, int nrhs, int max_iter);
  * one launch that keeps every SM's FP64 unit busy and returns the FLOPs it performs, so
  * that the caller can time it (CUDA events on `stream`) and obtain the device's FP64
  * ceiling, against which the FP64 kernels of this library are graded.
- *   kind   0: mma.sync m8n8k4 .f64 (the FP64 tensor path), 1: FP64 FMAs
+ *   kind   0: mma.sync m8n8k4 .f64 (the FP64 tensor path), 1: FP64 FMAs,
+ *          2: both at once, even warps on mma.sync and odd warps on FMAs,
+ *          3: both at once, every warp alternating its mma.sync and FMA chains
+ *          (kinds 2 and 3 show whether the two paths share the FP64 unit)
  *   reps   1..2^24 loop turns (each launch runs for about reps x 10 us on a GB300)
  *   stream cudaStream_t (NULL = default stream); asynchronous
  *   flops  (host, may be NULL) FLOPs of the launch
@@ -358,8 +368,8 @@ iga_status iga_fp64_probe(int kind, int reps, void *stream, double *flops);
  * -- the word a tensor-core FD kernel sets when one of its bounded waits runs out -- by a
  * host-to-device copy on the handle's stream, so that a test can check, without making
  * any device wait run out, that the next solve returns IGA_ERR_DEVICE_TIMEOUT, clears the
- * word, and that the handle stays usable.  Synchronous.  Only TF32 / BF16 handles have
- * the word.  Errors: INVALID_ARG (null handle, no tensor-core FD, solve in flight), CUDA. */
+ * word, and that the handle stays usable.  Synchronous.  Only the tensor-core forms
+ * (TF32, BF16, TF32X3, FP64_TC) have the word.  Errors: INVALID_ARG (null handle, no tensor-core FD, solve in flight), CUDA. */
 iga_status iga_test_set_device_error(iga_handle h, int code);
 
 /* Release everything the handle owns.  NULL is accepted. */

@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import Geometry, check
 
 GEOM = {"identity": 0, "annulus": 1, "revolved": 2}
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3, "tf32x3": 4}
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2, "none": 3, "tf32x3": 4, "fp64tc": 5}
 FACTOR = {"tau": 0, "M": 1, "B1": 2, "K": 3, "lambda": 4, "U": 5, "Vt": 6}
 GRID = {"latency": 0, "throughput": 1}
 SCHEME = {"collocation": 0, "wq": 1}
@@ -125,10 +125,10 @@ class Problem:
 
     def fd_kernel(self, nrhs=1):
         """Name of the kernel that runs this handle's FD mode products for nrhs
-        right-hand sides: fold_mma, fold_fma, dense_mma or tensor_core."""
+        right-hand sides: fold_mma, fold_fma, dense_mma, tensor_core or fp64_slices."""
         k = ctypes.c_int()
         check(self.lib.iga_fd_kernel(self.h, int(nrhs), ctypes.byref(k)), "iga_fd_kernel")
-        return ("fold_mma", "fold_fma", "dense_mma", "tensor_core")[k.value]
+        return ("fold_mma", "fold_fma", "dense_mma", "tensor_core", "fp64_slices")[k.value]
 
     def operator_flops(self):
         """Algorithmic FLOPs of one operator application (iga_operator_flops)."""
@@ -309,8 +309,8 @@ def solve_batched(problems, rhs, out, tol=1e-8, max_iter=200, history=False):
 
 def fp64_probe(kind=0, reps=1000, stream=None):
     """Enqueue one FP64 throughput probe launch (``iga_fp64_probe``: kind 0 = FP64
-    mma.sync, 1 = FP64 FMAs) on ``stream`` and return its FLOP count; time it with CUDA
-    events on the same stream."""
+    mma.sync, 1 = FP64 FMAs, 2 = both on alternate warps, 3 = both in every warp) on
+    ``stream`` and return its FLOP count; time it with CUDA events on the same stream."""
     lib = _lib.load()
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -320,13 +320,15 @@ def fp64_probe(kind=0, reps=1000, stream=None):
     return fl.value
 
 
-def measure_fp64_peak(reps=1000, trials=5, stream=None):
+def measure_fp64_peak(reps=1000, trials=5, stream=None, mixed=False):
     """FP64 ceiling of the current device in GFLOP/s: the best of ``trials`` timed launches
-    of each probe kind (after one warm-up launch each).  Returns dict(dmma, fma, peak)."""
+    of each probe kind (after one warm-up launch each).  Returns dict(dmma, fma, peak);
+    ``mixed`` adds the two probes that run both paths at once (split, interleaved)."""
     if stream is None:
         stream = torch.cuda.current_stream()
     out = {}
-    for kind, name in ((0, "dmma"), (1, "fma")):
+    kinds = ((0, "dmma"), (1, "fma")) + (((2, "split"), (3, "interleaved")) if mixed else ())
+    for kind, name in kinds:
         fp64_probe(kind, reps, stream)
         best = 0.0
         for _ in range(trials):

@@ -52,7 +52,7 @@ iga_status iga_setup_scheme(int d, int n_elem, int p, const iga_geometry *geom, 
     if (p < 2 || p > iga::kMaxDeg) throw iga::Error{IGA_ERR_INVALID_ARG, "p must be in 2..6"};
     if (n_elem < 3 || n_elem > 4096)
       throw iga::Error{IGA_ERR_INVALID_ARG, "n_elem must be in 3..4096"};
-    if (precision < IGA_PREC_FP64 || precision > IGA_PREC_TF32X3)
+    if (precision < IGA_PREC_FP64 || precision > IGA_PREC_FP64_TC)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad precision"};
     if (scheme != IGA_SCHEME_COLLOCATION && scheme != IGA_SCHEME_WQ_GALERKIN)
       throw iga::Error{IGA_ERR_INVALID_ARG, "bad discretization scheme"};
@@ -320,7 +320,8 @@ iga_status iga_fd_kernel(iga_handle h, int nrhs, int *kind) {
     const iga::Ctx &c = h->c;
     if (c.prec == IGA_PREC_NONE)
       throw iga::Error{IGA_ERR_INVALID_ARG, "unpreconditioned handle"};
-    if (c.prec != IGA_PREC_FP64) *kind = IGA_FD_KERNEL_TENSOR_CORE;
+    if (c.prec == IGA_PREC_FP64_TC) *kind = IGA_FD_KERNEL_FP64_SLICES;
+    else if (c.prec != IGA_PREC_FP64) *kind = IGA_FD_KERNEL_TENSOR_CORE;
     else if (!c.fold_ok) *kind = IGA_FD_KERNEL_DENSE_MMA;
     else
       *kind = iga::use_fold_fma((long long)nrhs * (c.N / c.n), c.n) ? IGA_FD_KERNEL_FOLD_FMA
@@ -377,10 +378,11 @@ iga_status iga_test_set_device_error(iga_handle h, int code) {
   return guarded([&]() -> iga_status {
     if (!h) throw iga::Error{IGA_ERR_INVALID_ARG, "null handle"};
     iga::Ctx &c = h->c;
-    if (!c.tc) throw iga::Error{IGA_ERR_INVALID_ARG, "the handle has no tensor-core FD"};
+    int *ew = c.tc ? iga::tc_fd_error_word(*c.tc)
+                   : c.f64tc ? iga::f64tc_error_word(*c.f64tc) : nullptr;
+    if (!ew) throw iga::Error{IGA_ERR_INVALID_ARG, "the handle has no tensor-core FD"};
     if (c.pending) throw iga::Error{IGA_ERR_INVALID_ARG, "a solve is in flight on this handle"};
-    IGA_CUDA_TRY(cudaMemcpyAsync(iga::tc_fd_error_word(*c.tc), &code, sizeof(int),
-                                 cudaMemcpyHostToDevice, c.stream));
+    IGA_CUDA_TRY(cudaMemcpyAsync(ew, &code, sizeof(int), cudaMemcpyHostToDevice, c.stream));
     IGA_CUDA_TRY(cudaStreamSynchronize(c.stream));
     return IGA_OK;
   });

@@ -24,6 +24,19 @@ struct TcFdDeleter {
   void operator()(TcFd *p) const { destroy_tc_fd(p); }
 };
 
+// FP64 FD on exact BF16 slice products (IGA_PREC_FP64_TC) -- kernels_fd_f64tc.cu
+struct F64TcFd;
+bool f64tc_supported(int n);
+F64TcFd *make_f64tc_fd(int d, int n, const Factor1D &f, cudaStream_t s, int R_max,
+                       const double *dinv);
+void f64tc_fd_apply(F64TcFd &fd, IdxPtr<const double> in, IdxPtr<double> out, int R,
+                    cudaStream_t s);
+void destroy_f64tc_fd(F64TcFd *fd);
+int *f64tc_error_word(F64TcFd &fd);
+struct F64TcFdDeleter {
+  void operator()(F64TcFd *p) const { destroy_f64tc_fd(p); }
+};
+
 struct OpPlan {
   int nA = 0;
   int ordA[3] = {0, 0, 0};
@@ -97,6 +110,7 @@ struct Ctx {
   DevBuf<double> op_scratch;  // (nA + nB) x R_max x N
   DevBuf<double> fd_scratch;  // 2 x R_max x N
   std::unique_ptr<TcFd, TcFdDeleter> tc;
+  std::unique_ptr<F64TcFd, F64TcFdDeleter> f64tc;
   DevBuf<double> b, x, x0, w, r;
 
   // Krylov workspace for (ws_max_iter, ws_R)

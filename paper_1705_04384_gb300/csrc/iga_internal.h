@@ -244,6 +244,7 @@ void ensure_kernels_loaded();
 void preload_kernels_fd64();
 void preload_kernels_fd64_fma();
 void preload_kernels_fd_tc();
+void preload_kernels_fd_f64tc();
 void preload_kernels_geom_op();
 void preload_kernels_krylov();
 void preload_kernels_bicgstab();

@@ -1,0 +1,523 @@
+// FP64 FD (eq. FD2D / FD3D) with the mode products on the BF16 tensor cores, exact to FP64
+// accuracy: the FP64 form's preconditioner at tensor-core speed (precision IGA_PREC_FP64_TC).
+//
+// Each mode product C = A B (A: R n^{d-1} x n activation rows, B: an n x n factor stored
+// K-contiguous, as in the other FD paths) is evaluated by error-free splitting into
+// integer slices (the scheme of Ozaki, Ogita, Oishi and Rump, "Error-free transformations
+// of matrix multiplication by using fast routines of matrix multiplication", Numer.
+// Algorithms 59, 2012), restated here for BF16 products with FP32 accumulation:
+//   * every row i of A gets a power of two 2^{e_i} > max_k |A_ik| and every row j of the
+//     stored factor (output column j) a power of two 2^{f_j} > max_k |B_kj|;
+//   * |A_ik| 2^{56 - e_i}, truncated to an integer F < 2^56, is written in base 2^7 as eight
+//     digits 0..127 (most significant first), which carry the sign of A_ik: A_ik =
+//     2^{e_i} sum_s d_s 2^{-7(s+1)} up to |A_ik| 2^{-56}; the same for B with digits d'_t;
+//   * a digit is an integer of at most 7 bits, exact in BF16; a product of two digits is
+//     below 2^14, and a sum of K <= 132 of them below 2^21.1, exact in FP32.  The pairs
+//     (s, t) with s + t = w accumulate into one FP32 accumulator G_w (w = 0..7), at most
+//     w + 1 <= 8 pairs: below 8 K 127^2 < 2^24 for K <= 130, so every G_w is the exact
+//     integer; at K = 131, 132 only G_7, which carries 2^-49 of the result's scale, can
+//     round (by at most 2^-63 of it);
+//   * C_ij = 2^{e_i + f_j - 63} sum_{w <= 7} G_w 2^{7 (7 - w)}, formed exactly in a 128-bit
+//     integer and rounded once to FP64.
+// The pairs with s + t > 7 are dropped; with the truncated digit tails the error of C_ij is
+// below 3 K 2^{-56} 2^{e_i + f_j} (about 5.4e-15 of 2^{e_i + f_j} at K = 130), the size of an
+// FP64 dot product's rounding.  No FP64 arithmetic is used except the FD diagonal's
+// multiplication: GB300's FP64 unit is shared by FMAs and the FP64 tensor path, and the
+// FP64 FD products run at its ceiling.
+//
+// Kernels: f64tc_split_kernel (one warp per row of A: the row's scale, then its 8 BF16 digit
+// slices; integer operations only) and f64tc_gemm_kernel (one 128-row x n_tile tile per CTA:
+// the factor's 8 slices stay in shared memory, the activation's slices stream through a
+// TMA ring, one thread issues the 36 slice-pair MMAs per 16-wide K-step into 8 TMEM
+// accumulators, four warps form the FP64 outputs in the layout-rotating order of the other
+// FD paths).  Every wait is bounded and reports through the context's device error word.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+
+#include "context.h"
+#include "tc_ptx.cuh"
+
+namespace iga {
+
+constexpr int kSlices = 8;        // base-2^7 digits per value
+constexpr int kDigitBits = 7;
+constexpr int kF64TcM = 128;      // rows per tile
+constexpr int kF64TcThreads = 128;
+constexpr int kF64TcMaxChunks = 4;  // n <= 256: the factor's slices fit in shared memory
+constexpr int kF64TcSmemBudget = 225 * 1024;  // ring + resident factor (plus 1024 alignment)
+constexpr uint32_t kF64TcABytes = kF64TcM * 128;  // one 64-wide K-chunk of one slice
+
+// ------------------------------------------------------------------ splitting
+// The BF16 bits of a digit d in [-127, 127]: 2^23 + 128 + d is exact in FP32 (its low byte
+// is d + 128), and subtracting 2^23 + 128 leaves d exactly; d has at most 7 significant
+// bits, so the upper half of the FP32 word is d in BF16.
+__device__ __forceinline__ unsigned short digit_bf16(int d) {
+  const float f = __int_as_float(0x4B000000 | (d + 128)) - 8388736.0f;
+  return (unsigned short)(__float_as_uint(f) >> 16);
+}
+
+// The 56-bit truncated magnitude |x| 2^{56 - e} (x < 2^e in magnitude), from the bits of x.
+__device__ __forceinline__ unsigned long long fixed56(unsigned long long bits, int e) {
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & ((1ull << 52) - 1);
+  int eeff = ex;
+  if (ex) m |= 1ull << 52; else eeff = 1;  // subnormal: no hidden bit, exponent of 1
+  const int sh = eeff - e - 1019;          // |x| = m 2^{eeff - 1075}; at most 3
+  if (sh >= 0) return m << sh;
+  return -sh >= 64 ? 0ull : m >> (-sh);
+}
+
+// One warp per row of length n of the FP64 input (row r at in + r n): the row's exponent e
+// (max |x| < 2^e) to rowexp[r] and the digits of every value to slices[s * sstride + r * kp
+// + k].  The padding columns k >= n are never read (the tensor maps end at n).
+__global__ void __launch_bounds__(256) f64tc_split_kernel(IdxPtr<const double> inp, int rows, int n,
+                                                          int kp, unsigned short *slices,
+                                                          long long sstride, int *rowexp) {
+  pdl_entry();
+  const double *in = inp.get();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (long long r = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows;
+       r += (long long)gridDim.x * wpb) {
+    const unsigned long long *x = (const unsigned long long *)(in + r * n);
+    // the largest magnitude: non-negative doubles order as their bit patterns
+    unsigned long long mx = 0;
+    for (int k = lane; k < n; k += 32) mx = max(mx, x[k] & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int emax = (int)(mx >> 52);
+    const int e = emax ? emax - 1022 : -1022;  // max < 2^e (zero and subnormal rows: -1022)
+    if (lane == 0) rowexp[r] = e;
+    unsigned short *o = slices + r * kp;
+    for (int k = lane; k < n; k += 32) {
+      const unsigned long long b = x[k];
+      const unsigned long long F = fixed56(b, e);
+      const bool neg = (b >> 63) != 0;
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) {
+        int dg = (int)((F >> (kDigitBits * (kSlices - 1 - s))) & 127ull);
+        o[s * sstride + k] = digit_bf16(neg ? -dg : dg);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ recombination
+// 2^E t for the 128-bit integer t, rounded to nearest (ties to even) once.
+__device__ __forceinline__ double scaled_i128_to_double(__int128 t, int E) {
+  if (t == 0) return 0.0;
+  const bool neg = t < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long mant;
+  int ex = msb;  // value = mant 2^{ex - 52} 2^E, mant in [2^52, 2^53)
+  if (msb > 52) {
+    const int sh = msb - 52;
+    mant = (unsigned long long)(u >> sh);
+    const unsigned __int128 rem = u - ((unsigned __int128)mant << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant >> 53) {
+        mant >>= 1;
+        ++ex;
+      }
+    }
+  } else {
+    mant = (unsigned long long)u << (52 - msb);
+  }
+  const int be = ex + E + 1023;
+  if (be <= 0 || be >= 2047) {  // outside the normal range (not met by the FD's values)
+    const double m = (double)mant;
+    return neg ? -ldexp(m, ex - 52 + E) : ldexp(m, ex - 52 + E);
+  }
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+// 8 columns of one TMEM lane per thread; the wait is in the same statement, so no use of
+// r can be scheduled before the load has completed.
+__device__ __forceinline__ void tmem_ld8_wait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+}
+
+struct F64TcEpi {
+  double *out;      // FP64 output base
+  const int *oidx;  // optional device step index: out += (*oidx) * ostride
+  long long ostride;
+  int n, ld_out, nmid;  // the rotation of tc_store_rows: row a + n (m + nmid r) ->
+                        // a + ld_out (m + nmid col + nmid N r)
+  const double *dinv;   // reciprocal FD diagonal in DOF order (nullptr: none)
+  int *err;
+};
+
+// ------------------------------------------------------------------ slice-product GEMM
+// grid (row tiles, column tiles), 128 threads.  Shared memory (after 1024-byte alignment):
+// the factor's slices [t][chunk] (n_tile rows x 128 bytes each), then the ring of the
+// activation's slice chunks (128 rows x 128 bytes each); the ring depth is what the dynamic
+// shared-memory size leaves.  TMEM: accumulator w at columns w n_tile.
+__global__ void __launch_bounds__(kF64TcThreads, 1)
+    f64tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                      const __grid_constant__ CUtensorMap mapB, int M, int N, int K, int n_tile,
+                      int tmem_cols, uint32_t idesc, const int *__restrict__ rowexp,
+                      const int *__restrict__ colexp, F64TcEpi epi) {
+  pdl_entry();
+  extern __shared__ uint8_t smem_raw[];
+  constexpr int kMaxRing = 8;
+  __shared__ __align__(8) uint64_t full_bar[kMaxRing];
+  __shared__ __align__(8) uint64_t empty_bar[kMaxRing];
+  __shared__ __align__(8) uint64_t b_bar;
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int mma_failed;
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kF64TcM, c0 = blockIdx.y * n_tile;
+  const int nchunks = (K + 63) / 64;
+  const uint32_t b_bytes = (uint32_t)n_tile * 128;
+  const uint32_t b_total = (uint32_t)(kSlices * nchunks) * b_bytes;
+  const int ring = min(kMaxRing, (int)((dynamic_smem_bytes() - 1024u - b_total) / kF64TcABytes));
+  uint8_t *sB = smem;
+  uint8_t *sA = smem + b_total;
+  const int nsteps = kSlices * nchunks;  // activation slice chunks, slice-major
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < ring; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], 1);
+    }
+    mbar_init(&b_bar, 1);
+    mbar_init(&done_bar, 1);
+    mma_failed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, (uint32_t)tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // the factor's slices for this column tile, once
+    mbar_expect_tx(&b_bar, b_total);
+    for (int t = 0; t < kSlices; ++t)
+      for (int c = 0; c < nchunks; ++c)
+        tma_load_3d(sB + (t * nchunks + c) * b_bytes, &mapB, &b_bar, c * 64, c0, t);
+    int issued = 0;
+    for (int g = 0; g < nsteps; ++g) {
+      const int q = g % ring, use = g / ring;
+      if (use > 0 && !mbar_wait(&empty_bar[q], (uint32_t)((use - 1) & 1))) {
+        atomicExch(epi.err, 11);
+        break;
+      }
+      mbar_expect_tx(&full_bar[q], kF64TcABytes);
+      tma_load_3d(sA + q * kF64TcABytes, &mapA, &full_bar[q], (g % nchunks) * 64, m0, g / nchunks);
+      ++issued;
+    }
+    // no copy may still be landing when the CTA exits
+    mbar_wait(&b_bar, 0);
+    for (int h = issued > ring ? issued - ring : 0; h < issued; ++h)
+      mbar_wait(&full_bar[h % ring], (uint32_t)((h / ring) & 1));
+  } else if (warp == 1 && lane == 0) {
+    bool ok = mbar_wait(&b_bar, 0);
+    if (!ok) {
+      atomicExch(epi.err, 12);
+      mma_failed = 1;
+    }
+    for (int g = 0; ok && g < nsteps; ++g) {
+      const int q = g % ring, use = g / ring;
+      if (!mbar_wait(&full_bar[q], (uint32_t)(use & 1))) {
+        atomicExch(epi.err, 13);
+        mma_failed = 1;
+        break;
+      }
+      tc_fence_after();
+      const int s = g / nchunks, c = g % nchunks;
+      const int ksteps = min(4, (K - c * 64 + 15) / 16);
+      const uint32_t a0 = smem_u32(sA + q * kF64TcABytes);
+      for (int t = 0; t + s < kSlices; ++t) {
+        const uint32_t b0 = smem_u32(sB + (t * nchunks + c) * b_bytes);
+        const uint32_t dt = tmem + (uint32_t)((s + t) * n_tile);
+        for (int j = 0; j < ksteps; ++j)  // accumulator s + t starts at s = 0, c = 0, j = 0
+          mma_issue<1>(dt, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc,
+                       (s > 0 || c > 0 || j > 0) ? 1u : 0u);
+      }
+      mma_commit(&empty_bar[q]);
+    }
+    // committed on every path: TMEM is released only after every issued MMA has completed
+    mma_commit(&done_bar);
+  }
+  __syncwarp();
+
+  const bool have = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0) ? 1 : 0) != 0;
+  if (!have) {
+    if (lane == 0) atomicExch(epi.err, 14);
+  } else if (!*(volatile int *)&mma_failed) {
+    tc_fence_after();
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    long long obase = 0;
+    const double *dinv_row = nullptr;
+    int erow = 0;
+    if (row < M) {
+      const int a = row % epi.n, rest = row / epi.n;
+      const int m = rest % epi.nmid, rr = rest / epi.nmid;
+      obase = (long long)a + (long long)epi.ld_out * (m + (long long)epi.nmid * N * rr);
+      if (epi.dinv) dinv_row = epi.dinv + a + (long long)epi.n * m;
+      erow = rowexp[row];
+    }
+    const long long cstride = (long long)epi.ld_out * epi.nmid;
+    const long long dstride = (long long)epi.n * epi.nmid;
+    double *out = epi.out + (epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0);
+    for (int cc = 0; cc < n_tile; cc += 8) {
+      uint32_t v[kSlices][8];
+#pragma unroll
+      for (int w = 0; w < kSlices; ++w) tmem_ld8_wait(tl + (uint32_t)(w * n_tile + cc), v[w]);
+      if (row < M) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int col = c0 + cc + q;
+          if (col < N) {
+            __int128 t = 0;
+#pragma unroll
+            for (int w = 0; w < kSlices; ++w) {
+              const long long gw = (long long)__float2ll_rn(__uint_as_float(v[w][q]));
+              t += (__int128)gw << (kDigitBits * (kSlices - 1 - w));
+            }
+            double x = scaled_i128_to_double(t, erow + colexp[col] - 63);
+            if (dinv_row) x *= __ldg(dinv_row + dstride * col);
+            out[obase + cstride * col] = x;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, (uint32_t)tmem_cols);
+}
+
+// ------------------------------------------------------------------ host side
+struct F64TcFd {
+  int d = 0, n = 0, kp = 0, M = 0, R_max = 1, nchunks = 0;
+  int n_tile = 32, tmem_cols = 256;
+  size_t smem = 0;
+  uint32_t idesc = 0;
+  DevBuf<unsigned short> slA, slVt, slU;  // digit slices (BF16 bits)
+  DevBuf<int> rowexp, eVt, eU;
+  DevBuf<double> t0, t1;                  // FP64 intermediates
+  DevBuf<int> err;
+  CUtensorMap mapA{}, mapVt{}, mapU{};
+  const double *dinv = nullptr;
+};
+
+// The digits of a factor on the host: row j of the n x n matrix B (row-major) gets the
+// exponent f_j (max |B_j.| < 2^{f_j}) and its values' 8 digits, as the split kernel does.
+static void split_factor_host(const std::vector<double> &B, int n, int kp,
+                              std::vector<unsigned short> &sl, std::vector<int> &ex) {
+  sl.assign((size_t)kSlices * n * kp, 0);
+  ex.assign(n, 0);
+  auto bits_of = [](double v) {
+    unsigned long long b;
+    std::memcpy(&b, &v, 8);
+    return b;
+  };
+  auto bf16_of_digit = [](int dg) {
+    const float f = (float)dg;  // |dg| <= 127: exact, and exact in BF16
+    unsigned int u;
+    std::memcpy(&u, &f, 4);
+    return (unsigned short)(u >> 16);
+  };
+  for (int j = 0; j < n; ++j) {
+    unsigned long long mx = 0;
+    for (int k = 0; k < n; ++k) mx = std::max(mx, bits_of(B[(size_t)j * n + k]) & 0x7FFFFFFFFFFFFFFFull);
+    const int emax = (int)(mx >> 52);
+    const int e = emax ? emax - 1022 : -1022;
+    ex[j] = e;
+    for (int k = 0; k < n; ++k) {
+      const unsigned long long b = bits_of(B[(size_t)j * n + k]);
+      const int bx = (int)((b >> 52) & 0x7FF);
+      unsigned long long m = b & ((1ull << 52) - 1);
+      int eeff = bx;
+      if (bx) m |= 1ull << 52; else eeff = 1;
+      const int sh = eeff - e - 1019;
+      const unsigned long long F = sh >= 0 ? (m << sh) : (-sh >= 64 ? 0ull : m >> (-sh));
+      const bool neg = (b >> 63) != 0;
+      for (int s = 0; s < kSlices; ++s) {
+        const int dg = (int)((F >> (kDigitBits * (kSlices - 1 - s))) & 127ull);
+        sl[(size_t)s * n * kp + (size_t)j * kp + k] = bf16_of_digit(neg ? -dg : dg);
+      }
+    }
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 f64tc_encoder() {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    IGA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                  cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled not available"};
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3D map over kSlices stacked row-major BF16 matrices (rows x kp, inner extent n: reads
+// past n are zero); box = one 128-byte K-chunk x box_rows of one slice.
+static void make_slice_map(CUtensorMap &m, const void *base, long long n, long long rows,
+                           long long kp, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)rows, (cuuint64_t)kSlices};
+  cuuint64_t strides[2] = {(cuuint64_t)(kp * 2), (cuuint64_t)(rows * kp * 2)};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = f64tc_encoder()(
+      &m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+}
+
+bool f64tc_supported(int n) { return n >= 1 && (n + 63) / 64 <= kF64TcMaxChunks; }
+
+F64TcFd *make_f64tc_fd(int d, int n, const Factor1D &f, cudaStream_t s, int R_max,
+                       const double *dinv) {
+  if (!f64tc_supported(n))
+    throw Error{IGA_ERR_UNSUPPORTED, "the FP64 tensor-core FD takes n <= 256"};
+  auto *t = new F64TcFd();
+  try {
+    t->d = d;
+    t->n = n;
+    t->kp = (n + 7) / 8 * 8;  // 16-byte row pitch for the tensor maps
+    long long M = 1;
+    for (int l = 0; l < d - 1; ++l) M *= n;
+    t->M = (int)M;
+    t->R_max = R_max;
+    t->nchunks = (n + 63) / 64;
+    t->dinv = dinv;
+    t->n_tile = 32;
+    t->tmem_cols = 256;  // kSlices accumulators of n_tile columns
+    const size_t b_total = (size_t)kSlices * t->nchunks * t->n_tile * 128;
+    const int ring = (int)std::min<size_t>(8, (kF64TcSmemBudget - b_total) / kF64TcABytes);
+    if (ring < 2) throw Error{IGA_ERR_UNSUPPORTED, "FP64 tensor-core FD: no room for the ring"};
+    t->smem = 1024 + b_total + (size_t)ring * kF64TcABytes;
+    // instruction descriptor: D = F32, A = B = BF16, K-major, N >> 3, M >> 4
+    t->idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(t->n_tile >> 3) << 17) |
+               ((uint32_t)(kF64TcM >> 4) << 24);
+    // factors: V^T for the forward products, U for the inverse ones (host buffers kept
+    // until the stream synchronisation below)
+    std::vector<unsigned short> slv, slu;
+    std::vector<int> exv, exu;
+    split_factor_host(f.Vt, n, t->kp, slv, exv);
+    split_factor_host(f.U, n, t->kp, slu, exu);
+    auto put = [&](auto &dst, const auto &h) {
+      dst.alloc(h.size());
+      IGA_CUDA_TRY(cudaMemcpyAsync(dst.ptr, h.data(), h.size() * sizeof(h[0]),
+                                   cudaMemcpyHostToDevice, s));
+    };
+    put(t->slVt, slv);
+    put(t->eVt, exv);
+    put(t->slU, slu);
+    put(t->eU, exu);
+    const long long rows = (long long)R_max * M;
+    t->slA.alloc((size_t)kSlices * rows * t->kp);
+    IGA_CUDA_TRY(cudaMemsetAsync(t->slA.ptr, 0, (size_t)kSlices * rows * t->kp * 2, s));
+    t->rowexp.alloc((size_t)rows);
+    t->t0.alloc((size_t)rows * n);
+    t->t1.alloc((size_t)rows * n);
+    t->err.alloc(1);
+    IGA_CUDA_TRY(cudaMemsetAsync(t->err.ptr, 0, sizeof(int), s));
+    make_slice_map(t->mapA, t->slA.ptr, n, rows, t->kp, kF64TcM);
+    make_slice_map(t->mapVt, t->slVt.ptr, n, n, t->kp, t->n_tile);
+    make_slice_map(t->mapU, t->slU.ptr, n, n, t->kp, t->n_tile);
+    {
+      // one attribute per device, the largest any problem needs (it belongs to the kernel)
+      static std::atomic<bool> smem_set[64] = {};
+      int dev = 0;
+      IGA_CUDA_TRY(cudaGetDevice(&dev));
+      const bool done = dev >= 0 && dev < 64 && smem_set[dev].load(std::memory_order_acquire);
+      std::unique_lock<DeviceLock> lk(device_mutex(), std::defer_lock);
+      if (!done) lk.lock();
+      if (!done && dev >= 0 && dev < 64 && !smem_set[dev].load(std::memory_order_relaxed)) {
+        IGA_CUDA_TRY(cudaFuncSetAttribute(f64tc_gemm_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          1024 + kF64TcSmemBudget));
+        smem_set[dev].store(true, std::memory_order_release);
+      }
+    }
+    IGA_CUDA_TRY(cudaStreamSynchronize(s));
+  } catch (...) {
+    delete t;
+    throw;
+  }
+  return t;
+}
+
+void destroy_f64tc_fd(F64TcFd *t) { delete t; }
+int *f64tc_error_word(F64TcFd &t) { return t.err.ptr; }
+
+// The chain: for each of the 2d mode products, split its input (the FD input, then the
+// previous product's FP64 output) into digit slices and multiply by the factor's slices;
+// the d-th product is scaled by the FD diagonal, the last writes `out`.
+void f64tc_fd_apply(F64TcFd &t, IdxPtr<const double> in, IdxPtr<double> out, int R,
+                    cudaStream_t s) {
+  if (R < 1 || R > t.R_max) throw Error{IGA_ERR_INVALID_ARG, "too many right-hand sides"};
+  const int rows = R * t.M;
+  const long long sstride = (long long)t.R_max * t.M * t.kp;
+  const int split_blocks = (int)std::min<long long>((rows + 7) / 8, 152LL * 8);
+  const dim3 grid((rows + kF64TcM - 1) / kF64TcM, (t.n + t.n_tile - 1) / t.n_tile);
+  IdxPtr<const double> src = in;
+  double *bufs[2] = {t.t0.ptr, t.t1.ptr};
+  const int total = 2 * t.d;
+  for (int g = 0; g < total; ++g) {
+    launch_pdl(kPdlTensorCore, f64tc_split_kernel, dim3(split_blocks), dim3(256), 0, s, src, rows,
+               t.n, t.kp, t.slA.ptr, sstride, t.rowexp.ptr);
+    IGA_LAUNCH_CHECK();
+    const bool fwd = g < t.d, last = g == total - 1;
+    F64TcEpi e{};
+    if (last) {
+      e.out = out.base;
+      e.oidx = out.idx;
+      e.ostride = out.stride;
+      if (out.idx && out.off) throw Error{IGA_ERR_INVALID_ARG, "unsupported output offset"};
+    } else {
+      e.out = bufs[g & 1];
+    }
+    e.n = t.n;
+    e.ld_out = t.n;
+    e.nmid = t.M / t.n;
+    e.dinv = g == t.d - 1 ? t.dinv : nullptr;
+    e.err = t.err.ptr;
+    launch_pdl(kPdlTensorCore, f64tc_gemm_kernel, grid, dim3(kF64TcThreads), t.smem, s, t.mapA,
+               fwd ? t.mapVt : t.mapU, rows, t.n, t.n, t.n_tile, t.tmem_cols, t.idesc,
+               (const int *)t.rowexp.ptr, (const int *)(fwd ? t.eVt.ptr : t.eU.ptr), e);
+    IGA_LAUNCH_CHECK();
+    if (!last) src = plain_ptr<const double>(bufs[g & 1]);
+  }
+}
+
+void preload_kernels_fd_f64tc() {
+  cudaFuncAttributes a;
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, f64tc_split_kernel));
+  IGA_CUDA_TRY(cudaFuncGetAttributes(&a, f64tc_gemm_kernel));
+}
+
+}  // namespace iga

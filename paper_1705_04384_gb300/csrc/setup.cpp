@@ -596,6 +596,7 @@ void ensure_kernels_loaded() {
   preload_kernels_fd64();
   preload_kernels_fd64_fma();
   preload_kernels_fd_tc();
+  preload_kernels_fd_f64tc();
   preload_kernels_geom_op();
   preload_kernels_krylov();
   preload_kernels_bicgstab();

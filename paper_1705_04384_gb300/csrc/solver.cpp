@@ -64,8 +64,11 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   if (has_wind && scheme == 1)
     throw Error{IGA_ERR_INVALID_ARG, "the weighted-quadrature scheme takes no wind"};
   fac = get_factor(n_elem, p, stream, 0.0, scheme);
-  if (has_wind && tensor_core_prec(prec))
+  if (has_wind && (tensor_core_prec(prec) || prec == IGA_PREC_FP64_TC))
     throw Error{IGA_ERR_INVALID_ARG, "a wind requires precision FP64 or NONE"};
+  if (prec == IGA_PREC_FP64_TC && !f64tc_supported(fac->n))
+    throw Error{IGA_ERR_UNSUPPORTED, "precision FP64_TC takes n <= 256 basis functions per "
+                                     "direction"};
   // per-direction FD factors: the pencil (K + w_l B', M) of Sec. 3.2 (w_l = 0: Poisson)
   for (int l = 0; l < 3; ++l)
     facd[l] = (l >= d || geom.wind[l] == 0.0) ? fac : get_factor(n_elem, p, stream, geom.wind[l]);
@@ -100,6 +103,10 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   } else if (tensor_core_prec(prec)) {
     dinv32.alloc(N);
     launch_fd_diag_inverse(fac->d_lam.ptr, n, d, nullptr, dinv32.ptr, stream);
+  } else if (prec == IGA_PREC_FP64_TC) {
+    // the slice products use the unfolded factors (V^T, U) and eigen-order
+    dinv.alloc(N);
+    launch_fd_diag_inverse(fac->d_lam.ptr, n, d, dinv.ptr, nullptr, stream);
   }
   const double t3 = wall_seconds();
   ensure_capacity(1);
@@ -195,6 +202,11 @@ void Ctx::ensure_capacity(int R) {
     tc.reset();
     R_max = 0;  // until the new tensor-core context exists
     tc.reset(make_tc_fd(d, n, prec, *fac, stream, R, dinv32.ptr));
+  }
+  if (prec == IGA_PREC_FP64_TC) {
+    f64tc.reset();
+    R_max = 0;
+    f64tc.reset(make_f64tc_fd(d, n, *fac, stream, R, dinv.ptr));
   }
   R_max = R;
 }
@@ -342,6 +354,9 @@ void Ctx::precond(IdxPtr<const double> in, double *out, int R, cudaStream_t s) {
     throw Error{IGA_ERR_INVALID_ARG, "precond on an unpreconditioned handle"};
   } else if (prec == IGA_PREC_FP64) {
     fd_chain_fp64<double>(*this, in, plain_ptr<double>(out), R, s);
+  } else if (prec == IGA_PREC_FP64_TC) {
+    if (!f64tc) throw Error{IGA_ERR_CUDA, "FP64 tensor-core FD context missing"};
+    f64tc_fd_apply(*f64tc, in, plain_ptr<double>(out), R, s);
   } else {
     if (!tc) throw Error{IGA_ERR_CUDA, "tensor-core FD context missing"};
     tc_fd_apply_f64out(*tc, in, out, R, s);
@@ -363,7 +378,7 @@ void Ctx::ensure_ws(int max_iter, int R) {
   const size_t vecs = (size_t)Rc * N;
   V.alloc((size_t)(mi + 1) * vecs);
   IGA_CUDA_TRY(cudaMemsetAsync(V.ptr, 0, (size_t)(mi + 1) * vecs * 8, stream));
-  if (prec == IGA_PREC_FP64) Zd.alloc((size_t)mi * vecs);
+  if (prec == IGA_PREC_FP64 || prec == IGA_PREC_FP64_TC) Zd.alloc((size_t)mi * vecs);
   if (tensor_core_prec(prec)) Zf.alloc((size_t)mi * vecs);
   const long long hstride = (long long)(mi + 1) * mi;
   H.alloc((size_t)Rc * hstride);
@@ -392,7 +407,7 @@ void Ctx::ensure_ws(int max_iter, int R) {
   IGA_CUDA_TRY(cudaMallocHost(&h_hist, (size_t)Rc * (mi + 2) * 8));
   ws = KrylovWs{};
   ws.V = V.ptr;
-  if (prec == IGA_PREC_FP64) {
+  if (prec == IGA_PREC_FP64 || prec == IGA_PREC_FP64_TC) {
     ws.Z = Zd.ptr;
     ws.z_fp32 = 0;
   } else if (prec == IGA_PREC_NONE) {
@@ -435,6 +450,11 @@ void Ctx::launch_iteration(cudaGraphConditionalHandle cond, int has_cond, cudaSt
   } else if (prec == IGA_PREC_FP64) {
     IdxPtr<double> zk{(double *)ws.Z, kptr, 0, blk};
     fd_chain_fp64<double>(*this, vk, zk, R, s);
+    operator_and_pass1<double>(IdxPtr<const double>{(const double *)ws.Z, kptr, 0, blk}, R, s);
+  } else if (prec == IGA_PREC_FP64_TC) {
+    if (!f64tc) throw Error{IGA_ERR_CUDA, "FP64 tensor-core FD context missing"};
+    IdxPtr<double> zk{(double *)ws.Z, kptr, 0, blk};
+    f64tc_fd_apply(*f64tc, vk, zk, R, s);
     operator_and_pass1<double>(IdxPtr<const double>{(const double *)ws.Z, kptr, 0, blk}, R, s);
   } else {
     if (!tc) throw Error{IGA_ERR_CUDA, "tensor-core FD context missing"};
@@ -593,11 +613,12 @@ iga_status Ctx::collect(int *iters, double *hist_out, double *relres, int *statu
   if (!pending) throw Error{IGA_ERR_INVALID_ARG, "no solve in flight on this handle"};
   pending = false;
   IGA_CUDA_TRY(cudaEventSynchronize(done_ev));
-  if (tc) {
+  int *ew = tc ? tc_fd_error_word(*tc) : f64tc ? f64tc_error_word(*f64tc) : nullptr;
+  if (ew) {
     int err = 0;
-    IGA_CUDA_TRY(cudaMemcpy(&err, tc_fd_error_word(*tc), sizeof(int), cudaMemcpyDeviceToHost));
+    IGA_CUDA_TRY(cudaMemcpy(&err, ew, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
-      IGA_CUDA_TRY(cudaMemset(tc_fd_error_word(*tc), 0, sizeof(int)));
+      IGA_CUDA_TRY(cudaMemset(ew, 0, sizeof(int)));
       throw Error{IGA_ERR_DEVICE_TIMEOUT,
                   "a tensor-core FD wait timed out (code " + std::to_string(err) + ")"};
     }

@@ -37,9 +37,10 @@ def main():
     a = ap.parse_args()
     if a.op == "fp64peak":
         # the FP64 ceiling (iga_fp64_probe): best of a.reps timed launches per probe kind
-        r = measure_fp64_peak(reps=1000, trials=a.reps)
+        r = measure_fp64_peak(reps=1000, trials=a.reps, mixed=True)
         print(json.dumps({"op": "fp64peak", "gflops_dmma": r["dmma"], "gflops_fma": r["fma"],
-                          "gflops_peak": r["peak"], "trials": a.reps}))
+                          "gflops_peak": r["peak"], "gflops_both_split_warps": r["split"],
+                          "gflops_both_in_each_warp": r["interleaved"], "trials": a.reps}))
         return
     P = Problem(a.d, a.ne, a.p, geometry=a.geometry, precision=a.precision, scheme=a.scheme)
     g = torch.Generator(device="cpu").manual_seed(0)

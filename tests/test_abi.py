@@ -65,7 +65,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     bad = Geometry(1, 2.0, 1.0)
     assert lib.iga_setup(2, 32, 3, ctypes.byref(bad), 0, None, ctypes.byref(h)) == 1
     assert lib.iga_setup(2, 32, 3, ctypes.byref(g), 7, None, ctypes.byref(h)) == 1
-    assert lib.iga_setup(2, 32, 3, ctypes.byref(g), 5, None, ctypes.byref(h)) == 1
+    assert lib.iga_setup(2, 32, 3, ctypes.byref(g), 6, None, ctypes.byref(h)) == 1
     assert lib.iga_setup(2, 32, 3, ctypes.byref(g), -1, None, ctypes.byref(h)) == 1
     assert lib.iga_setup(2, 32, 3, None, 0, None, ctypes.byref(h)) == 1
     assert lib.iga_dims(None, None, None) == 1
@@ -114,7 +114,8 @@ def test_batch_and_noalloc_argument_checks(lib):
 
 
 def test_fp64_probe_argument_checks(lib):
-    assert lib.iga_fp64_probe(2, 10, None, None) == 1
+    assert lib.iga_fp64_probe(4, 10, None, None) == 1
+    assert lib.iga_fp64_probe(-1, 10, None, None) == 1
     assert lib.iga_fp64_probe(0, 0, None, None) == 1
     assert b"reps" in lib.iga_last_error()
 
