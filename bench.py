@@ -8,6 +8,8 @@ step = one solve for each p (setup cached).  Four forms of the same solves:
   tf32    flexible GMRES with the FD mode products on the tensor cores in TF32 ("mixed"),
   tf32x3  the same with error-compensated TF32 (hi/lo operand split, three MMAs per step;
           "tf32x3"),
+  fp64tc  plain GMRES with the FP64 FD on the BF16 tensor cores by exact integer slice
+          products (FP64-accurate; "fp64tc"),
   bf16    the same with BF16 operands ("bf16"),
 each with per-solve p50/p99, time to solution with and without setup, the error against
 the FP64 oracle's solution (p = 4) and the roofline of its dominant kernel.  The FP64
@@ -189,6 +191,20 @@ def committed_traffic(summary="fd_fold_mma_3d_ne128.md", files=("kernels_fd64.cu
     if vals.get("kernel_source_sha256_16") != kernel_source_hash(files):
         return None
     return float(vals["traffic_bytes_per_launch"]) if "traffic_bytes_per_launch" in vals else None
+
+
+def f64tc_issued_flops(n, d):
+    """BF16 MMA FLOPs one FD apply of the FP64_TC form issues (kernels_fd_f64tc.cu's tiling:
+    128-row tiles, 64-column tiles when the factor's 8 slices leave room for a 2-stage ring,
+    else 32, every column tile at full width; 36 slice pairs per 16-wide K-step;
+    2 x 128 x N x 16 per MMA)."""
+    nchunks = (n + 63) // 64
+    budget = 225 * 1024
+    nt = 64 if budget - 8 * nchunks * 64 * 128 >= 2 * 128 * 128 else 32
+    width = (n + nt - 1) // nt * nt
+    ksteps = sum(min(4, (n - 64 * c + 15) // 16) for c in range(nchunks))
+    row_tiles = (n ** (d - 1) + 127) // 128
+    return 2.0 * d * row_tiles * 36 * ksteps * 2 * 128 * 16 * width
 
 
 def measured_peaks():
@@ -438,7 +454,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) * 1e-3 / reps
 
-    forms = ["fp64"] if args.no_mixed else ["fp64", "tf32", "tf32x3", "bf16"]
+    forms = ["fp64"] if args.no_mixed else ["fp64", "tf32", "tf32x3", "bf16", "fp64tc"]
     probs = {f: make(f) for f in forms}
 
     if world > 1:
@@ -513,6 +529,22 @@ def run_ours(args):
     for f in forms[1:]:
         Pf = q4[f]["P"]
         t_fd = time_calls(lambda: Pf.precond_apply(q4[f]["rhs"], out=buf), 20)
+        if f == "fp64tc":
+            fl_issued = f64tc_issued_flops(n4, d)
+            bf16_peak = peaks.get("bf16_tflops", 1900.0)
+            out[f]["roofline"] = {
+                "bound": "tensor", "achieved": fl_issued / t_fd / 1e12, "peak": bf16_peak,
+                "unit": "TFLOP/s", "frac": fl_issued / t_fd / 1e12 / bf16_peak, "traffic": None,
+                "kernel": "2d x (f64tc_split_kernel + f64tc_gemm_kernel) (one FD apply: BF16 "
+                          "digit-slice products, 36 slice pairs per K-step)",
+                "per_apply_us": t_fd * 1e6, "issued_flops_per_apply": fl_issued,
+                "fp64_equivalent_tflops": 2.0 * d * 2.0 * n4 ** (d + 1) / t_fd / 1e12,
+                "peak_note": ("of measured" if "bf16_tflops" in peaks else "of fallback") +
+                             " dense BF16 (cuBLAS, burst); achieved = BF16 MMA FLOPs issued "
+                             "(zero-padded K-steps and column tiles included); "
+                             "fp64_equivalent_tflops = the dense FD's 2d x 2 n^(d+1) FP64 "
+                             "FLOPs per apply over the same time"}
+            continue
         by = 24.0 * N4
         tfl = 2.0 * d * 2.0 * n4 ** (d + 1)
         out[f]["roofline"] = {
@@ -624,6 +656,7 @@ def run_ours(args):
             "clocks": clk, "fp64_peak_gflops": fp64,
             "rel_err_vs_oracle": oracle_err,
             "mixed": out.get("tf32"), "tf32x3": out.get("tf32x3"), "bf16": out.get("bf16"),
+            "fp64tc": out.get("fp64tc"),
             "bicgstab": bicg_out,
             "secondary_3d_annulus_ne64": secondary, "batched": batched}
     print(json.dumps(line), flush=True)

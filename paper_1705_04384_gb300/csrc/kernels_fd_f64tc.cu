@@ -17,19 +17,20 @@
 //     w + 1 <= 8 pairs: below 8 K 127^2 < 2^24 for K <= 130, so every G_w is the exact
 //     integer; at K = 131, 132 only G_7, which carries 2^-49 of the result's scale, can
 //     round (by at most 2^-63 of it);
-//   * C_ij = 2^{e_i + f_j - 63} sum_{w <= 7} G_w 2^{7 (7 - w)}, formed exactly in a 128-bit
-//     integer and rounded once to FP64.
-// The pairs with s + t > 7 are dropped; with the truncated digit tails the error of C_ij is
-// below 3 K 2^{-56} 2^{e_i + f_j} (about 5.4e-15 of 2^{e_i + f_j} at K = 130), the size of an
-// FP64 dot product's rounding.  No FP64 arithmetic is used except the FD diagonal's
-// multiplication: GB300's FP64 unit is shared by FMAs and the FP64 tensor path, and the
-// FP64 FD products run at its ceiling.
+//   * C_ij = 2^{e_i + f_j - 63} sum_{w <= 7} G_w 2^{7 (7 - w)}, rounded once to FP64: two
+//     exact 64-bit partial sums and one FMA (recombine).
+// The pairs with s + t > 7 are dropped (s + t = 8: 7 pairs of at most K 2^{-56} 2^{e_i + f_j}
+// each, the rest 2^-7 smaller) and the digit tails are below 2^-56 of each scale, so the
+// error of C_ij is below about 9 K 2^{-56} 2^{e_i + f_j} (1.6e-14 of 2^{e_i + f_j} at K = 130),
+// the size of an FP64 dot product's worst-case rounding; measured on random data, 9e-16.  No FP64 arithmetic is used except the FD diagonal's
+// multiplication and three operations per output in the recombination: GB300's FP64 unit is
+// shared by FMAs and the FP64 tensor path, and the FP64 FD products run at its ceiling.
 //
 // Kernels: f64tc_split_kernel (one warp per row of A: the row's scale, then its 8 BF16 digit
 // slices; integer operations only) and f64tc_gemm_kernel (one 128-row x n_tile tile per CTA:
 // the factor's 8 slices stay in shared memory, the activation's slices stream through a
 // TMA ring, one thread issues the 36 slice-pair MMAs per 16-wide K-step into 8 TMEM
-// accumulators, four warps form the FP64 outputs in the layout-rotating order of the other
+// accumulators, eight warps form the FP64 outputs in the layout-rotating order of the other
 // FD paths).  Every wait is bounded and reports through the context's device error word.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -47,7 +48,7 @@ namespace iga {
 constexpr int kSlices = 8;        // base-2^7 digits per value
 constexpr int kDigitBits = 7;
 constexpr int kF64TcM = 128;      // rows per tile
-constexpr int kF64TcThreads = 128;
+constexpr int kF64TcThreads = 256;  // 8 epilogue warps: two per TMEM lane quarter
 constexpr int kF64TcMaxChunks = 4;  // n <= 256: the factor's slices fit in shared memory
 constexpr int kF64TcSmemBudget = 225 * 1024;  // ring + resident factor (plus 1024 alignment)
 constexpr uint32_t kF64TcABytes = kF64TcM * 128;  // one 64-wide K-chunk of one slice
@@ -98,9 +99,13 @@ __global__ void __launch_bounds__(256) f64tc_split_kernel(IdxPtr<const double> i
       const unsigned long long b = x[k];
       const unsigned long long F = fixed56(b, e);
       const bool neg = (b >> 63) != 0;
+      // digits 0..3 are bits 55..28 of F, digits 4..7 bits 27..0: two 28-bit halves, so
+      // that the digit extraction runs on 32-bit shifts
+      const unsigned int fh = (unsigned int)(F >> 28), fl = (unsigned int)(F & 0xFFFFFFFull);
 #pragma unroll
       for (int s = 0; s < kSlices; ++s) {
-        int dg = (int)((F >> (kDigitBits * (kSlices - 1 - s))) & 127ull);
+        const unsigned int half = s < 4 ? fh : fl;
+        const int dg = (int)((half >> (kDigitBits * (3 - (s & 3)))) & 127u);
         o[s * sstride + k] = digit_bf16(neg ? -dg : dg);
       }
     }
@@ -108,38 +113,39 @@ __global__ void __launch_bounds__(256) f64tc_split_kernel(IdxPtr<const double> i
 }
 
 // ------------------------------------------------------------------ recombination
-// 2^E t for the 128-bit integer t, rounded to nearest (ties to even) once.
-__device__ __forceinline__ double scaled_i128_to_double(__int128 t, int E) {
-  if (t == 0) return 0.0;
-  const bool neg = t < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
-  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  unsigned long long mant;
-  int ex = msb;  // value = mant 2^{ex - 52} 2^E, mant in [2^52, 2^53)
-  if (msb > 52) {
-    const int sh = msb - 52;
-    mant = (unsigned long long)(u >> sh);
-    const unsigned __int128 rem = u - ((unsigned __int128)mant << sh);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    if (rem > half || (rem == half && (mant & 1ull))) {
-      ++mant;
-      if (mant >> 53) {
-        mant >>= 1;
-        ++ex;
-      }
-    }
-  } else {
-    mant = (unsigned long long)u << (52 - msb);
+// The integer value of an FP32 word that holds an integer of magnitude below 2^25 (below
+// 2^24 except G_7 at K = 131, 132), with integer operations only (the float-to-integer
+// conversions with 64-bit results run on the FP64 unit).
+__device__ __forceinline__ int exact_int_of_f32(uint32_t u) {
+  const int ex = (int)((u >> 23) & 0xFFu) - 127;  // 0..24 for a nonzero integer
+  if (ex < 0) return 0;
+  const unsigned int m = (u & 0x7FFFFFu) | 0x800000u;
+  const int mag = (int)(ex <= 23 ? m >> (23 - ex) : m << (ex - 23));
+  return (u >> 31) ? -mag : mag;
+}
+
+// x 2^E for a normal FP64 x and an integer E, exactly, by adding E to the exponent field
+// (ldexp where the result would leave the normal range, which the FD's values do not).
+__device__ __forceinline__ double scale_pow2(double x, int E) {
+  if (x == 0.0) return 0.0;
+  const long long bits = __double_as_longlong(x);
+  const int be = (int)((bits >> 52) & 0x7FF) + E;
+  if (be <= 0 || be >= 2047) return ldexp(x, E);
+  return __longlong_as_double(bits + ((long long)E << 52));
+}
+
+// 2^E sum_w G_w 2^{7 (7 - w)} for the eight exact accumulator words, rounded once: the sum
+// splits into H 2^28 + L with H = sum_{w<4} G_w 2^{7 (3 - w)} (|H| < 2^44) and L the same of
+// G_4..G_7 (|L| < 2^47), both exact in int64 and in FP64, and one FMA forms H 2^28 + L with a
+// single rounding.
+__device__ __forceinline__ double recombine(const uint32_t (&g)[kSlices], int E) {
+  long long H = 0, L = 0;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    H = (H << kDigitBits) + exact_int_of_f32(g[w]);
+    L = (L << kDigitBits) + exact_int_of_f32(g[w + 4]);
   }
-  const int be = ex + E + 1023;
-  if (be <= 0 || be >= 2047) {  // outside the normal range (not met by the FD's values)
-    const double m = (double)mant;
-    return neg ? -ldexp(m, ex - 52 + E) : ldexp(m, ex - 52 + E);
-  }
-  const unsigned long long bits =
-      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
+  return scale_pow2(fma((double)H, 268435456.0, (double)L), E);
 }
 
 // 8 columns of one TMEM lane per thread; the wait is in the same statement, so no use of
@@ -169,6 +175,13 @@ struct F64TcEpi {
 // the factor's slices [t][chunk] (n_tile rows x 128 bytes each), then the ring of the
 // activation's slice chunks (128 rows x 128 bytes each); the ring depth is what the dynamic
 // shared-memory size leaves.  TMEM: accumulator w at columns w n_tile.
+// Measured at 3D n = 130: the MMA-issuing thread spends ~160 cycles per M = 128, K = 16
+// instruction whatever N (32 or 64) -- staging the activation's K-steps in TMEM with
+// tcgen05.cp, so that an MMA reads only the factor tile from shared memory, measured slower
+// (1420 against 1211 us per FD apply) -- so the widest tile that TMEM (kSlices n_tile <= 512)
+// and shared memory allow is the fastest: fewer instructions per product (64 columns: 907 us
+// at n = 130; a last column tile narrowed to its 2 columns' MMA width, N = 16, measured the
+// same).
 __global__ void __launch_bounds__(kF64TcThreads, 1)
     f64tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapB, int M, int N, int K, int n_tile,
@@ -267,8 +280,10 @@ __global__ void __launch_bounds__(kF64TcThreads, 1)
     if (lane == 0) atomicExch(epi.err, 14);
   } else if (!*(volatile int *)&mma_failed) {
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the column half w / 4
+    const int q4 = warp & 3, half = warp >> 2;
+    const int row = m0 + q4 * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
     long long obase = 0;
     const double *dinv_row = nullptr;
     int erow = 0;
@@ -282,7 +297,8 @@ __global__ void __launch_bounds__(kF64TcThreads, 1)
     const long long cstride = (long long)epi.ld_out * epi.nmid;
     const long long dstride = (long long)epi.n * epi.nmid;
     double *out = epi.out + (epi.oidx ? (long long)(*epi.oidx) * epi.ostride : 0);
-    for (int cc = 0; cc < n_tile; cc += 8) {
+    const int cw = n_tile / 2;  // columns of this warp
+    for (int cc = half * cw; cc < (half + 1) * cw; cc += 8) {
       uint32_t v[kSlices][8];
 #pragma unroll
       for (int w = 0; w < kSlices; ++w) tmem_ld8_wait(tl + (uint32_t)(w * n_tile + cc), v[w]);
@@ -291,13 +307,10 @@ __global__ void __launch_bounds__(kF64TcThreads, 1)
         for (int q = 0; q < 8; ++q) {
           const int col = c0 + cc + q;
           if (col < N) {
-            __int128 t = 0;
+            uint32_t g[kSlices];
 #pragma unroll
-            for (int w = 0; w < kSlices; ++w) {
-              const long long gw = (long long)__float2ll_rn(__uint_as_float(v[w][q]));
-              t += (__int128)gw << (kDigitBits * (kSlices - 1 - w));
-            }
-            double x = scaled_i128_to_double(t, erow + colexp[col] - 63);
+            for (int w = 0; w < kSlices; ++w) g[w] = v[w][q];
+            double x = recombine(g, erow + colexp[col] - 63);
             if (dinv_row) x *= __ldg(dinv_row + dstride * col);
             out[obase + cstride * col] = x;
           }
@@ -413,10 +426,16 @@ F64TcFd *make_f64tc_fd(int d, int n, const Factor1D &f, cudaStream_t s, int R_ma
     t->R_max = R_max;
     t->nchunks = (n + 63) / 64;
     t->dinv = dinv;
-    t->n_tile = 32;
-    t->tmem_cols = 256;  // kSlices accumulators of n_tile columns
+    // 64-column tiles (TMEM holds the kSlices accumulators exactly) when the factor's
+    // slices leave room for a 2-stage ring, else 32
+    auto ring_for = [&](int nt) {
+      const size_t b = (size_t)kSlices * t->nchunks * nt * 128;
+      return b >= (size_t)kF64TcSmemBudget ? 0 : (int)std::min<size_t>(8, (kF64TcSmemBudget - b) / kF64TcABytes);
+    };
+    t->n_tile = ring_for(64) >= 2 ? 64 : 32;
+    t->tmem_cols = kSlices * t->n_tile;  // 512 or 256
     const size_t b_total = (size_t)kSlices * t->nchunks * t->n_tile * 128;
-    const int ring = (int)std::min<size_t>(8, (kF64TcSmemBudget - b_total) / kF64TcABytes);
+    const int ring = ring_for(t->n_tile);
     if (ring < 2) throw Error{IGA_ERR_UNSUPPORTED, "FP64 tensor-core FD: no room for the ring"};
     t->smem = 1024 + b_total + (size_t)ring * kF64TcABytes;
     // instruction descriptor: D = F32, A = B = BF16, K-major, N >> 3, M >> 4
