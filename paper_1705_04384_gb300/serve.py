@@ -36,7 +36,8 @@ _FIXED_PER_DOF = {2: 8 * (5 + 3 + 2 + 5) + 3 * 4, 3: 8 * (9 + 9 + 2 + 5) + 3 * 4
 
 def handle_bytes(d, N, max_iter, precision):
     z = 4 if precision in ("tf32", "bf16", "tf32x3") else (0 if precision == "none" else 8)
-    split = 3 * 4 if precision == "tf32x3" else 0
+    # TF32X3: the FD scratch twice (hi and lo); FP64_TC: 8 BF16 slices and 2 FP64 intermediates
+    split = 3 * 4 if precision == "tf32x3" else (8 * 2 + 2 * 8 if precision == "fp64tc" else 0)
     return int(N * (_FIXED_PER_DOF[d] + split + (max_iter + 1) * 8 + max_iter * z)) + (1 << 20)
 
 
