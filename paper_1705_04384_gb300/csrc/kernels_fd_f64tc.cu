@@ -22,9 +22,10 @@
 // The pairs with s + t > 7 are dropped (s + t = 8: 7 pairs of at most K 2^{-56} 2^{e_i + f_j}
 // each, the rest 2^-7 smaller) and the digit tails are below 2^-56 of each scale, so the
 // error of C_ij is below about 9 K 2^{-56} 2^{e_i + f_j} (1.6e-14 of 2^{e_i + f_j} at K = 130),
-// the size of an FP64 dot product's worst-case rounding; measured on random data, 9e-16.  No FP64 arithmetic is used except the FD diagonal's
-// multiplication and three operations per output in the recombination: GB300's FP64 unit is
-// shared by FMAs and the FP64 tensor path, and the FP64 FD products run at its ceiling.
+// the size of an FP64 dot product's worst-case rounding; measured on random data, 9e-16.
+// FP64 arithmetic is limited to three operations per output in the recombination and the FD
+// diagonal's multiplication: GB300's FP64 unit is shared by FMAs and the FP64 tensor path,
+// and the FP64 FD products run at its ceiling.
 //
 // Kernels: f64tc_split_kernel (one warp per row of A: the row's scale, then its 8 BF16 digit
 // slices; integer operations only) and f64tc_gemm_kernel (one 128-row x n_tile tile per CTA:
@@ -135,9 +136,12 @@ __device__ __forceinline__ double scale_pow2(double x, int E) {
 }
 
 // 2^E sum_w G_w 2^{7 (7 - w)} for the eight exact accumulator words, rounded once: the sum
-// splits into H 2^28 + L with H = sum_{w<4} G_w 2^{7 (3 - w)} (|H| < 2^44) and L the same of
+// splits into H 2^28 + L with H = sum_{w<4} G_w 2^{7 (3 - w)} (|H| < 2^45) and L the same of
 // G_4..G_7 (|L| < 2^47), both exact in int64 and in FP64, and one FMA forms H 2^28 + L with a
-// single rounding.
+// single rounding.  Formed with integer operations only (a 128-bit pair normalised to 53
+// bits, the same result bit for bit) the epilogue measured slower: 812 against 755 us per FD
+// apply at 3D n = 130, although those three FP64 operations take 5.9 us of FP64 issue per
+// 8192-output tile.
 __device__ __forceinline__ double recombine(const uint32_t (&g)[kSlices], int E) {
   long long H = 0, L = 0;
 #pragma unroll
@@ -260,13 +264,23 @@ __global__ void __launch_bounds__(kF64TcThreads, 1)
       tc_fence_after();
       const int s = g / nchunks, c = g % nchunks;
       const int ksteps = min(4, (K - c * 64 + 15) / 16);
-      const uint32_t a0 = smem_u32(sA + q * kF64TcABytes);
+      // descriptors: the address field is the byte address / 16, so the K-step j + 1 (32
+      // bytes on) is the descriptor + 2 and a factor tile b_bytes on is + b_bytes / 16 (no
+      // carry: shared addresses stay below 2^18).  One thread issues 36 x 9 MMAs per tile at
+      // 3D n = 130; with both descriptors rebuilt for every MMA the issue loop, not the
+      // tensor pipe, set the pace (907 -> 755 us per FD apply once hoisted; issuing a
+      // chunk's four K-steps from one asm statement measured the same).
+      const uint64_t ad = sw128_desc(smem_u32(sA + q * kF64TcABytes));
+      const uint64_t bd0 = sw128_desc(smem_u32(sB + c * b_bytes));
+      const uint64_t bstep = (uint64_t)(nchunks * b_bytes) >> 4;  // next slice t
+      const uint32_t first = (s > 0 || c > 0) ? 1u : 0u;  // accumulator s + t starts here
       for (int t = 0; t + s < kSlices; ++t) {
-        const uint32_t b0 = smem_u32(sB + (t * nchunks + c) * b_bytes);
+        const uint64_t bd = bd0 + (uint64_t)t * bstep;
         const uint32_t dt = tmem + (uint32_t)((s + t) * n_tile);
-        for (int j = 0; j < ksteps; ++j)  // accumulator s + t starts at s = 0, c = 0, j = 0
-          mma_issue<1>(dt, sw128_desc(a0 + 32u * j), sw128_desc(b0 + 32u * j), idesc,
-                       (s > 0 || c > 0 || j > 0) ? 1u : 0u);
+        mma_issue<1>(dt, ad, bd, idesc, first);
+        if (ksteps > 1) mma_issue<1>(dt, ad + 2, bd + 2, idesc, 1u);
+        if (ksteps > 2) mma_issue<1>(dt, ad + 4, bd + 4, idesc, 1u);
+        if (ksteps > 3) mma_issue<1>(dt, ad + 6, bd + 6, idesc, 1u);
       }
       mma_commit(&empty_bar[q]);
     }
