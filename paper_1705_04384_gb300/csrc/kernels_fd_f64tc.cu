@@ -95,19 +95,27 @@ __global__ void __launch_bounds__(256) f64tc_split_kernel(IdxPtr<const double> i
     const int emax = (int)(mx >> 52);
     const int e = emax ? emax - 1022 : -1022;  // max < 2^e (zero and subnormal rows: -1022)
     if (lane == 0) rowexp[r] = e;
-    unsigned short *o = slices + r * kp;
-    for (int k = lane; k < n; k += 32) {
-      const unsigned long long b = x[k];
-      const unsigned long long F = fixed56(b, e);
-      const bool neg = (b >> 63) != 0;
+    // two adjacent values per lane: one 4-byte store (two BF16 digits) per slice; the row
+    // pitch kp is a multiple of 8 values, so pairs starting at even k are 4-byte aligned
+    unsigned int *o[kSlices];
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) o[s] = (unsigned int *)(slices + s * sstride + r * kp);
+    for (int k = 2 * lane; k < n; k += 64) {
+      const bool two = k + 1 < n;
+      const unsigned long long b0 = x[k], b1 = two ? x[k + 1] : 0ull;
+      const unsigned long long F0 = fixed56(b0, e), F1 = fixed56(b1, e);
+      const bool n0 = (b0 >> 63) != 0, n1 = (b1 >> 63) != 0;
       // digits 0..3 are bits 55..28 of F, digits 4..7 bits 27..0: two 28-bit halves, so
       // that the digit extraction runs on 32-bit shifts
-      const unsigned int fh = (unsigned int)(F >> 28), fl = (unsigned int)(F & 0xFFFFFFFull);
+      const unsigned int h0 = (unsigned int)(F0 >> 28), l0 = (unsigned int)(F0 & 0xFFFFFFFull);
+      const unsigned int h1 = (unsigned int)(F1 >> 28), l1 = (unsigned int)(F1 & 0xFFFFFFFull);
 #pragma unroll
       for (int s = 0; s < kSlices; ++s) {
-        const unsigned int half = s < 4 ? fh : fl;
-        const int dg = (int)((half >> (kDigitBits * (3 - (s & 3)))) & 127u);
-        o[s * sstride + k] = digit_bf16(neg ? -dg : dg);
+        const int sh = kDigitBits * (3 - (s & 3));
+        const int d0 = (int)(((s < 4 ? h0 : l0) >> sh) & 127u);
+        const int d1 = (int)(((s < 4 ? h1 : l1) >> sh) & 127u);
+        const unsigned int lo16 = digit_bf16(n0 ? -d0 : d0), hi16 = digit_bf16(n1 ? -d1 : d1);
+        o[s][k >> 1] = lo16 | (hi16 << 16);  // the digit of k + 1 >= n lands in padding
       }
     }
   }
