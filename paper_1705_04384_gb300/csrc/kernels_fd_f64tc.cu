@@ -20,9 +20,10 @@
 //   * C_ij = 2^{e_i + f_j - 63} sum_{w <= 7} G_w 2^{7 (7 - w)}, rounded once to FP64: two
 //     exact 64-bit partial sums and one FMA (recombine).
 // The pairs with s + t > 7 are dropped (s + t = 8: 7 pairs of at most K 2^{-56} 2^{e_i + f_j}
-// each, the rest 2^-7 smaller) and the digit tails are below 2^-56 of each scale, so the
-// error of C_ij is below about 9 K 2^{-56} 2^{e_i + f_j} (1.6e-14 of 2^{e_i + f_j} at K = 130),
-// the size of an FP64 dot product's worst-case rounding; measured on random data, 9e-16.
+// each, the rest 2^-7 smaller) and the digit tails are below 2^-56 of each scale; with the
+// final rounding of a result of up to K 2^{e_i + f_j}, the error of C_ij is below about
+// 13 K 2^{-56} 2^{e_i + f_j} (2.3e-14 of 2^{e_i + f_j} at K = 130), the size of an FP64 dot
+// product's worst-case rounding; measured on random data, 9e-16.
 // FP64 arithmetic is limited to three operations per output in the recombination and the FD
 // diagonal's multiplication: GB300's FP64 unit is shared by FMAs and the FP64 tensor path,
 // and the FP64 FD products run at its ceiling.
