@@ -27,7 +27,7 @@ def _rhs(N, nrhs, seed):
 
 
 @pytest.mark.parametrize("grid", ["latency", "throughput"])
-@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16", "none", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32", "bf16", "none", "tf32x3", "fp64tc"])
 @pytest.mark.parametrize("d,ne,p", [(2, 30, 3), (3, 9, 4)])
 def test_multi_rhs_bitwise_equals_single(prec, d, ne, p, grid):
     R = ref(d, ne, p)

@@ -100,7 +100,7 @@ def test_initial_guess_and_reproducibility(monkeypatch):
         assert i5["status"] == 0 and i5["half_steps"] < i1["half_steps"]
 
 
-@pytest.mark.parametrize("precision", ["tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("precision", ["tf32", "bf16", "tf32x3", "fp64tc"])
 def test_tensor_core_preconditioner(precision):
     R = ref(3, 10, 3)
     b = _rand(R.N, 15)

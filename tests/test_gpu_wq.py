@@ -126,7 +126,7 @@ def test_wq_gmres_fixed_k_and_to_tolerance(d, ne, p, geo):
         assert np.linalg.norm(b - R.A @ x) <= 1.05e-8 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3", "fp64tc"])
 def test_wq_precision_form_reaches_fp64_residual(prec):
     R = ref(2, 24, 4, "annulus")
     b = _rand(R.N, 5)
