@@ -414,10 +414,11 @@ __device__ __forceinline__ void pass2_fused(const KrylovWs &ws, int r,
 // (stash[j * kRT + thread]) and the dots read them back from there.  The same FMAs in the
 // same order as subtract_proj followed by chunk_dots (the path for more vectors), and the
 // same partials, so both give bitwise the same w', h2 and norm.  Measured at 2.2e6 rows
-// (config 3), 16 vectors: the two-sweep path took 38 us more than 15 vectors in one sweep;
-// this one 12 us more (16..21 vectors: 26-32 us less than the two-sweep path).
+// (the 3D 128-element annulus), 16 vectors: the two-sweep path took 38 us more than 15
+// vectors in one sweep, this one 12 us more (16..21 vectors: 26-32 us less than the
+// two-sweep path).
 // 24 and more spill registers (NA = 32 accumulators); 22 and 23 measured slower than 16..21
-// (config 3: 23 vectors took 306 us against 226 us on the two-sweep path)
+// (the 3D 128-element annulus: 23 vectors took 306 us against 226 us on the two-sweep path)
 constexpr int kStashMax = 21;
 template <int NV>
 __device__ __forceinline__ void pass2_stash(const KrylovWs &ws, int r,
