@@ -88,7 +88,7 @@ typedef struct {
  * about the cost of the latency-bound TF32 products.  FP64_TC: the FP64 form (plain GMRES,
  * FP64 FD to FP64 accuracy) with the FD mode products on the BF16 tensor cores by exact
  * integer slice products (error-free splitting of Ozaki et al. 2012: 8 digits of 7 bits
- * per value, exact FP32 sums, recombined in 128-bit integers); n <= 256, no wind.
+ * per value, exact FP32 sums, recombined exactly before one rounding); n <= 148, no wind.
  * NONE: no preconditioner (P = I).                                                     */
 typedef enum {
   IGA_PREC_FP64 = 0,

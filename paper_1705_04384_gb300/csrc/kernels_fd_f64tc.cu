@@ -12,11 +12,13 @@
 //     digits 0..127 (most significant first), which carry the sign of A_ik: A_ik =
 //     2^{e_i} sum_s d_s 2^{-7(s+1)} up to |A_ik| 2^{-56}; the same for B with digits d'_t;
 //   * a digit is an integer of at most 7 bits, exact in BF16; a product of two digits is
-//     below 2^14, and a sum of K <= 132 of them below 2^21.1, exact in FP32.  The pairs
-//     (s, t) with s + t = w accumulate into one FP32 accumulator G_w (w = 0..7), at most
-//     w + 1 <= 8 pairs: below 8 K 127^2 < 2^24 for K <= 130, so every G_w is the exact
-//     integer; at K = 131, 132 only G_7, which carries 2^-49 of the result's scale, can
-//     round (by at most 2^-63 of it);
+//     below 2^14, and a sum of K <= kF64TcMaxK = 148 of them below 2^21.2, exact in FP32.
+//     The pairs (s, t) with s + t = w accumulate into one FP32 accumulator G_w (w = 0..7),
+//     at most w + 1 pairs: |G_w| <= (w + 1) K 127^2, below 2^24 for every w <= 6 at
+//     K <= 148 (and for w = 7 at K <= 130), so G_0..G_6 are the exact integers; only G_7,
+//     whose unit is 2^-63 of the result's scale, can round, by at most one unit.  Beyond
+//     K = 148 a rounded G_6 (and for larger K G_5, G_4 ...) would cost 2^-56 (2^-49, 2^-42
+//     ...) of the scale, more than an FP64 dot product's rounding: the form stops there;
 //   * C_ij = 2^{e_i + f_j - 63} sum_{w <= 7} G_w 2^{7 (7 - w)}, rounded once to FP64: two
 //     exact 64-bit partial sums and one FMA (recombine).
 // The pairs with s + t > 7 are dropped (s + t = 8: 7 pairs of at most K 2^{-56} 2^{e_i + f_j}
@@ -51,7 +53,7 @@ constexpr int kSlices = 8;        // base-2^7 digits per value
 constexpr int kDigitBits = 7;
 constexpr int kF64TcM = 128;      // rows per tile
 constexpr int kF64TcThreads = 256;  // 8 epilogue warps: two per TMEM lane quarter
-constexpr int kF64TcMaxChunks = 4;  // n <= 256: the factor's slices fit in shared memory
+constexpr int kF64TcMaxK = 148;   // the contraction length that keeps G_0..G_6 exact
 constexpr int kF64TcSmemBudget = 225 * 1024;  // ring + resident factor (plus 1024 alignment)
 constexpr uint32_t kF64TcABytes = kF64TcM * 128;  // one 64-wide K-chunk of one slice
 
@@ -432,12 +434,12 @@ static void make_slice_map(CUtensorMap &m, const void *base, long long n, long l
     throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
 }
 
-bool f64tc_supported(int n) { return n >= 1 && (n + 63) / 64 <= kF64TcMaxChunks; }
+bool f64tc_supported(int n) { return n >= 1 && n <= kF64TcMaxK; }
 
 F64TcFd *make_f64tc_fd(int d, int n, const Factor1D &f, cudaStream_t s, int R_max,
                        const double *dinv) {
   if (!f64tc_supported(n))
-    throw Error{IGA_ERR_UNSUPPORTED, "the FP64 tensor-core FD takes n <= 256"};
+    throw Error{IGA_ERR_UNSUPPORTED, "the FP64 tensor-core FD takes n <= 148"};
   auto *t = new F64TcFd();
   try {
     t->d = d;

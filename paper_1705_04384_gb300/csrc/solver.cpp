@@ -67,7 +67,7 @@ void Ctx::setup(int d_, int n_elem_, int p_, const iga_geometry &g_, int prec_, 
   if (has_wind && (tensor_core_prec(prec) || prec == IGA_PREC_FP64_TC))
     throw Error{IGA_ERR_INVALID_ARG, "a wind requires precision FP64 or NONE"};
   if (prec == IGA_PREC_FP64_TC && !f64tc_supported(fac->n))
-    throw Error{IGA_ERR_UNSUPPORTED, "precision FP64_TC takes n <= 256 basis functions per "
+    throw Error{IGA_ERR_UNSUPPORTED, "precision FP64_TC takes n <= 148 basis functions per "
                                      "direction"};
   // per-direction FD factors: the pencil (K + w_l B', M) of Sec. 3.2 (w_l = 0: Poisson)
   for (int l = 0; l < 3; ++l)
