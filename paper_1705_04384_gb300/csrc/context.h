@@ -2,6 +2,9 @@
 // FD buffers, Krylov workspace and the captured solve graphs.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <map>
 #include <utility>
 
@@ -23,6 +26,10 @@ int *tc_fd_error_word(TcFd &fd);
 struct TcFdDeleter {
   void operator()(TcFd *p) const { destroy_tc_fd(p); }
 };
+
+// The driver's cuTensorMapEncodeTiled (kernels_fd_tc.cu), for the tensor maps of both
+// tensor-core FD paths.
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder();
 
 // FP64 FD on exact BF16 slice products (IGA_PREC_FP64_TC) -- kernels_fd_f64tc.cu
 struct F64TcFd;

@@ -402,22 +402,6 @@ static void split_factor_host(const std::vector<double> &B, int n, int kp,
   }
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 f64tc_encoder() {
-  static std::mutex mu;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    IGA_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                                  cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
-      throw Error{IGA_ERR_CUDA, "cuTensorMapEncodeTiled not available"};
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
-
 // 3D map over kSlices stacked row-major BF16 matrices (rows x kp, inner extent n: reads
 // past n are zero); box = one 128-byte K-chunk x box_rows of one slice.
 static void make_slice_map(CUtensorMap &m, const void *base, long long n, long long rows,
@@ -426,7 +410,7 @@ static void make_slice_map(CUtensorMap &m, const void *base, long long n, long l
   cuuint64_t strides[2] = {(cuuint64_t)(kp * 2), (cuuint64_t)(rows * kp * 2)};
   cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = f64tc_encoder()(
+  const CUresult r = tmap_encoder()(
       &m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -663,7 +663,8 @@ static void autotune(TcFd &t, cudaStream_t s) {
 
 int tc_fd_tile(const TcFd &t) { return t.n_tile; }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+// The driver's cuTensorMapEncodeTiled, looked up once (shared with kernels_fd_f64tc.cu).
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static std::mutex mu;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   std::lock_guard<std::mutex> lk(mu);
