@@ -25,7 +25,21 @@ def _ptr(t):
 
 
 class Problem:
-    """One collocation problem: ``iga_setup`` ... ``iga_destroy``."""
+    """One problem on one device: ``iga_setup_scheme`` ... ``iga_destroy``.
+
+    d (2 or 3), n_elem elements per direction, degree p; geometry "identity", "annulus" or
+    "revolved" with radii r_inner < r_outer; scheme "collocation" or "wq" (weighted-quadrature
+    Galerkin); wind: a constant convection field (collocation, FP64 or no preconditioner).
+    precision selects the FD preconditioner's arithmetic (``iga_precision``):
+      "fp64"    plain GMRES, FP64 FD;
+      "fp64tc"  plain GMRES, the FP64 FD to FP64 accuracy from exact BF16 slice products on
+                the tensor cores (n <= 148, no wind);
+      "tf32", "bf16", "tf32x3"  flexible GMRES, the FD on the tensor cores with FP32
+                accumulation ("tf32x3": error-compensated TF32);
+      "none"    no preconditioner.
+    grid "latency" (one solve at a time) or "throughput" (batched / served); stream: the
+    torch CUDA stream the handle's work runs on.
+    """
 
     def __init__(self, d, n_elem, p, geometry="annulus", r_inner=1.0, r_outer=2.0,
                  precision="fp64", device="cuda", stream=None, grid="latency", wind=None,
